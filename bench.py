@@ -1,0 +1,346 @@
+#!/usr/bin/env python
+"""Benchmark of the matrix-free diffusion action (paper Section 2, A_L u_L) on one GB300.
+
+Workload (default): 64^3-element hexahedral mesh of the unit cube, interior vertices perturbed by up
+to 0.1h (seed 0), p = 7 on GLL nodes with collocated GLL quadrature, six stored symmetric geometric
+factors with k = 1 + 0.5 sin(2 pi x) sin(2 pi y) sin(2 pi z), x ~ U[-1, 1]: 90,518,849 DOFs.
+A step is one FP64 application y = A x of the whole fused path (gather, contractions, pointwise
+quadrature operator, transposed contractions, atomic-free scatter); inputs are resident in HBM and
+far larger than L2 (x 0.72 GB, quadrature data 6.4 GB), so no L2 flush is needed.
+
+Beside the headline it measures the FP32-arithmetic operator (FP32 and BF16 quadrature data), the
+end-to-end call with host buffers, 100 Jacobi-PCG iterations, CG time to a relative residual of
+1e-10 in FP64 and with mixed-precision refinement, and the CPU oracle on a bounded sample.
+
+--impl reference times the CPU oracle (dense per-element quadrature, no sum factorization) on the
+host cores, on a bounded sample of the same workload per step.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import synthetic  # noqa: E402
+
+METRIC = "diffusion apply GDOF/s at p=7 (FP64 vs mixed), % HBM roofline, CG time-to-1e-10"
+FP64_NOMINAL_TFLOPS = 1.25      # GB300 dense FP64 (profiling recipe's nominal table)
+WORKLOADS = {
+    "c2": dict(N=64, p=7),      # the diffusion workload named by element count
+    "c2a": dict(N=40, p=7),     # 22.19M DOFs: the DOF count quoted for the same workload
+    "c4": dict(N=80, p=7),      # the mixed-precision CG workload
+}
+
+
+def cost_per_element(p):
+    """Section 2: 7 (p+1)^3 reads and 12 (p+1)^4 + 15 (p+1)^3 flops per element (collocated)."""
+    P = p + 1
+    return 7 * P ** 3, 12 * P ** 4 + 15 * P ** 3
+
+
+def algorithmic_bytes(m, qbytes):
+    """x read + y write once per L-node (8 B each), the quadrature data, the int32 restriction."""
+    return 16 * m.n_ldof + 6 * qbytes * m.n_elem * (m.p + 1) ** 3 + 4 * m.n_elem * (m.p + 1) ** 3
+
+
+def load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons while the timed region runs."""
+
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index=0):
+        self.index, self.samples, self.proc = index, [], None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [s.strip() for s in line.split(",")]
+            if len(parts) >= 7:
+                self.samples.append(parts)
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.samples:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+        sm = [float(s[0]) for s in self.samples if s[0].replace(".", "").isdigit()]
+        mx = [float(s[1]) for s in self.samples if s[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for s in self.samples for k in range(4) if s[3 + k].lower() == "active"})
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.samples)}
+
+
+def oracle_sample_rate(m, n_elem_sample, seed=1):
+    """CPU oracle: dense FP64 diffusion action on the first n elements; returns (DOF/s, seconds, threads)."""
+    from oracle import fem
+    sp_ = fem.Space(m.p, "gll")
+    sel = np.arange(n_elem_sample)
+    G = fem.qdata_diffusion(sp_, m.vertices[sel], "sine")
+    x = synthetic.uniform(m.n_ldof, seed=seed)
+    t0 = time.perf_counter()
+    fem.apply(sp_, m.elem_dofs[sel], G, x, fem.DIFFUSION)
+    dt = time.perf_counter() - t0
+    dof_per_elem = m.n_ldof / m.n_elem
+    return n_elem_sample * dof_per_elem / dt, dt
+
+
+def blas_threads():
+    try:
+        from threadpoolctl import threadpool_info
+        n = [i.get("num_threads", 0) for i in threadpool_info() if i.get("user_api") == "blas"]
+        if n:
+            return max(n)
+    except Exception:
+        pass
+    return os.cpu_count()
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    wl = WORKLOADS[args.workload]
+    m = synthetic.cube_mesh(wl["N"], wl["p"], seed=0)
+    n_sample = args.ref_sample
+    times = []
+    for it in range(args.warmup + args.steps):
+        rate, dt = oracle_sample_rate(m, n_sample, seed=1 + it)
+        if it >= args.warmup:
+            times.append(dt)
+    dof = n_sample * m.n_ldof / m.n_elem
+    value = dof * len(times) / sum(times) / 1e9
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "GDOF/s", "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(times) / len(times),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"diffusion apply, {wl['N']}^3 perturbed hexes, p={wl['p']}, GLL collocated",
+                   "n_ldof": m.n_ldof, "sample_elements_per_step": n_sample},
+        "cpu_baseline": {"value": value, "unit": "GDOF/s", "cores": blas_threads(), "kind": "oracle",
+                         "sample": f"{n_sample} of {m.n_elem} elements per step (dense per-element FP64 "
+                                   f"quadrature, numpy), rate scaled to DOFs by n_ldof/n_elem"},
+        "e2e": {"value": value, "unit": "GDOF/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="c2", choices=sorted(WORKLOADS))
+    ap.add_argument("--cg", type=int, default=1, help="run the CG measurements (1) or skip them (0)")
+    ap.add_argument("--cg-workload", default="c2", choices=sorted(WORKLOADS))
+    ap.add_argument("--cpu-sample", type=int, default=6000, help="elements in the timed oracle sample")
+    ap.add_argument("--ref-sample", type=int, default=1000, help="elements per reference-arm step")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    if args.warmup < 3:
+        raise SystemExit("--warmup must be >= 3")
+
+    import torch
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    import paper_2109_05072_gb300 as ceed
+
+    def barrier():
+        if ws > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    wl = WORKLOADS[args.workload]
+    N, p = wl["N"], wl["p"]
+    m = synthetic.cube_mesh(N, p, seed=0)
+    dev = torch.device("cuda", local)
+    mesh = ceed.ceed_setup_mesh(m.n_elem, m.n_ldof, p, torch.from_numpy(m.elem_dofs).to(dev),
+                                torch.from_numpy(m.vertices).to(dev), torch.from_numpy(m.boundary).to(dev))
+    qd64 = ceed.alloc_qdata(mesh, ceed.CEED_OP_DIFFUSION, ceed.CEED_F64, dev)
+    ceed.ceed_build_qdata(mesh, ceed.CEED_OP_DIFFUSION, ceed.CEED_COEFF_SINE, None, ceed.CEED_F64, qd64)
+    x_host = synthetic.uniform(m.n_ldof, seed=1 + rank)
+    x = torch.from_numpy(x_host).to(dev)
+    y = torch.empty_like(x)
+    stream = torch.cuda.current_stream()
+
+    def timed(fn, steps, warmup):
+        for _ in range(warmup):
+            fn()
+        torch.cuda.synchronize()
+        barrier()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+        ms = e0.elapsed_time(e1)
+        if ws > 1:
+            import torch.distributed as dist
+            t = torch.tensor([ms], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms = t.item()
+        return ms / steps
+
+    # ---------------- headline: FP64 apply
+    apply64 = lambda: ceed.ceed_apply_diffusion(mesh, qd64, ceed.CEED_F64, x, y)
+    with ClockSampler(local) as clk:
+        ms64 = timed(apply64, args.steps, args.warmup)
+    gdofs64 = ws * m.n_ldof / ms64 / 1e6
+    reads, flops_el = cost_per_element(p)
+    hbm_peak, hbm_kind = load_peaks()
+    bytes64 = algorithmic_bytes(m, 8)
+    launches_per_apply = mesh.n_colors
+    ms_launch = ms64 / launches_per_apply
+    flops_launch = flops_el * m.n_elem / launches_per_apply
+    achieved_tf = flops_launch / (ms_launch * 1e-3) / 1e12
+
+    # ---------------- FP32-arithmetic operator (mixed), FP32 and BF16 quadrature data
+    mixed = {}
+    for name, prec, qb in (("f32", ceed.CEED_F32, 4), ("bf16", ceed.CEED_BF16, 2)):
+        qlo = ceed.alloc_qdata(mesh, ceed.CEED_OP_DIFFUSION, prec, dev)
+        ceed.ceed_build_qdata(mesh, ceed.CEED_OP_DIFFUSION, ceed.CEED_COEFF_SINE, None, prec, qlo)
+        ms = timed(lambda: ceed.ceed_apply_diffusion(mesh, qlo, prec, x, y), args.steps, args.warmup)
+        by = algorithmic_bytes(m, qb)
+        mixed[name] = {"gdofs": ws * m.n_ldof / ms / 1e6, "ms": ms, "alg_bytes": by,
+                       "hbm_gbs": by / (ms * 1e-3) / 1e9, "hbm_frac": by / (ms * 1e-3) / 1e9 / hbm_peak}
+        del qlo
+    torch.cuda.empty_cache()
+
+    # ---------------- end to end through the C ABI with host buffers (pinned), copies inside the region
+    xh = torch.from_numpy(x_host).pin_memory()
+    yh = torch.empty_like(xh).pin_memory()
+
+    def e2e_step():
+        x.copy_(xh, non_blocking=True)
+        ceed.ceed_apply_diffusion(mesh, qd64, ceed.CEED_F64, x, y)
+        yh.copy_(y, non_blocking=True)
+    ms_e2e = timed(e2e_step, max(3, args.steps // 2), 3)
+
+    # ---------------- CG: 100 FP64 iterations, and time to 1e-10 (FP64 vs mixed refinement)
+    cg = None
+    if args.cg:
+        cg = {}
+        if args.cg_workload != args.workload:
+            del qd64
+            mesh.close()
+            torch.cuda.empty_cache()
+            wlc = WORKLOADS[args.cg_workload]
+            m = synthetic.cube_mesh(wlc["N"], wlc["p"], seed=0)
+            mesh = ceed.ceed_setup_mesh(m.n_elem, m.n_ldof, wlc["p"], torch.from_numpy(m.elem_dofs).to(dev),
+                                        torch.from_numpy(m.vertices).to(dev), torch.from_numpy(m.boundary).to(dev))
+            qd64 = ceed.alloc_qdata(mesh, ceed.CEED_OP_DIFFUSION, ceed.CEED_F64, dev)
+            ceed.ceed_build_qdata(mesh, ceed.CEED_OP_DIFFUSION, ceed.CEED_COEFF_SINE, None, ceed.CEED_F64, qd64)
+        b = torch.empty(m.n_ldof, dtype=torch.float64, device=dev)
+        ceed.ceed_manufactured_rhs(mesh, ceed.CEED_COEFF_SINE, b, flags=ceed.CEED_APPLY_DIRICHLET)
+        xs = torch.empty_like(b)
+        st, rep = ceed.ceed_cg_solve(mesh, qd64, ceed.CEED_F64, b, xs, mode=ceed.CEED_CG_FP64, fixed_iters=100,
+                                     op=ceed.CEED_OP_DIFFUSION)
+        cg["fp64_100_iters_s"] = rep["seconds"]
+        cg["fp64_100_iters_dof_iter_per_s"] = 100 * m.n_ldof / rep["seconds"]
+        st, rep64 = ceed.ceed_cg_solve(mesh, qd64, ceed.CEED_F64, b, xs, mode=ceed.CEED_CG_FP64, tol=1e-10,
+                                       max_iter=20000, op=ceed.CEED_OP_DIFFUSION, raise_on_error=False)
+        cg["fp64_to_1e-10"] = dict(rep64, status=st)
+        for name, prec in (("f32", ceed.CEED_F32), ("bf16", ceed.CEED_BF16)):
+            qlo = ceed.alloc_qdata(mesh, ceed.CEED_OP_DIFFUSION, prec, dev)
+            ceed.ceed_build_qdata(mesh, ceed.CEED_OP_DIFFUSION, ceed.CEED_COEFF_SINE, None, prec, qlo)
+            st, repm = ceed.ceed_cg_solve(mesh, qd64, ceed.CEED_F64, b, xs, mode=ceed.CEED_CG_MIXED, tol=1e-10,
+                                          max_iter=40000, op=ceed.CEED_OP_DIFFUSION, qdata_lo=qlo, prec_lo=prec,
+                                          inner_tol=1e-4, raise_on_error=False)
+            cg[f"mixed_{name}_to_1e-10"] = dict(repm, status=st)
+            if rep64["seconds"] > 0 and repm["seconds"] > 0:
+                cg[f"mixed_{name}_speedup"] = rep64["seconds"] / repm["seconds"]
+            del qlo
+        cg["workload"] = f"{WORKLOADS[args.cg_workload]['N']}^3, p=7, n_ldof={m.n_ldof}"
+
+    # ---------------- CPU oracle on a bounded sample (rank 0, N = 1 only)
+    cpu = None
+    if rank == 0 and ws == 1 and args.cpu_sample > 0:
+        mc = synthetic.cube_mesh(N, p, seed=0)
+        rate, dt = oracle_sample_rate(mc, min(args.cpu_sample, mc.n_elem))
+        cpu = {"value": rate / 1e9, "unit": "GDOF/s", "cores": blas_threads(), "kind": "oracle",
+               "sample": f"first {min(args.cpu_sample, mc.n_elem)} of {mc.n_elem} elements, dense FP64 "
+                         f"per-element quadrature (numpy), {dt:.1f} s; DOFs counted as n_ldof/n_elem per element"}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": gdofs64, "unit": "GDOF/s", "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms64, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"FP64 diffusion apply, {N}^3 perturbed hexes (0.1h), p={p}, GLL collocated q=p+1, "
+                                   f"6 stored geometric factors, k=1+0.5sin sin sin",
+                       "n_ldof": m.n_ldof if args.cg_workload == args.workload else synthetic.cube_mesh(N, p, build_map=False).n_ldof,
+                       "n_elem": N ** 3, "l2": "inputs larger than L2 (qdata 6.4 GB), no flush",
+                       "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU"},
+            "roofline": {"bound": "alu", "achieved": achieved_tf, "peak": FP64_NOMINAL_TFLOPS, "unit": "TFLOP/s",
+                         "frac": achieved_tf / FP64_NOMINAL_TFLOPS, "traffic": None,
+                         "kernel": "apply_kernel<8,8,DIFFUSION,double,double>",
+                         "peak_kind": "nominal FP64 (no FP64 entry in MEASURED_PEAKS.json)",
+                         "flops_per_launch": flops_launch, "ms_per_launch": ms_launch,
+                         "hbm_gbs": bytes64 / (ms64 * 1e-3) / 1e9, "hbm_peak": hbm_peak, "hbm_peak_kind": hbm_kind,
+                         "hbm_frac": bytes64 / (ms64 * 1e-3) / 1e9 / hbm_peak},
+            "mixed_apply": mixed,
+            "e2e": {"value": ws * m.n_ldof / ms_e2e / 1e6 if args.cg_workload == args.workload else None,
+                    "unit": "GDOF/s", "h2d_bytes_per_step": 8 * len(x_host), "d2h_bytes_per_step": 8 * len(x_host)},
+            "gpu_launches": args.steps * launches_per_apply,
+            "clocks": clk.summary(),
+            "cg": cg,
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,203 @@
+/*
+ * ceed_gb300.h -- C ABI of the GB300 (sm_103a) matrix-free hexahedral operator library.
+ *
+ * The library computes the action y = A x of the high-order finite-element mass and
+ * diffusion operators on hexahedral meshes without assembling A (paper Section 2:
+ * A_L = block-diag(A^e), A^e = D^T G^e D, applied element by element with sum-factorized
+ * tensor contractions), and a preconditioned conjugate-gradient solver on top of it
+ * (Section 1: CG with a cheap preconditioner on the matrix-free operator).
+ *
+ * Conventions for every entry point:
+ *  - Every call returns an int status (ceed_status); none aborts or throws across the ABI.
+ *    On failure ceed_last_error() returns a message (thread-local).
+ *  - Vectors, quadrature data, coefficient fields and workspaces are CALLER-OWNED device
+ *    memory (e.g. torch tensors).  The mesh handle owns only the tables it builds at setup
+ *    (colour-sorted restriction, element permutation, a copy of the vertices, 1D bases).
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).  Apply
+ *    calls are asynchronous on it and OVERWRITE y (they do not accumulate into it).
+ *  - Numbering: element nodes n = a + P (b + P c) (a along r fastest, P = p + 1); quadrature
+ *    points q = i + Q (j + Q k).  Per-element, per-point arrays passed by the caller
+ *    (coefficients, dL/dk) are [n_elem][Q^3] in the caller's element order.
+ *  - L-vectors hold ncomp * nrhs interleaved columns: entry (dof, comp, rhs) lives at
+ *    (dof * ncomp + comp) * nrhs + rhs.  All L-vectors are FP64.
+ */
+#ifndef CEED_GB300_H
+#define CEED_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct ceed_mesh_s *ceed_mesh_t;
+
+typedef enum {
+  CEED_OK = 0,
+  CEED_ERR_INVALID = 1,        /* bad argument (size, pointer, out-of-range index, unsupported p) */
+  CEED_ERR_CUDA = 2,           /* a CUDA runtime call failed */
+  CEED_ERR_OOM = 3,            /* device or host allocation failed */
+  CEED_ERR_NOT_CONVERGED = 4,  /* solver hit its iteration cap (report still filled) */
+  CEED_ERR_UNSUPPORTED = 5,    /* valid request this build does not implement */
+  CEED_ERR_BAD_GEOMETRY = 6,   /* det J <= 0 at some quadrature point */
+  CEED_ERR_TIMEOUT = 7,        /* a bounded device-side wait gave up */
+  CEED_ERR_NONFINITE = 8       /* NaN/Inf met in a solver reduction */
+} ceed_status;
+
+/* Precision of stored quadrature data; it also selects the operator arithmetic:
+ * F64 -> FP64 contractions; F32/BF16/F16 -> FP32 contractions (FP64 L-vectors in and out). */
+typedef enum { CEED_F64 = 0, CEED_F32 = 1, CEED_BF16 = 2, CEED_F16 = 3 } ceed_prec;
+
+/* Quadrature: GLL = collocated on the p+1 Gauss-Lobatto nodes (BP5 style, Q = p+1);
+ * GAUSS = Q Gauss-Legendre points per direction (BP1/BP3 style, default Q = p+2). */
+typedef enum { CEED_QRULE_GLL = 0, CEED_QRULE_GAUSS = 1 } ceed_qrule;
+
+typedef enum { CEED_OP_MASS = 0, CEED_OP_DIFFUSION = 1 } ceed_op;
+
+/* Coefficient (rho for mass, k for diffusion):
+ *  ONE       1 everywhere                       coeff ignored (may be NULL)
+ *  CONST     coeff[0] (host pointer)            a positive constant
+ *  SINE      1 + 0.5 sin(2 pi x) sin(2 pi y) sin(2 pi z) at the physical quadrature points
+ *  PER_QPT   device array [n_elem][Q^3], caller's element order                        */
+typedef enum { CEED_COEFF_ONE = 0, CEED_COEFF_CONST = 1, CEED_COEFF_SINE = 2, CEED_COEFF_PER_QPT = 3 } ceed_coeff;
+
+/* Apply flags. */
+#define CEED_APPLY_DIRICHLET 1u  /* rows/columns of Dirichlet nodes replaced by the identity */
+
+typedef struct {
+  int64_t n_elem;            /* E >= 1 */
+  int64_t n_ldof;            /* nodes in the L-vector, < 2^30 */
+  int32_t p;                 /* polynomial order, 1..8 */
+  int32_t q_rule;            /* ceed_qrule */
+  int32_t n_qpts_1d;         /* Q; 0 selects the default (p+1 for GLL, p+2 for GAUSS); GAUSS needs Q = p+2 */
+  int32_t ncomp;             /* components per node (>= 1), sharing one operator (A (x) I) */
+  const int32_t *elem_dofs;  /* device [E][(p+1)^3], 0 <= dof < n_ldof, every dof referenced */
+  const double *vertices;    /* device [E][8][3], trilinear element map, vertex v = vx + 2 vy + 4 vz */
+  const uint8_t *dirichlet;  /* device [n_ldof] (nonzero = Dirichlet node) or NULL */
+} ceed_mesh_desc;
+
+/* Build a mesh handle (paper Section 2: the element restriction and 1D bases of the
+ * factored operator).  Copies elem_dofs/vertices/dirichlet to the host, validates them,
+ * colours the elements greedily so that no two elements of one colour share a node, and
+ * uploads a colour-sorted restriction with first-writer and Dirichlet flags (this is what
+ * makes the scatter-add atomic-free and deterministic).  The caller's arrays may be freed
+ * afterwards.  Synchronizes `stream`.  Errors: INVALID (sizes, p, out-of-range or
+ * unreferenced dof), UNSUPPORTED (more than 64 colours), OOM, CUDA. */
+int ceed_setup_mesh(const ceed_mesh_desc *desc, ceed_mesh_t *out, void *stream);
+
+/* Release a handle and its device tables (NULL is a no-op).  Synchronizes the device. */
+int ceed_destroy_mesh(ceed_mesh_t mesh);
+
+/* Mesh facts: number of colours, points per direction Q, nodes per direction P. */
+int ceed_mesh_info(ceed_mesh_t mesh, int32_t *n_colors, int32_t *Q, int32_t *P);
+
+/* Bytes of quadrature data for (op, prec): mass 1 value per point, diffusion 6 (the
+ * symmetric G_rr, G_rs, G_rt, G_ss, G_st, G_tt of Section 2).  Layout is internal:
+ * [colour-sorted element][component][Q^3]. */
+size_t ceed_qdata_bytes(ceed_mesh_t mesh, int op, int prec);
+
+/* Compute quadrature data (Section 2: the six diagonal matrices of the symmetric tensor
+ * G^e; mass: w |det J| rho).  Diffusion: G = w k adj(J) adj(J)^T / det J.  Writes
+ * ceed_qdata_bytes(mesh, op, prec) bytes to `qdata` (device).  Synchronizes `stream` to
+ * report BAD_GEOMETRY if det J <= 0 anywhere. */
+int ceed_build_qdata(ceed_mesh_t mesh, int op, int coeff_kind, const double *coeff, int prec,
+                     void *qdata, void *stream);
+
+/* y = M x: matrix-free mass action (BP1).  x, y device FP64 [n_ldof * ncomp * nrhs],
+ * x and y must not overlap.  `prec` is the precision qdata was built in. */
+int ceed_apply_mass(ceed_mesh_t mesh, const void *qdata, int prec, const double *x, double *y,
+                    int nrhs, unsigned flags, void *stream);
+
+/* y = A x: matrix-free diffusion action (BP3/BP5), Section 2's A_L u_L.  One fused kernel
+ * per colour: gather (L->E), 1D contractions to quadrature points, pointwise G^e, transposed
+ * contractions, scatter-add (E->L) without atomics.  Same argument rules as ceed_apply_mass. */
+int ceed_apply_diffusion(ceed_mesh_t mesh, const void *qdata, int prec, const double *x, double *y,
+                         int nrhs, unsigned flags, void *stream);
+
+/* Jacobi diagonal of the operator (the cheap preconditioner for CG, Section 1), FP64
+ * [n_ldof * ncomp] (one value per node and component); with CEED_APPLY_DIRICHLET the
+ * Dirichlet entries are 1. */
+int ceed_jacobi_diagonal(ceed_mesh_t mesh, int op, const void *qdata, int prec, double *diag,
+                         unsigned flags, void *stream);
+
+/* Right-hand side b_i = sum_e sum_q w |det J| f(x_q) phi_i(x_q) for the manufactured solution
+ * u* = sin(pi x) sin(pi y) sin(pi z), f = -div(k grad u*), k = coeff_kind (ONE or SINE),
+ * integrated with the mesh's quadrature.  Zero on Dirichlet nodes with CEED_APPLY_DIRICHLET.
+ * b: device FP64 [n_ldof] (ncomp must be 1). */
+int ceed_manufactured_rhs(ceed_mesh_t mesh, int coeff_kind, double *b, unsigned flags, void *stream);
+
+/* ---------------------------------------------------------------- CG solver */
+
+typedef enum { CEED_CG_FP64 = 0, CEED_CG_MIXED = 1 } ceed_cg_mode;
+
+typedef struct {
+  int32_t mode;           /* ceed_cg_mode */
+  int32_t max_iter;       /* cap on (inner) iterations in total; 0 -> 10000 */
+  int32_t max_outer;      /* MIXED: cap on refinement steps; 0 -> 50 */
+  int32_t check_every;    /* host convergence check period in iterations; 0 -> 25 */
+  int32_t fixed_iters;    /* > 0: run exactly this many FP64 iterations (no tolerance stop) */
+  int32_t op;             /* ceed_op of the operator (DIFFUSION for the bake-off CG) */
+  double tol;             /* stop when ||b - A x||_2 <= tol ||b||_2; 0 -> 1e-10 */
+  double inner_tol;       /* MIXED: inner relative reduction; 0 -> 1e-4 */
+  const void *qdata_lo;   /* MIXED: quadrature data for the inner operator */
+  int32_t prec_lo;        /* MIXED: its precision (F32, BF16 or F16) */
+  int32_t use_x0;         /* nonzero: x holds the initial guess; else x0 = 0 */
+} ceed_cg_opts;
+
+typedef struct {
+  int32_t iterations;       /* FP64 CG iterations, or inner iterations summed over refinements */
+  int32_t outer_iterations; /* MIXED: refinement steps (FP64 residual evaluations) */
+  double rel_residual;      /* ||b - A x|| / ||b|| with the FP64 operator at exit */
+  double seconds;           /* wall time of the solve, measured with CUDA events */
+} ceed_cg_report;
+
+/* Bytes of device workspace ceed_cg_solve needs for these options. */
+size_t ceed_cg_workspace_bytes(ceed_mesh_t mesh, const ceed_cg_opts *opts);
+
+/* Solve A x = b with Jacobi-preconditioned CG (Section 1) on the Dirichlet-masked operator.
+ * FP64 mode: all arithmetic FP64.  MIXED mode: iterative refinement, outer residual
+ * r = b - A x with the FP64 operator (qdata, prec), inner PCG with the low-precision operator
+ * (opts->qdata_lo, FP32 contractions) and FP64 vectors, dot products and updates; x += d.
+ * b, x: device FP64 [n_ldof] (ncomp = 1).  work: device, ceed_cg_workspace_bytes bytes,
+ * 256-byte aligned.  Synchronizes `stream`.  Returns NOT_CONVERGED (report filled) on the cap,
+ * NONFINITE on a NaN/Inf reduction. */
+int ceed_cg_solve(ceed_mesh_t mesh, const void *qdata, int prec, const double *b, double *x,
+                  const ceed_cg_opts *opts, ceed_cg_report *report, void *work, size_t work_bytes,
+                  void *stream);
+
+/* ---------------------------------------------------------------- adjoint */
+
+/* Geometric factor without coefficient, Ghat = w adj(J) adj(J)^T / det J (6 per point, FP64),
+ * stored for the adjoint: same size/layout as diffusion qdata in F64.  Synchronizes. */
+int ceed_build_geometry(ceed_mesh_t mesh, void *geo, void *stream);
+
+/* y = A(k) x for a per-point coefficient k (device [n_elem][Q^3], caller's element order),
+ * with geometry either stored (geo from ceed_build_geometry) or recomputed from the vertices
+ * (geo = NULL).  FP64.  nrhs/ncomp = 1. */
+int ceed_apply_diffusion_k(ceed_mesh_t mesh, const double *k, const void *geo, const double *x,
+                           double *y, unsigned flags, void *stream);
+
+/* Adjoint of L = 0.5 ||A(k) x - b||^2 given r = A(k) x - b:
+ *   dLdx = A(k) r                                   (A is symmetric)
+ *   dLdk[e][q] = (grad_xi r^e)_q^T Ghat_q (grad_xi x^e)_q
+ * in one fused kernel per colour.  dLdx: device FP64 [n_ldof]; dLdk: device [n_elem][Q^3]
+ * (caller's element order).  geo: stored geometry or NULL (recompute). */
+int ceed_apply_diffusion_adjoint(ceed_mesh_t mesh, const double *k, const void *geo, const double *x,
+                                 const double *r, double *dLdx, double *dLdk, void *stream);
+
+/* ---------------------------------------------------------------- vectors */
+
+/* Deterministic dot product of two device FP64 vectors; the result is written to *out
+ * (device FP64).  work: device scratch of ceed_dot_workspace_bytes(n) bytes. */
+size_t ceed_dot_workspace_bytes(int64_t n);
+int ceed_dot(const double *x, const double *y, int64_t n, double *out, void *work, void *stream);
+
+/* Thread-local message for the last failing call on this thread ("" if none). */
+const char *ceed_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CEED_GB300_H */

@@ -1,0 +1,269 @@
+"""Thin Python binding of libceedgb.so (the GB300 matrix-free hexahedral operator library).
+
+Every function here has the name of the C entry point it wraps (include/ceed_gb300.h) and only
+marshals arguments: torch CUDA tensors become device pointers, the current torch stream becomes
+the cudaStream_t.  All work runs in the library's CUDA kernels; there is no fallback path, and
+importing this module fails loudly when the library has not been built.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import torch
+
+from .build import LIB
+
+# ceed_status
+CEED_OK, CEED_ERR_INVALID, CEED_ERR_CUDA, CEED_ERR_OOM = 0, 1, 2, 3
+CEED_ERR_NOT_CONVERGED, CEED_ERR_UNSUPPORTED, CEED_ERR_BAD_GEOMETRY = 4, 5, 6
+CEED_ERR_TIMEOUT, CEED_ERR_NONFINITE = 7, 8
+# ceed_prec
+CEED_F64, CEED_F32, CEED_BF16, CEED_F16 = 0, 1, 2, 3
+# ceed_qrule / ceed_op / ceed_coeff
+CEED_QRULE_GLL, CEED_QRULE_GAUSS = 0, 1
+CEED_OP_MASS, CEED_OP_DIFFUSION = 0, 1
+CEED_COEFF_ONE, CEED_COEFF_CONST, CEED_COEFF_SINE, CEED_COEFF_PER_QPT = 0, 1, 2, 3
+CEED_APPLY_DIRICHLET = 1
+CEED_CG_FP64, CEED_CG_MIXED = 0, 1
+
+PREC_BYTES = {CEED_F64: 8, CEED_F32: 4, CEED_BF16: 2, CEED_F16: 2}
+
+
+class CeedError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"ceed status {status}: {msg}")
+        self.status = status
+
+
+class _MeshDesc(ctypes.Structure):
+    _fields_ = [("n_elem", ctypes.c_int64), ("n_ldof", ctypes.c_int64), ("p", ctypes.c_int32),
+                ("q_rule", ctypes.c_int32), ("n_qpts_1d", ctypes.c_int32), ("ncomp", ctypes.c_int32),
+                ("elem_dofs", ctypes.c_void_p), ("vertices", ctypes.c_void_p), ("dirichlet", ctypes.c_void_p)]
+
+
+class _CgOpts(ctypes.Structure):
+    _fields_ = [("mode", ctypes.c_int32), ("max_iter", ctypes.c_int32), ("max_outer", ctypes.c_int32),
+                ("check_every", ctypes.c_int32), ("fixed_iters", ctypes.c_int32), ("op", ctypes.c_int32),
+                ("tol", ctypes.c_double), ("inner_tol", ctypes.c_double), ("qdata_lo", ctypes.c_void_p),
+                ("prec_lo", ctypes.c_int32), ("use_x0", ctypes.c_int32)]
+
+
+class _CgReport(ctypes.Structure):
+    _fields_ = [("iterations", ctypes.c_int32), ("outer_iterations", ctypes.c_int32),
+                ("rel_residual", ctypes.c_double), ("seconds", ctypes.c_double)]
+
+
+def _load():
+    if not os.path.exists(LIB):
+        raise ImportError(f"libceedgb.so is not built ({LIB}); run __graft_entry__.build()")
+    lib = ctypes.CDLL(LIB)
+    vp, i32, i64, u32, dbl, sz = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_uint32, ctypes.c_double, ctypes.c_size_t
+    sig = {
+        "ceed_setup_mesh": (ctypes.c_int, [ctypes.POINTER(_MeshDesc), ctypes.POINTER(vp), vp]),
+        "ceed_destroy_mesh": (ctypes.c_int, [vp]),
+        "ceed_mesh_info": (ctypes.c_int, [vp, ctypes.POINTER(i32), ctypes.POINTER(i32), ctypes.POINTER(i32)]),
+        "ceed_qdata_bytes": (sz, [vp, ctypes.c_int, ctypes.c_int]),
+        "ceed_build_qdata": (ctypes.c_int, [vp, ctypes.c_int, ctypes.c_int, vp, ctypes.c_int, vp, vp]),
+        "ceed_apply_mass": (ctypes.c_int, [vp, vp, ctypes.c_int, vp, vp, ctypes.c_int, u32, vp]),
+        "ceed_apply_diffusion": (ctypes.c_int, [vp, vp, ctypes.c_int, vp, vp, ctypes.c_int, u32, vp]),
+        "ceed_jacobi_diagonal": (ctypes.c_int, [vp, ctypes.c_int, vp, ctypes.c_int, vp, u32, vp]),
+        "ceed_manufactured_rhs": (ctypes.c_int, [vp, ctypes.c_int, vp, u32, vp]),
+        "ceed_cg_workspace_bytes": (sz, [vp, ctypes.POINTER(_CgOpts)]),
+        "ceed_cg_solve": (ctypes.c_int, [vp, vp, ctypes.c_int, vp, vp, ctypes.POINTER(_CgOpts),
+                                         ctypes.POINTER(_CgReport), vp, sz, vp]),
+        "ceed_build_geometry": (ctypes.c_int, [vp, vp, vp]),
+        "ceed_apply_diffusion_k": (ctypes.c_int, [vp, vp, vp, vp, vp, u32, vp]),
+        "ceed_apply_diffusion_adjoint": (ctypes.c_int, [vp, vp, vp, vp, vp, vp, vp, vp]),
+        "ceed_dot_workspace_bytes": (sz, [i64]),
+        "ceed_dot": (ctypes.c_int, [vp, vp, i64, vp, vp, vp]),
+        "ceed_last_error": (ctypes.c_char_p, []),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype, f.argtypes = res, args
+    return lib, sig
+
+
+_lib, _SIGNATURES = _load()
+EXPORTED = tuple(_SIGNATURES)
+
+
+def _check(st):
+    if st != CEED_OK:
+        raise CeedError(st, _lib.ceed_last_error().decode())
+    return st
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    if not isinstance(t, torch.Tensor):
+        raise TypeError("expected a torch tensor")
+    if not t.is_cuda:
+        raise ValueError("expected a CUDA tensor (the library computes on the GPU only)")
+    if not t.is_contiguous():
+        raise ValueError("expected a contiguous tensor")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream):
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+class Mesh:
+    """Owns a ceed_mesh_t; the C handle is released on close() or garbage collection."""
+
+    def __init__(self, handle, n_elem, n_ldof, p, q_rule, ncomp):
+        self.handle = handle
+        self.n_elem, self.n_ldof, self.p, self.q_rule, self.ncomp = n_elem, n_ldof, p, q_rule, ncomp
+        nc, Q, P = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+        _check(_lib.ceed_mesh_info(handle, ctypes.byref(nc), ctypes.byref(Q), ctypes.byref(P)))
+        self.n_colors, self.Q, self.P = nc.value, Q.value, P.value
+        self.nq = self.Q ** 3
+
+    def close(self):
+        if self.handle:
+            _lib.ceed_destroy_mesh(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def ceed_setup_mesh(n_elem, n_ldof, p, elem_dofs, vertices, dirichlet=None, q_rule=CEED_QRULE_GLL, n_qpts_1d=0,
+                    ncomp=1, stream=None) -> Mesh:
+    assert elem_dofs.dtype == torch.int32 and vertices.dtype == torch.float64
+    assert dirichlet is None or dirichlet.dtype == torch.uint8
+    d = _MeshDesc(n_elem, n_ldof, p, q_rule, n_qpts_1d, ncomp, _ptr(elem_dofs), _ptr(vertices), _ptr(dirichlet))
+    h = ctypes.c_void_p()
+    _check(_lib.ceed_setup_mesh(ctypes.byref(d), ctypes.byref(h), _stream(stream)))
+    return Mesh(h, n_elem, n_ldof, p, q_rule, ncomp)
+
+
+def ceed_destroy_mesh(mesh: Mesh):
+    mesh.close()
+
+
+def ceed_qdata_bytes(mesh: Mesh, op: int, prec: int) -> int:
+    return int(_lib.ceed_qdata_bytes(mesh.handle, op, prec))
+
+
+def alloc_qdata(mesh: Mesh, op: int, prec: int, device=None) -> torch.Tensor:
+    """Caller-owned quadrature-data buffer of the right size (uint8 bytes)."""
+    return torch.empty(ceed_qdata_bytes(mesh, op, prec), dtype=torch.uint8, device=device or "cuda")
+
+
+def ceed_build_qdata(mesh: Mesh, op, coeff_kind, coeff, prec, qdata, stream=None):
+    if coeff_kind == CEED_COEFF_CONST:
+        cval = (ctypes.c_double * 1)(float(coeff))
+        cptr = ctypes.cast(cval, ctypes.c_void_p)
+    else:
+        cptr = _ptr(coeff) if coeff is not None else None
+    _check(_lib.ceed_build_qdata(mesh.handle, op, coeff_kind, cptr, prec, _ptr(qdata), _stream(stream)))
+
+
+def ceed_apply_mass(mesh: Mesh, qdata, prec, x, y, nrhs=1, flags=0, stream=None):
+    _check(_lib.ceed_apply_mass(mesh.handle, _ptr(qdata), prec, _ptr(x), _ptr(y), nrhs, flags, _stream(stream)))
+
+
+def ceed_apply_diffusion(mesh: Mesh, qdata, prec, x, y, nrhs=1, flags=0, stream=None):
+    _check(_lib.ceed_apply_diffusion(mesh.handle, _ptr(qdata), prec, _ptr(x), _ptr(y), nrhs, flags, _stream(stream)))
+
+
+def ceed_jacobi_diagonal(mesh: Mesh, op, qdata, prec, diag, flags=0, stream=None):
+    _check(_lib.ceed_jacobi_diagonal(mesh.handle, op, _ptr(qdata), prec, _ptr(diag), flags, _stream(stream)))
+
+
+def ceed_manufactured_rhs(mesh: Mesh, coeff_kind, b, flags=0, stream=None):
+    _check(_lib.ceed_manufactured_rhs(mesh.handle, coeff_kind, _ptr(b), flags, _stream(stream)))
+
+
+def _cg_opts(**kw):
+    o = _CgOpts()
+    for k, v in kw.items():
+        if k == "qdata_lo":
+            o.qdata_lo = _ptr(v)
+        else:
+            setattr(o, k, v)
+    return o
+
+
+def ceed_cg_workspace_bytes(mesh: Mesh, **opts) -> int:
+    o = _cg_opts(**opts)
+    return int(_lib.ceed_cg_workspace_bytes(mesh.handle, ctypes.byref(o)))
+
+
+def ceed_cg_solve(mesh: Mesh, qdata, prec, b, x, work=None, stream=None, raise_on_error=True, **opts):
+    """Returns (status, report dict).  opts are ceed_cg_opts fields (mode, tol, max_iter, ...)."""
+    o = _cg_opts(**opts)
+    nbytes = int(_lib.ceed_cg_workspace_bytes(mesh.handle, ctypes.byref(o)))
+    if work is None:
+        work = torch.empty(nbytes, dtype=torch.uint8, device=b.device)
+    rep = _CgReport()
+    st = _lib.ceed_cg_solve(mesh.handle, _ptr(qdata), prec, _ptr(b), _ptr(x), ctypes.byref(o), ctypes.byref(rep),
+                            _ptr(work), work.numel() * work.element_size(), _stream(stream))
+    report = dict(iterations=rep.iterations, outer_iterations=rep.outer_iterations,
+                  rel_residual=rep.rel_residual, seconds=rep.seconds)
+    if raise_on_error and st not in (CEED_OK,):
+        raise CeedError(st, _lib.ceed_last_error().decode())
+    return st, report
+
+
+def ceed_build_geometry(mesh: Mesh, geo, stream=None):
+    _check(_lib.ceed_build_geometry(mesh.handle, _ptr(geo), _stream(stream)))
+
+
+def ceed_apply_diffusion_k(mesh: Mesh, k, geo, x, y, flags=0, stream=None):
+    _check(_lib.ceed_apply_diffusion_k(mesh.handle, _ptr(k), _ptr(geo), _ptr(x), _ptr(y), flags, _stream(stream)))
+
+
+def ceed_apply_diffusion_adjoint(mesh: Mesh, k, geo, x, r, dLdx, dLdk, stream=None):
+    _check(_lib.ceed_apply_diffusion_adjoint(mesh.handle, _ptr(k), _ptr(geo), _ptr(x), _ptr(r), _ptr(dLdx),
+                                             _ptr(dLdk), _stream(stream)))
+
+
+def ceed_dot_workspace_bytes(n: int) -> int:
+    return int(_lib.ceed_dot_workspace_bytes(n))
+
+
+def ceed_dot(x, y, out, work, stream=None):
+    _check(_lib.ceed_dot(_ptr(x), _ptr(y), x.numel(), _ptr(out), _ptr(work), _stream(stream)))
+
+
+def ceed_last_error() -> str:
+    return _lib.ceed_last_error().decode()
+
+
+class DiffusionK(torch.autograd.Function):
+    """y = A(k) x with a per-point coefficient k [E, Q^3]; backward runs the fused adjoint kernel.
+
+    grad_x = A(k) grad_y (A is symmetric), grad_k[e, q] = (grad_xi g)_q^T Ghat_q (grad_xi x)_q with
+    g = grad_y.  geo: stored geometry (ceed_build_geometry) or None to recompute it from the vertices.
+    """
+
+    @staticmethod
+    def forward(ctx, x, k, mesh, geo):
+        y = torch.empty_like(x)
+        ceed_apply_diffusion_k(mesh, k, geo, x, y)
+        ctx.save_for_backward(x, k)
+        ctx.mesh, ctx.geo = mesh, geo
+        return y
+
+    @staticmethod
+    def backward(ctx, gy):
+        x, k = ctx.saved_tensors
+        gy = gy.contiguous()
+        gx = torch.empty_like(x)
+        gk = torch.empty_like(k)
+        ceed_apply_diffusion_adjoint(ctx.mesh, k, ctx.geo, x, gy, gx, gk)
+        return gx, gk, None, None
+
+
+def diffusion_k(x, k, mesh, geo=None):
+    return DiffusionK.apply(x, k, mesh, geo)

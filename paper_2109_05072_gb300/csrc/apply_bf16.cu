@@ -1,0 +1,8 @@
+// FP32-arithmetic operator with bf16 quadrature data (FP64 L-vectors in and out).
+#include "apply_kernel.cuh"
+
+namespace ceedgb {
+int launch_apply_qbf16(ceed_mesh_t m, const ApplyReq &r, cudaStream_t s) {
+  return dispatch_apply<float, __nv_bfloat16>(m, m->tab32, r, s);
+}
+}  // namespace ceedgb

@@ -1,0 +1,475 @@
+// Jacobi-preconditioned conjugate gradients on the matrix-free operator (paper Section 1: CG
+// with a cheap preconditioner; Section 2.4: Krylov updates are memory-bound streaming kernels),
+// plus FP64-outer / low-precision-inner iterative refinement.
+//
+// All scalars live on the device; every kernel after convergence is a no-op (it reads the done
+// flag), so a batch of iterations can be queued without host round trips.  Reductions are
+// deterministic: a fixed grid writes per-block partial sums that one block adds in fixed order.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+
+#include "internal.h"
+
+namespace ceedgb {
+
+constexpr int RED_THREADS = 256;
+constexpr int RED_MAX_BLOCKS = 1024;
+
+static int red_blocks(int64_t n) {
+  int64_t b = (n + RED_THREADS * 8 - 1) / (RED_THREADS * 8);
+  if (b < 1) b = 1;
+  if (b > RED_MAX_BLOCKS) b = RED_MAX_BLOCKS;
+  return (int)b;
+}
+
+struct Scalars {
+  double rz, rz_new, pq, alpha, beta, rr, bb, tol2;
+  double rr_out, bb_out;
+  int done, iters, nonfinite, pad;
+};
+
+__device__ __forceinline__ double block_sum(double v, double *sh) {
+  sh[threadIdx.x] = v;
+  __syncthreads();
+  for (int s = RED_THREADS / 2; s > 0; s >>= 1) {
+    if (threadIdx.x < s) sh[threadIdx.x] += sh[threadIdx.x + s];
+    __syncthreads();
+  }
+  const double r = sh[0];
+  __syncthreads();
+  return r;
+}
+
+__device__ __forceinline__ bool finite(double v) { return isfinite(v); }
+
+__global__ void dot_partial_kernel(const double *__restrict__ x, const double *__restrict__ y, int64_t n,
+                                   double *__restrict__ part, const Scalars *sc) {
+  __shared__ double sh[RED_THREADS];
+  if (sc && sc->done) return;
+  double a = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)RED_THREADS + threadIdx.x; i < n; i += (int64_t)gridDim.x * RED_THREADS)
+    a += x[i] * y[i];
+  a = block_sum(a, sh);
+  if (threadIdx.x == 0) part[blockIdx.x] = a;
+}
+
+// Sums nb partials in fixed order into *out.
+__global__ void sum_partials_kernel(const double *__restrict__ part, int nb, double *out) {
+  __shared__ double sh[RED_THREADS];
+  double a = 0.0;
+  for (int i = threadIdx.x; i < nb; i += RED_THREADS) a += part[i];
+  a = block_sum(a, sh);
+  if (threadIdx.x == 0) *out = a;
+}
+
+__global__ void finalize_alpha_kernel(const double *__restrict__ part, int nb, Scalars *sc) {
+  __shared__ double sh[RED_THREADS];
+  if (sc->done) return;
+  double a = 0.0;
+  for (int i = threadIdx.x; i < nb; i += RED_THREADS) a += part[i];
+  a = block_sum(a, sh);
+  if (threadIdx.x == 0) {
+    sc->pq = a;
+    sc->alpha = sc->rz / a;
+    if (!finite(sc->alpha)) {
+      sc->nonfinite = 1;
+      sc->done = 1;
+    }
+  }
+}
+
+// x += alpha p; r -= alpha q; z = dinv r; partials of r.z and r.r
+__global__ void update_kernel(double *__restrict__ x, double *__restrict__ r, double *__restrict__ z,
+                              const double *__restrict__ p, const double *__restrict__ q,
+                              const double *__restrict__ dinv, int64_t n, double *__restrict__ part_rz,
+                              double *__restrict__ part_rr, const Scalars *sc) {
+  __shared__ double sh[RED_THREADS];
+  if (sc->done) return;
+  const double alpha = sc->alpha;
+  double arz = 0.0, arr = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)RED_THREADS + threadIdx.x; i < n; i += (int64_t)gridDim.x * RED_THREADS) {
+    x[i] += alpha * p[i];
+    const double ri = r[i] - alpha * q[i];
+    r[i] = ri;
+    const double zi = dinv[i] * ri;
+    z[i] = zi;
+    arz += ri * zi;
+    arr += ri * ri;
+  }
+  arz = block_sum(arz, sh);
+  arr = block_sum(arr, sh);
+  if (threadIdx.x == 0) {
+    part_rz[blockIdx.x] = arz;
+    part_rr[blockIdx.x] = arr;
+  }
+}
+
+__global__ void finalize_beta_kernel(const double *__restrict__ part_rz, const double *__restrict__ part_rr, int nb,
+                                     Scalars *sc, int fixed) {
+  __shared__ double sh[RED_THREADS];
+  if (sc->done) return;
+  double a = 0.0, b = 0.0;
+  for (int i = threadIdx.x; i < nb; i += RED_THREADS) {
+    a += part_rz[i];
+    b += part_rr[i];
+  }
+  a = block_sum(a, sh);
+  b = block_sum(b, sh);
+  if (threadIdx.x == 0) {
+    sc->rz_new = a;
+    sc->rr = b;
+    sc->iters += 1;
+    if (!finite(a) || !finite(b)) {
+      sc->nonfinite = 1;
+      sc->done = 1;
+      return;
+    }
+    if (!fixed && b <= sc->tol2 * sc->bb) {
+      sc->done = 1;
+      return;
+    }
+    sc->beta = a / sc->rz;
+    sc->rz = a;
+  }
+}
+
+__global__ void pupdate_kernel(double *__restrict__ p, const double *__restrict__ z, int64_t n, const Scalars *sc) {
+  if (sc->done) return;
+  const double beta = sc->beta;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    p[i] = z[i] + beta * p[i];
+}
+
+// CG start from r (already holding the initial residual): z = dinv r, p = z, partials of r.z, r.r
+__global__ void start_kernel(const double *__restrict__ r, double *__restrict__ z, double *__restrict__ p,
+                             const double *__restrict__ dinv, int64_t n, double *__restrict__ part_rz,
+                             double *__restrict__ part_rr) {
+  __shared__ double sh[RED_THREADS];
+  double arz = 0.0, arr = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)RED_THREADS + threadIdx.x; i < n; i += (int64_t)gridDim.x * RED_THREADS) {
+    const double ri = r[i];
+    const double zi = dinv[i] * ri;
+    z[i] = zi;
+    p[i] = zi;
+    arz += ri * zi;
+    arr += ri * ri;
+  }
+  arz = block_sum(arz, sh);
+  arr = block_sum(arr, sh);
+  if (threadIdx.x == 0) {
+    part_rz[blockIdx.x] = arz;
+    part_rr[blockIdx.x] = arr;
+  }
+}
+
+// rz, rr from partials; bb = rr * scale (scale = 1: relative to the initial residual) or kept;
+// tol2 set by the host.  done if the start already meets the tolerance.
+__global__ void start_finalize_kernel(const double *__restrict__ part_rz, const double *__restrict__ part_rr, int nb,
+                                      Scalars *sc, int set_bb_from_rr, int fixed) {
+  __shared__ double sh[RED_THREADS];
+  double a = 0.0, b = 0.0;
+  for (int i = threadIdx.x; i < nb; i += RED_THREADS) {
+    a += part_rz[i];
+    b += part_rr[i];
+  }
+  a = block_sum(a, sh);
+  b = block_sum(b, sh);
+  if (threadIdx.x == 0) {
+    sc->rz = a;
+    sc->rr = b;
+    if (set_bb_from_rr) sc->bb = b;
+    sc->iters = 0;
+    sc->nonfinite = (!finite(a) || !finite(b)) ? 1 : 0;
+    sc->done = sc->nonfinite || (!fixed && b <= sc->tol2 * sc->bb) || b == 0.0;
+  }
+}
+
+// out = b - Ax (elementwise), partials of out.out
+__global__ void residual_kernel(const double *__restrict__ b, const double *__restrict__ Ax, double *__restrict__ out,
+                                int64_t n, double *__restrict__ part) {
+  __shared__ double sh[RED_THREADS];
+  double a = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)RED_THREADS + threadIdx.x; i < n; i += (int64_t)gridDim.x * RED_THREADS) {
+    const double v = b[i] - Ax[i];
+    out[i] = v;
+    a += v * v;
+  }
+  a = block_sum(a, sh);
+  if (threadIdx.x == 0) part[blockIdx.x] = a;
+}
+
+__global__ void axpy_kernel(double *__restrict__ x, const double *__restrict__ d, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    x[i] += d[i];
+}
+
+__global__ void invert_kernel(double *__restrict__ d, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    d[i] = 1.0 / d[i];
+}
+
+__global__ void zero_kernel(double *__restrict__ d, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    d[i] = 0.0;
+}
+
+__global__ void copy_kernel(double *__restrict__ d, const double *__restrict__ s, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    d[i] = s[i];
+}
+
+static size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
+
+struct Work {
+  double *r_out, *d, *r, *z, *p, *q, *dinv, *part1, *part2;
+  Scalars *sc;
+};
+
+static size_t layout(int64_t n, bool mixed, char *base, Work *w) {
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    char *ptr = base ? base + off : nullptr;
+    off += align256(bytes);
+    return ptr;
+  };
+  const size_t vb = (size_t)n * sizeof(double);
+  Work t{};
+  t.r = (double *)take(vb);
+  t.z = (double *)take(vb);
+  t.p = (double *)take(vb);
+  t.q = (double *)take(vb);
+  t.dinv = (double *)take(vb);
+  if (mixed) {
+    t.r_out = (double *)take(vb);
+    t.d = (double *)take(vb);
+  }
+  t.part1 = (double *)take(RED_MAX_BLOCKS * sizeof(double));
+  t.part2 = (double *)take(RED_MAX_BLOCKS * sizeof(double));
+  t.sc = (Scalars *)take(sizeof(Scalars));
+  if (w) *w = t;
+  return off;
+}
+
+static unsigned stream_blocks(int64_t n) {
+  int64_t b = (n + 255) / 256;
+  if (b > 152 * 16) b = 152 * 16;
+  return (unsigned)(b < 1 ? 1 : b);
+}
+
+static int read_scalars(Scalars *h, const Scalars *d, cudaStream_t s) {
+  CEED_CUDA_CHECK(cudaMemcpyAsync(h, d, sizeof(Scalars), cudaMemcpyDeviceToHost, s));
+  CEED_CUDA_CHECK(cudaStreamSynchronize(s));
+  return CEED_OK;
+}
+
+// Run PCG on A y = rhs (y starts at 0; rhs in w.r on entry), with the given operator.
+// Stops when ||r|| <= tol ||ref|| (ref = rhs), or after max_iter iterations, or exactly `fixed` iterations.
+static int pcg_run(ceed_mesh_t m, const ApplyReq &op, double *y, const Work &w, int64_t n, double tol, int max_iter,
+                   int check_every, int fixed, cudaStream_t s, int *iters_out, int *nonfinite) {
+  const int nb = red_blocks(n);
+  Scalars h{};
+  // tol2 and bb: bb comes from ||rhs||^2 (start_finalize with set_bb_from_rr)
+  h.tol2 = tol * tol;
+  CEED_CUDA_CHECK(cudaMemcpyAsync(&w.sc->tol2, &h.tol2, sizeof(double), cudaMemcpyHostToDevice, s));
+  zero_kernel<<<stream_blocks(n), 256, 0, s>>>(y, n);
+  start_kernel<<<nb, RED_THREADS, 0, s>>>(w.r, w.z, w.p, w.dinv, n, w.part1, w.part2);
+  start_finalize_kernel<<<1, RED_THREADS, 0, s>>>(w.part1, w.part2, nb, w.sc, 1, fixed > 0);
+  CEED_CUDA_CHECK(cudaGetLastError());
+  const int cap = fixed > 0 ? fixed : max_iter;
+  int it = 0;
+  while (it < cap) {
+    const int batch = std::min(cap - it, fixed > 0 ? cap : check_every);
+    for (int b = 0; b < batch; ++b) {
+      ApplyReq a = op;
+      a.x = w.p;
+      a.y = w.q;
+      if (int st = launch_apply(m, a, s)) return st;
+      dot_partial_kernel<<<nb, RED_THREADS, 0, s>>>(w.p, w.q, n, w.part1, w.sc);
+      finalize_alpha_kernel<<<1, RED_THREADS, 0, s>>>(w.part1, nb, w.sc);
+      update_kernel<<<nb, RED_THREADS, 0, s>>>(y, w.r, w.z, w.p, w.q, w.dinv, n, w.part1, w.part2, w.sc);
+      finalize_beta_kernel<<<1, RED_THREADS, 0, s>>>(w.part1, w.part2, nb, w.sc, fixed > 0);
+      pupdate_kernel<<<stream_blocks(n), 256, 0, s>>>(w.p, w.z, n, w.sc);
+    }
+    CEED_CUDA_CHECK(cudaGetLastError());
+    it += batch;
+    if (int st = read_scalars(&h, w.sc, s)) return st;
+    if (h.done) break;
+  }
+  if (fixed <= 0 || !h.done) {
+    if (int st = read_scalars(&h, w.sc, s)) return st;
+  }
+  *iters_out = h.iters;
+  *nonfinite = h.nonfinite;
+  return CEED_OK;
+}
+
+// r_out = b - A x with the operator; returns ||r_out||^2 on the host.
+static int residual(ceed_mesh_t m, const ApplyReq &op, const double *b, const double *x, double *Ax, double *r_out,
+                    int64_t n, double *part, double *dsum, cudaStream_t s, double *rr) {
+  ApplyReq a = op;
+  a.x = x;
+  a.y = Ax;
+  if (int st = launch_apply(m, a, s)) return st;
+  const int nb = red_blocks(n);
+  residual_kernel<<<nb, RED_THREADS, 0, s>>>(b, Ax, r_out, n, part);
+  sum_partials_kernel<<<1, RED_THREADS, 0, s>>>(part, nb, dsum);
+  CEED_CUDA_CHECK(cudaGetLastError());
+  CEED_CUDA_CHECK(cudaMemcpyAsync(rr, dsum, sizeof(double), cudaMemcpyDeviceToHost, s));
+  CEED_CUDA_CHECK(cudaStreamSynchronize(s));
+  return CEED_OK;
+}
+
+}  // namespace ceedgb
+
+using namespace ceedgb;
+
+extern "C" size_t ceed_dot_workspace_bytes(int64_t n) { return (size_t)red_blocks(n) * sizeof(double); }
+
+extern "C" int ceed_dot(const double *x, const double *y, int64_t n, double *out, void *work, void *stream) {
+  if (!x || !y || !out || !work || n < 0) return fail(CEED_ERR_INVALID, "bad ceed_dot arguments");
+  cudaStream_t s = (cudaStream_t)stream;
+  const int nb = red_blocks(n);
+  dot_partial_kernel<<<nb, RED_THREADS, 0, s>>>(x, y, n, (double *)work, nullptr);
+  sum_partials_kernel<<<1, RED_THREADS, 0, s>>>((const double *)work, nb, out);
+  CEED_CUDA_CHECK(cudaGetLastError());
+  return CEED_OK;
+}
+
+static void fill_defaults(const ceed_cg_opts *in, ceed_cg_opts *o) {
+  *o = *in;
+  if (o->max_iter <= 0) o->max_iter = 10000;
+  if (o->max_outer <= 0) o->max_outer = 50;
+  if (o->check_every <= 0) o->check_every = 10;
+  if (o->tol <= 0) o->tol = 1e-10;
+  if (o->inner_tol <= 0) o->inner_tol = 1e-4;
+}
+
+extern "C" size_t ceed_cg_workspace_bytes(ceed_mesh_t m, const ceed_cg_opts *opts) {
+  if (!m || !opts) return 0;
+  return layout(m->n_ldof, opts->mode == CEED_CG_MIXED, nullptr, nullptr);
+}
+
+extern "C" int ceed_cg_solve(ceed_mesh_t m, const void *qdata, int prec, const double *b, double *x,
+                             const ceed_cg_opts *opts_in, ceed_cg_report *report, void *work, size_t work_bytes,
+                             void *stream) {
+  if (int st = check_mesh(m)) return st;
+  if (!qdata || !b || !x || !opts_in || !report || !work) return fail(CEED_ERR_INVALID, "null argument");
+  if (m->ncomp != 1) return fail(CEED_ERR_UNSUPPORTED, "CG needs ncomp = 1");
+  if (!m->has_dirichlet) return fail(CEED_ERR_INVALID, "CG needs a Dirichlet mask on the mesh");
+  if (prec != CEED_F64) return fail(CEED_ERR_INVALID, "the CG operator (outer operator in MIXED mode) must be FP64");
+  if (((uintptr_t)work & 255) != 0) return fail(CEED_ERR_INVALID, "workspace must be 256-byte aligned");
+  ceed_cg_opts o;
+  fill_defaults(opts_in, &o);
+  const bool mixed = o.mode == CEED_CG_MIXED;
+  if (mixed && (!o.qdata_lo || (o.prec_lo != CEED_F32 && o.prec_lo != CEED_BF16 && o.prec_lo != CEED_F16)))
+    return fail(CEED_ERR_INVALID, "MIXED mode needs qdata_lo in F32, BF16 or F16");
+  if (o.op != CEED_OP_MASS && o.op != CEED_OP_DIFFUSION) return fail(CEED_ERR_INVALID, "unknown operator");
+  const int64_t n = m->n_ldof;
+  if (work_bytes < layout(n, mixed, nullptr, nullptr)) return fail(CEED_ERR_INVALID, "workspace too small");
+  Work w;
+  layout(n, mixed, (char *)work, &w);
+  cudaStream_t s = (cudaStream_t)stream;
+  std::memset(report, 0, sizeof(*report));
+
+  cudaEvent_t ev0, ev1;
+  CEED_CUDA_CHECK(cudaEventCreate(&ev0));
+  CEED_CUDA_CHECK(cudaEventCreate(&ev1));
+  CEED_CUDA_CHECK(cudaEventRecord(ev0, s));
+
+  ApplyReq op64{};
+  op64.op = o.op;
+  op64.prec = CEED_F64;
+  op64.qdata = qdata;
+  op64.ncol = 1;
+  op64.masked = 1;
+  // Jacobi preconditioner from the FP64 operator
+  if (int st = ceed_jacobi_diagonal(m, o.op, qdata, CEED_F64, w.dinv, CEED_APPLY_DIRICHLET, stream)) return st;
+  invert_kernel<<<stream_blocks(n), 256, 0, s>>>(w.dinv, n);
+  CEED_CUDA_CHECK(cudaGetLastError());
+
+  // ||b||^2
+  double bb = 0.0;
+  {
+    const int nb = red_blocks(n);
+    dot_partial_kernel<<<nb, RED_THREADS, 0, s>>>(b, b, n, w.part1, nullptr);
+    sum_partials_kernel<<<1, RED_THREADS, 0, s>>>(w.part1, nb, &w.sc->bb_out);
+    CEED_CUDA_CHECK(cudaMemcpyAsync(&bb, &w.sc->bb_out, sizeof(double), cudaMemcpyDeviceToHost, s));
+    CEED_CUDA_CHECK(cudaStreamSynchronize(s));
+  }
+  if (bb == 0.0) {
+    zero_kernel<<<stream_blocks(n), 256, 0, s>>>(x, n);
+    CEED_CUDA_CHECK(cudaStreamSynchronize(s));
+    return CEED_OK;
+  }
+  int status = CEED_OK;
+  double rr = 0.0;
+  if (!mixed) {
+    // r = b - A x0 (or b), then PCG for the correction y, x = x0 + y
+    if (o.use_x0) {
+      if (int st = residual(m, op64, b, x, w.q, w.r, n, w.part1, &w.sc->rr_out, s, &rr)) return st;
+    } else {
+      copy_kernel<<<stream_blocks(n), 256, 0, s>>>(w.r, b, n);
+      rr = bb;
+    }
+    // PCG on A y = r with the tolerance expressed against ||b||: scale tol by ||b|| / ||r0||
+    const double tol_r = o.tol * std::sqrt(bb / (rr > 0 ? rr : bb));
+    double *y = x;
+    // solve for the correction in x's storage when x0 = 0, else in a scratch vector then add
+    if (o.use_x0) {
+      // reuse q as scratch for the correction is not possible (q is the apply output); accumulate
+      // into x afterwards through w.z after the run would clobber z, so run directly on a copy
+      return fail(CEED_ERR_UNSUPPORTED, "use_x0 is supported in MIXED mode only");
+    }
+    int iters = 0, nonfin = 0;
+    if (int st = pcg_run(m, op64, y, w, n, tol_r, o.max_iter, o.check_every, o.fixed_iters, s, &iters, &nonfin))
+      return st;
+    report->iterations = iters;
+    report->outer_iterations = 1;
+    if (nonfin) status = fail(CEED_ERR_NONFINITE, "non-finite value in a CG reduction");
+    if (int st = residual(m, op64, b, x, w.q, w.r, n, w.part1, &w.sc->rr_out, s, &rr)) return st;
+    report->rel_residual = std::sqrt(rr / bb);
+    if (status == CEED_OK && o.fixed_iters <= 0 && report->rel_residual > o.tol)
+      status = fail(CEED_ERR_NOT_CONVERGED, "CG reached its iteration cap");
+  } else {
+    ApplyReq oplo = op64;
+    oplo.prec = o.prec_lo;
+    oplo.qdata = o.qdata_lo;
+    if (!o.use_x0) zero_kernel<<<stream_blocks(n), 256, 0, s>>>(x, n);
+    int total = 0, outer = 0;
+    while (true) {
+      if (int st = residual(m, op64, b, x, w.q, w.r_out, n, w.part1, &w.sc->rr_out, s, &rr)) return st;
+      report->rel_residual = std::sqrt(rr / bb);
+      if (!std::isfinite(rr)) {
+        status = fail(CEED_ERR_NONFINITE, "non-finite outer residual");
+        break;
+      }
+      if (report->rel_residual <= o.tol) break;
+      if (outer >= o.max_outer || total >= o.max_iter) {
+        status = fail(CEED_ERR_NOT_CONVERGED, "mixed-precision refinement reached its cap");
+        break;
+      }
+      copy_kernel<<<stream_blocks(n), 256, 0, s>>>(w.r, w.r_out, n);
+      int iters = 0, nonfin = 0;
+      if (int st = pcg_run(m, oplo, w.d, w, n, o.inner_tol, o.max_iter - total, o.check_every, 0, s, &iters, &nonfin))
+        return st;
+      total += iters;
+      outer += 1;
+      if (nonfin) {
+        status = fail(CEED_ERR_NONFINITE, "non-finite value in an inner CG reduction");
+        break;
+      }
+      axpy_kernel<<<stream_blocks(n), 256, 0, s>>>(x, w.d, n);
+    }
+    report->iterations = total;
+    report->outer_iterations = outer;
+  }
+  CEED_CUDA_CHECK(cudaEventRecord(ev1, s));
+  CEED_CUDA_CHECK(cudaEventSynchronize(ev1));
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, ev0, ev1);
+  report->seconds = ms * 1e-3;
+  cudaEventDestroy(ev0);
+  cudaEventDestroy(ev1);
+  return status;
+}

@@ -1,0 +1,406 @@
+// Mesh handle: 1D bases, element colouring, colour-sorted restriction; apply entry points.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <memory>
+#include <new>
+
+#include "internal.h"
+
+namespace ceedgb {
+
+static thread_local std::string g_last_error;
+
+int fail(int status, const std::string &msg) {
+  g_last_error = msg;
+  return status;
+}
+
+int cuda_fail(cudaError_t e, const char *where) {
+  g_last_error = std::string(where) + ": " + cudaGetErrorString(e);
+  return e == cudaErrorMemoryAllocation ? CEED_ERR_OOM : CEED_ERR_CUDA;
+}
+
+int check_mesh(ceed_mesh_t m) {
+  if (!m) return fail(CEED_ERR_INVALID, "null mesh handle");
+  return CEED_OK;
+}
+
+int nq_of(const ceed_mesh_t m) { return m->Q * m->Q * m->Q; }
+
+// ---------------------------------------------------------------------------------------------
+// 1D rules.  Legendre P_n and derivatives by the three-term recurrence; Newton iteration for
+// the roots.  Gauss: roots of P_n, w = 2 / ((1 - x^2) P_n'^2).  Gauss-Lobatto: +-1 and the roots
+// of P_{n-1}', w = 2 / (n (n - 1) P_{n-1}^2).
+static void legendre_eval(int n, double x, double *p, double *dp, double *d2p) {
+  double p0 = 1, p1 = x, d0 = 0, d1 = 1, s0 = 0, s1 = 0;
+  if (n == 0) {
+    *p = 1; *dp = 0; *d2p = 0;
+    return;
+  }
+  for (int k = 1; k < n; ++k) {
+    const double a = (2.0 * k + 1.0) / (k + 1.0), b = (double)k / (k + 1.0);
+    const double p2 = a * x * p1 - b * p0;
+    const double d2 = a * (p1 + x * d1) - b * d0;
+    const double s2 = a * (2.0 * d1 + x * s1) - b * s0;
+    p0 = p1; p1 = p2; d0 = d1; d1 = d2; s0 = s1; s1 = s2;
+  }
+  *p = p1; *dp = d1; *d2p = s1;
+}
+
+void gauss_rule(int n, double *x, double *w) {
+  const double pi = 3.14159265358979323846;
+  for (int i = 0; i < n; ++i) {
+    double t = -std::cos(pi * (i + 0.75) / (n + 0.5));
+    for (int it = 0; it < 100; ++it) {
+      double p, dp, d2p;
+      legendre_eval(n, t, &p, &dp, &d2p);
+      const double dt = p / dp;
+      t -= dt;
+      if (std::fabs(dt) < 1e-16) break;
+    }
+    double p, dp, d2p;
+    legendre_eval(n, t, &p, &dp, &d2p);
+    x[i] = t;
+    w[i] = 2.0 / ((1.0 - t * t) * dp * dp);
+  }
+}
+
+void gll_rule(int n, double *x, double *w) {
+  const double pi = 3.14159265358979323846;
+  const int m = n - 1;
+  for (int i = 0; i < n; ++i) {
+    double t = -std::cos(pi * i / m);
+    if (i > 0 && i < m) {
+      for (int it = 0; it < 100; ++it) {
+        double p, dp, d2p;
+        legendre_eval(m, t, &p, &dp, &d2p);
+        const double dt = dp / d2p;
+        t -= dt;
+        if (std::fabs(dt) < 1e-16) break;
+      }
+    }
+    if (i == 0) t = -1.0;
+    if (i == m) t = 1.0;
+    double p, dp, d2p;
+    legendre_eval(m, t, &p, &dp, &d2p);
+    x[i] = t;
+    w[i] = 2.0 / (n * m * p * p);
+  }
+}
+
+// Barycentric weights lambda_j = 1 / prod_{m != j} (x_j - x_m).
+static void bary_weights(int n, const double *x, double *lam) {
+  for (int j = 0; j < n; ++j) {
+    double d = 1.0;
+    for (int m = 0; m < n; ++m)
+      if (m != j) d *= (x[j] - x[m]);
+    lam[j] = 1.0 / d;
+  }
+}
+
+// Interpolation matrix B[q * n + a] = l_a(t_q) for the Lagrange basis through nodes x (barycentric form).
+static void interp_matrix(int n, const double *x, int nq, const double *t, double *B) {
+  double lam[MAX_Q];
+  bary_weights(n, x, lam);
+  for (int q = 0; q < nq; ++q) {
+    int hit = -1;
+    for (int a = 0; a < n; ++a)
+      if (t[q] == x[a]) hit = a;
+    if (hit >= 0) {
+      for (int a = 0; a < n; ++a) B[q * n + a] = (a == hit) ? 1.0 : 0.0;
+      continue;
+    }
+    double den = 0.0;
+    for (int a = 0; a < n; ++a) den += lam[a] / (t[q] - x[a]);
+    for (int a = 0; a < n; ++a) B[q * n + a] = (lam[a] / (t[q] - x[a])) / den;
+  }
+}
+
+// Collocation derivative D[i * n + j] = l_j'(x_i) for the Lagrange basis through x (barycentric
+// off-diagonal entries; the diagonal makes every row sum to zero).
+static void deriv_matrix(int n, const double *x, double *D) {
+  double lam[MAX_Q];
+  bary_weights(n, x, lam);
+  for (int i = 0; i < n; ++i) {
+    double s = 0.0;
+    for (int j = 0; j < n; ++j) {
+      if (j == i) continue;
+      const double v = (lam[j] / lam[i]) / (x[i] - x[j]);
+      D[i * n + j] = v;
+      s += v;
+    }
+    D[i * n + i] = -s;
+  }
+}
+
+static void build_tables(ceed_mesh_s *m) {
+  double w_gll[MAX_P];
+  gll_rule(m->P, m->gll_x, w_gll);
+  if (m->q_rule == CEED_QRULE_GLL) {
+    for (int i = 0; i < m->Q; ++i) {
+      m->rule.x[i] = m->gll_x[i];
+      m->rule.w[i] = w_gll[i];
+    }
+  } else {
+    gauss_rule(m->Q, m->rule.x, m->rule.w);
+  }
+  double B[MAX_Q * MAX_P], D[MAX_Q * MAX_Q];
+  interp_matrix(m->P, m->gll_x, m->Q, m->rule.x, B);
+  deriv_matrix(m->Q, m->rule.x, D);
+  std::memset(&m->tab64, 0, sizeof(m->tab64));
+  std::memset(&m->tab32, 0, sizeof(m->tab32));
+  for (int k = 0; k < m->Q * m->P; ++k) {
+    m->tab64.B[k] = B[k];
+    m->tab32.B[k] = (float)B[k];
+  }
+  for (int k = 0; k < m->Q * m->Q; ++k) {
+    m->tab64.D[k] = D[k];
+    m->tab32.D[k] = (float)D[k];
+  }
+}
+
+int launch_apply(ceed_mesh_t m, const ApplyReq &r, cudaStream_t s);
+int launch_apply_qf32(ceed_mesh_t m, const ApplyReq &r, cudaStream_t s);
+int launch_apply_qbf16(ceed_mesh_t m, const ApplyReq &r, cudaStream_t s);
+int launch_apply_qf16(ceed_mesh_t m, const ApplyReq &r, cudaStream_t s);
+
+int launch_apply_f32(ceed_mesh_t m, const ApplyReq &r, cudaStream_t s) {
+  switch (r.prec) {
+    case CEED_F32: return launch_apply_qf32(m, r, s);
+    case CEED_BF16: return launch_apply_qbf16(m, r, s);
+    case CEED_F16: return launch_apply_qf16(m, r, s);
+    default: return fail(CEED_ERR_INVALID, "unknown precision");
+  }
+}
+
+int launch_apply(ceed_mesh_t m, const ApplyReq &r, cudaStream_t s) {
+  if (r.prec == CEED_F64) return launch_apply_f64(m, r, s);
+  return launch_apply_f32(m, r, s);
+}
+
+}  // namespace ceedgb
+
+using namespace ceedgb;
+
+extern "C" const char *ceed_last_error(void) { return g_last_error.c_str(); }
+
+namespace {
+struct HostFree {
+  void operator()(ceed_mesh_s *m) const {
+    if (!m) return;
+    cudaFree(m->d_emap);
+    cudaFree(m->d_perm);
+    cudaFree(m->d_vertices);
+    cudaFree(m->d_err);
+    delete m;
+  }
+};
+}  // namespace
+
+extern "C" int ceed_setup_mesh(const ceed_mesh_desc *desc, ceed_mesh_t *out, void *stream) {
+  if (!desc || !out) return fail(CEED_ERR_INVALID, "null descriptor or output");
+  *out = nullptr;
+  if (desc->n_elem < 1 || desc->n_ldof < 1) return fail(CEED_ERR_INVALID, "n_elem and n_ldof must be >= 1");
+  if (desc->n_ldof > (int64_t)DOF_MASK) return fail(CEED_ERR_INVALID, "n_ldof must be < 2^30");
+  if (desc->p < 1 || desc->p > 8) return fail(CEED_ERR_INVALID, "p must be in 1..8");
+  if (desc->ncomp < 1) return fail(CEED_ERR_INVALID, "ncomp must be >= 1");
+  if (!desc->elem_dofs || !desc->vertices) return fail(CEED_ERR_INVALID, "elem_dofs and vertices are required");
+  const int P = desc->p + 1;
+  int Q = desc->n_qpts_1d;
+  if (desc->q_rule == CEED_QRULE_GLL) {
+    if (Q == 0) Q = P;
+    if (Q != P) return fail(CEED_ERR_UNSUPPORTED, "GLL quadrature is collocated: Q must be p+1");
+  } else if (desc->q_rule == CEED_QRULE_GAUSS) {
+    if (Q == 0) Q = P + 1;
+    if (Q != P + 1) return fail(CEED_ERR_UNSUPPORTED, "Gauss quadrature supports Q = p+2");
+  } else {
+    return fail(CEED_ERR_INVALID, "unknown quadrature rule");
+  }
+  const int64_t E = desc->n_elem, nd = (int64_t)P * P * P, nL = desc->n_ldof;
+  if (E * nd >= ((int64_t)1 << 40)) return fail(CEED_ERR_INVALID, "mesh too large");
+  cudaStream_t s = (cudaStream_t)stream;
+
+  std::unique_ptr<ceed_mesh_s, HostFree> m(new (std::nothrow) ceed_mesh_s());
+  if (!m) return fail(CEED_ERR_OOM, "host allocation");
+  CEED_CUDA_CHECK(cudaGetDevice(&m->device));
+  m->E = E;
+  m->n_ldof = nL;
+  m->p = desc->p;
+  m->P = P;
+  m->Q = Q;
+  m->q_rule = desc->q_rule;
+  m->ncomp = desc->ncomp;
+  build_tables(m.get());
+
+  // ---- copy the caller's arrays to the host
+  std::vector<uint32_t> map;
+  std::vector<double> vert;
+  std::vector<uint8_t> dir;
+  try {
+    map.resize(E * nd);
+    vert.resize(E * 24);
+    if (desc->dirichlet) dir.resize(nL);
+  } catch (...) {
+    return fail(CEED_ERR_OOM, "host allocation for the mesh copy");
+  }
+  CEED_CUDA_CHECK(cudaMemcpyAsync(map.data(), desc->elem_dofs, E * nd * 4, cudaMemcpyDeviceToHost, s));
+  CEED_CUDA_CHECK(cudaMemcpyAsync(vert.data(), desc->vertices, E * 24 * 8, cudaMemcpyDeviceToHost, s));
+  if (desc->dirichlet) CEED_CUDA_CHECK(cudaMemcpyAsync(dir.data(), desc->dirichlet, nL, cudaMemcpyDeviceToHost, s));
+  CEED_CUDA_CHECK(cudaStreamSynchronize(s));
+  m->has_dirichlet = desc->dirichlet != nullptr;
+
+  // ---- validate: in range, no repeated node inside an element, every node referenced
+  std::vector<int64_t> stamp;
+  try {
+    stamp.assign(nL, -1);
+  } catch (...) {
+    return fail(CEED_ERR_OOM, "host allocation");
+  }
+  for (int64_t e = 0; e < E; ++e) {
+    const uint32_t *row = &map[e * nd];
+    for (int64_t n = 0; n < nd; ++n) {
+      const int64_t v = (int32_t)row[n];
+      if (v < 0 || v >= nL) return fail(CEED_ERR_INVALID, "elem_dofs entry out of range at element " + std::to_string(e));
+      if (stamp[v] == e) return fail(CEED_ERR_INVALID, "node repeated inside element " + std::to_string(e));
+      stamp[v] = e;
+    }
+  }
+  for (int64_t v = 0; v < nL; ++v)
+    if (stamp[v] < 0) return fail(CEED_ERR_INVALID, "node " + std::to_string(v) + " belongs to no element");
+  std::vector<int64_t>().swap(stamp);
+
+  // ---- greedy colouring: no two elements of one colour share a node
+  std::vector<uint8_t> color(E);
+  {
+    std::vector<uint64_t> used;
+    try {
+      used.assign(nL, 0);
+    } catch (...) {
+      return fail(CEED_ERR_OOM, "host allocation");
+    }
+    int ncol = 0;
+    for (int64_t e = 0; e < E; ++e) {
+      const uint32_t *row = &map[e * nd];
+      uint64_t forb = 0;
+      for (int64_t n = 0; n < nd; ++n) forb |= used[row[n]];
+      if (forb == ~0ull) return fail(CEED_ERR_UNSUPPORTED, "element colouring needs more than 64 colours");
+      const int c = __builtin_ctzll(~forb);
+      color[e] = (uint8_t)c;
+      ncol = std::max(ncol, c + 1);
+      const uint64_t bit = 1ull << c;
+      for (int64_t n = 0; n < nd; ++n) used[row[n]] |= bit;
+    }
+    m->n_colors = ncol;
+  }
+  // stable counting sort by colour
+  std::vector<int64_t> start(m->n_colors + 1, 0);
+  for (int64_t e = 0; e < E; ++e) start[color[e] + 1]++;
+  for (int c = 0; c < m->n_colors; ++c) start[c + 1] += start[c];
+  m->color_start = start;
+  std::vector<int32_t> perm(E);
+  {
+    std::vector<int64_t> pos(start.begin(), start.end() - 1);
+    for (int64_t e = 0; e < E; ++e) perm[pos[color[e]]++] = (int32_t)e;
+  }
+  // colour-sorted restriction with first-writer and Dirichlet flags; sorted vertices
+  std::vector<uint32_t> emap;
+  std::vector<double> svert;
+  std::vector<uint8_t> seen;
+  try {
+    emap.resize(E * nd);
+    svert.resize(E * 24);
+    seen.assign(nL, 0);
+  } catch (...) {
+    return fail(CEED_ERR_OOM, "host allocation");
+  }
+  for (int64_t sidx = 0; sidx < E; ++sidx) {
+    const int64_t e = perm[sidx];
+    const uint32_t *row = &map[e * nd];
+    uint32_t *dst = &emap[sidx * nd];
+    for (int64_t n = 0; n < nd; ++n) {
+      const uint32_t v = row[n];
+      uint32_t f = v;
+      if (!seen[v]) {
+        f |= FLAG_FIRST;
+        seen[v] = 1;
+      }
+      if (!dir.empty() && dir[v]) f |= FLAG_DIR;
+      dst[n] = f;
+    }
+    std::memcpy(&svert[sidx * 24], &vert[e * 24], 24 * sizeof(double));
+  }
+
+  CEED_CUDA_CHECK(cudaMalloc(&m->d_emap, E * nd * 4));
+  CEED_CUDA_CHECK(cudaMalloc(&m->d_perm, E * 4));
+  CEED_CUDA_CHECK(cudaMalloc(&m->d_vertices, E * 24 * 8));
+  CEED_CUDA_CHECK(cudaMalloc(&m->d_err, sizeof(int) * 4));
+  CEED_CUDA_CHECK(cudaMemcpyAsync(m->d_emap, emap.data(), E * nd * 4, cudaMemcpyHostToDevice, s));
+  CEED_CUDA_CHECK(cudaMemcpyAsync(m->d_perm, perm.data(), E * 4, cudaMemcpyHostToDevice, s));
+  CEED_CUDA_CHECK(cudaMemcpyAsync(m->d_vertices, svert.data(), E * 24 * 8, cudaMemcpyHostToDevice, s));
+  CEED_CUDA_CHECK(cudaMemsetAsync(m->d_err, 0, sizeof(int) * 4, s));
+  CEED_CUDA_CHECK(cudaStreamSynchronize(s));
+  *out = m.release();
+  return CEED_OK;
+}
+
+extern "C" int ceed_destroy_mesh(ceed_mesh_t m) {
+  if (!m) return CEED_OK;
+  cudaDeviceSynchronize();
+  HostFree()(m);
+  return CEED_OK;
+}
+
+extern "C" int ceed_mesh_info(ceed_mesh_t m, int32_t *n_colors, int32_t *Q, int32_t *P) {
+  if (int st = check_mesh(m)) return st;
+  if (n_colors) *n_colors = m->n_colors;
+  if (Q) *Q = m->Q;
+  if (P) *P = m->P;
+  return CEED_OK;
+}
+
+static size_t prec_size(int prec) {
+  switch (prec) {
+    case CEED_F64: return 8;
+    case CEED_F32: return 4;
+    case CEED_BF16:
+    case CEED_F16: return 2;
+    default: return 0;
+  }
+}
+
+extern "C" size_t ceed_qdata_bytes(ceed_mesh_t m, int op, int prec) {
+  if (!m || prec_size(prec) == 0 || (op != CEED_OP_MASS && op != CEED_OP_DIFFUSION)) return 0;
+  return (size_t)m->E * (op == CEED_OP_DIFFUSION ? 6 : 1) * nq_of(m) * prec_size(prec);
+}
+
+static int apply_common(ceed_mesh_t m, int op, const void *qdata, int prec, const double *x, double *y, int nrhs,
+                        unsigned flags, void *stream) {
+  if (int st = check_mesh(m)) return st;
+  if (!qdata || !x || !y) return fail(CEED_ERR_INVALID, "null qdata, x or y");
+  if (x == y) return fail(CEED_ERR_INVALID, "x and y must not alias");
+  if (nrhs < 1) return fail(CEED_ERR_INVALID, "nrhs must be >= 1");
+  if (prec_size(prec) == 0) return fail(CEED_ERR_INVALID, "unknown precision");
+  if (prec != CEED_F64 && prec != CEED_F32 && prec != CEED_BF16 && prec != CEED_F16)
+    return fail(CEED_ERR_INVALID, "unknown precision");
+  ApplyReq r;
+  r.op = op;
+  r.prec = prec;
+  r.qdata = qdata;
+  r.x = x;
+  r.y = y;
+  r.ncol = m->ncomp * nrhs;
+  r.masked = (flags & CEED_APPLY_DIRICHLET) ? 1 : 0;
+  if (r.masked && !m->has_dirichlet) return fail(CEED_ERR_INVALID, "mesh has no Dirichlet mask");
+  return launch_apply(m, r, (cudaStream_t)stream);
+}
+
+extern "C" int ceed_apply_mass(ceed_mesh_t m, const void *qdata, int prec, const double *x, double *y, int nrhs,
+                               unsigned flags, void *stream) {
+  return apply_common(m, CEED_OP_MASS, qdata, prec, x, y, nrhs, flags, stream);
+}
+
+extern "C" int ceed_apply_diffusion(ceed_mesh_t m, const void *qdata, int prec, const double *x, double *y, int nrhs,
+                                    unsigned flags, void *stream) {
+  return apply_common(m, CEED_OP_DIFFUSION, qdata, prec, x, y, nrhs, flags, stream);
+}

@@ -1,0 +1,140 @@
+"""GPU parity of the PCG driver, mixed-precision refinement and the adjoint against the CPU oracle."""
+import numpy as np
+import pytest
+import scipy.sparse as sps
+import scipy.sparse.linalg as spla
+
+import synthetic
+from oracle import fem
+from _util import gpu_mesh, rel_err
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ceed():
+    import paper_2109_05072_gb300 as c
+    assert torch.cuda.is_available()
+    return c
+
+
+def _setup(ceed, N, p, seed=0):
+    m = synthetic.cube_mesh(N, p, seed=seed)
+    mesh = gpu_mesh(ceed, m, "gll")
+    qd = ceed.alloc_qdata(mesh, ceed.CEED_OP_DIFFUSION, ceed.CEED_F64)
+    ceed.ceed_build_qdata(mesh, ceed.CEED_OP_DIFFUSION, ceed.CEED_COEFF_SINE, None, ceed.CEED_F64, qd)
+    b = torch.empty(m.n_ldof, dtype=torch.float64, device="cuda")
+    ceed.ceed_manufactured_rhs(mesh, ceed.CEED_COEFF_SINE, b, flags=ceed.CEED_APPLY_DIRICHLET)
+    return m, mesh, qd, b
+
+
+def _oracle_solution(m, p):
+    sp_ = fem.Space(p, "gll")
+    G = fem.qdata_diffusion(sp_, m.vertices, "sine")
+    A = fem.assemble(sp_, m.elem_dofs, G, fem.DIFFUSION, m.n_ldof).tolil()
+    mask = m.boundary.astype(bool)
+    A[mask, :] = 0
+    A[:, mask] = 0
+    A = A.tocsr() + sps.diags(mask.astype(float))
+    b = fem.manufactured_rhs(sp_, m.vertices, m.elem_dofs, m.n_ldof, "sine", mask=mask)
+    return A, b, spla.spsolve(A.tocsc(), b)
+
+
+@pytest.mark.parametrize("N,p", [(3, 3), (4, 2), (2, 7)])
+def test_cg_fp64_matches_direct_solve(ceed, N, p):
+    m, mesh, qd, b = _setup(ceed, N, p)
+    A, bref, xref = _oracle_solution(m, p)
+    assert rel_err(b.cpu().numpy(), bref) <= 1e-12
+    x = torch.empty_like(b)
+    st, rep = ceed.ceed_cg_solve(mesh, qd, ceed.CEED_F64, b, x, mode=ceed.CEED_CG_FP64, tol=1e-10,
+                                 op=ceed.CEED_OP_DIFFUSION, max_iter=5000)
+    assert rep["rel_residual"] <= 1e-10
+    xh = x.cpu().numpy()
+    assert np.linalg.norm(bref - A @ xh) <= 1.5e-10 * np.linalg.norm(bref)
+    assert rel_err(xh, xref) <= 1e-8
+    # the oracle's own PCG on the same system takes a comparable number of iterations
+    d = fem.jacobi_diagonal(fem.Space(p, "gll"), m.elem_dofs, fem.qdata_diffusion(fem.Space(p, "gll"), m.vertices, "sine"),
+                            fem.DIFFUSION, m.n_ldof, mask=m.boundary)
+    _, it_ref, _, _ = fem.pcg(lambda v: A @ v, bref, 1.0 / d, tol=1e-10, maxit=5000)
+    assert abs(rep["iterations"] - it_ref) <= max(3, 0.05 * it_ref)
+    mesh.close()
+
+
+@pytest.mark.parametrize("prec_lo", [1, 2, 3])
+def test_mixed_refinement_reaches_fp64_tolerance(ceed, prec_lo):
+    N, p = 3, 5
+    m, mesh, qd, b = _setup(ceed, N, p)
+    A, bref, xref = _oracle_solution(m, p)
+    qlo = ceed.alloc_qdata(mesh, ceed.CEED_OP_DIFFUSION, prec_lo)
+    ceed.ceed_build_qdata(mesh, ceed.CEED_OP_DIFFUSION, ceed.CEED_COEFF_SINE, None, prec_lo, qlo)
+    x = torch.empty_like(b)
+    st, rep = ceed.ceed_cg_solve(mesh, qd, ceed.CEED_F64, b, x, mode=ceed.CEED_CG_MIXED, tol=1e-10,
+                                 op=ceed.CEED_OP_DIFFUSION, qdata_lo=qlo, prec_lo=prec_lo, inner_tol=1e-3)
+    assert rep["rel_residual"] <= 1e-10 and rep["outer_iterations"] >= 2
+    xh = x.cpu().numpy()
+    assert np.linalg.norm(bref - A @ xh) <= 1.5e-10 * np.linalg.norm(bref)
+    print(f"mixed prec {prec_lo}: outer {rep['outer_iterations']} inner {rep['iterations']}")
+    mesh.close()
+
+
+def test_cg_fixed_iterations_and_cap(ceed):
+    m, mesh, qd, b = _setup(ceed, 3, 4)
+    x = torch.empty_like(b)
+    st, rep = ceed.ceed_cg_solve(mesh, qd, ceed.CEED_F64, b, x, mode=ceed.CEED_CG_FP64, fixed_iters=7,
+                                 op=ceed.CEED_OP_DIFFUSION)
+    assert rep["iterations"] == 7
+    st, rep = ceed.ceed_cg_solve(mesh, qd, ceed.CEED_F64, b, x, mode=ceed.CEED_CG_FP64, tol=1e-14, max_iter=5,
+                                 op=ceed.CEED_OP_DIFFUSION, raise_on_error=False)
+    assert st == ceed.CEED_ERR_NOT_CONVERGED and rep["iterations"] == 5
+    mesh.close()
+
+
+def test_dot_deterministic(ceed):
+    n = 1_000_003
+    x = torch.from_numpy(synthetic.uniform(n, seed=1)).cuda()
+    y = torch.from_numpy(synthetic.uniform(n, seed=2)).cuda()
+    work = torch.empty(ceed.ceed_dot_workspace_bytes(n), dtype=torch.uint8, device="cuda")
+    out = torch.empty(1, dtype=torch.float64, device="cuda")
+    vals = []
+    for _ in range(3):
+        ceed.ceed_dot(x, y, out, work)
+        vals.append(out.item())
+    assert vals[0] == vals[1] == vals[2]
+    ref = float(np.dot(x.cpu().numpy(), y.cpu().numpy()))
+    assert abs(vals[0] - ref) <= 1e-12 * np.sqrt(n)
+
+
+@pytest.mark.parametrize("p,stored", [(4, True), (4, False), (8, True), (2, False)])
+def test_adjoint_matches_oracle(ceed, p, stored):
+    m = synthetic.HexMesh(3, 2, 2, p, seed=11)
+    sp_ = fem.Space(p, "gll")
+    mesh = gpu_mesh(ceed, m, "gll")
+    k = synthetic.lognormal(m.n_elem * sp_.nq, seed=1, sigma=0.5).reshape(m.n_elem, sp_.nq)
+    x = synthetic.uniform(m.n_ldof, seed=2)
+    b = synthetic.uniform(m.n_ldof, seed=3)
+    geo = None
+    if stored:
+        geo = ceed.alloc_qdata(mesh, ceed.CEED_OP_DIFFUSION, ceed.CEED_F64)
+        ceed.ceed_build_geometry(mesh, geo)
+    kd = torch.from_numpy(k).cuda()
+    xd = torch.from_numpy(x).cuda().requires_grad_(True)
+    kd.requires_grad_(True)
+    y = ceed.diffusion_k(xd, kd, mesh, geo)
+    bd = torch.from_numpy(b).cuda()
+    L = 0.5 * ((y - bd) ** 2).sum()
+    L.backward()
+    Lref, gx, gk = fem.adjoint(sp_, m.vertices, m.elem_dofs, k, x, b)
+    assert abs(L.item() - Lref) <= 1e-12 * abs(Lref)
+    assert rel_err(xd.grad.cpu().numpy(), gx) <= 1e-12
+    assert rel_err(kd.grad.cpu().numpy(), gk) <= 1e-12
+    # directional central difference in k on the GPU path itself (h = 1e-6 relative)
+    v = torch.from_numpy(synthetic.uniform(k.size, seed=4).reshape(k.shape)).cuda()
+    h = 1e-6 * kd.detach().abs().max() / v.abs().max()
+    with torch.no_grad():
+        Lp = 0.5 * ((ceed.diffusion_k(xd.detach(), kd.detach() + h * v, mesh, geo) - bd) ** 2).sum()
+        Lm = 0.5 * ((ceed.diffusion_k(xd.detach(), kd.detach() - h * v, mesh, geo) - bd) ** 2).sum()
+    fd = ((Lp - Lm) / (2 * h)).item()
+    an = (kd.grad * v).sum().item()
+    assert abs(fd - an) <= 1e-6 * abs(an)
+    mesh.close()
