@@ -2,15 +2,27 @@
 // quadrature points, pointwise quadrature operator, transposed contractions, scatter-add (E->L).
 //
 // Paper Section 2: w_L = A_L u_L with A_L = block-diag(A^e), A^e = D^T G^e D; the 3D derivative
-// is applied as 1D contractions u_r(r_i, s_j, t_k) = sum_m Dhat_im u_mjk (and likewise along s, t),
-// and G^e is six diagonal matrices G_rr ... G_tt.  Section 3 (cuda-gen): the whole operator in one
+// is applied as 1D contractions u_r(r_i, s_j, t_k) = sum_m Dhat_im u_mjk (likewise along s, t) and
+// G^e is six diagonal matrices G_rr ... G_tt.  Section 3 (cuda-gen): the whole operator in one
 // kernel with no global temporaries.  Section 1: sum factorization, O(p^{d+1}) work per element.
 //
-// Thread layout: Q x Q threads per element, thread (i, j) owns the column of points (i, j, 0..Q-1)
-// in registers; planes are exchanged through shared memory for the r and s passes, the t pass
-// stays in registers.  NE elements per thread block.  Elements of one colour share no node, so
-// the scatter is a plain (non-atomic) store for the first writer of a node and a load-add-store
-// for later colours: deterministic and atomic-free.
+// GB300 design (one thread block handles NE elements, Q x Q threads per element):
+//  * the element's quadrature data block is staged into shared memory by one TMA bulk copy
+//    (cp.async.bulk + mbarrier) issued at kernel entry, so it streams in while the gather and the
+//    forward contractions run; for several columns (components x right-hand sides) it is read once;
+//  * every global load of an element (restriction, x, and the old y of nodes already written by an
+//    earlier colour) is issued up front, so an element pays one memory latency, not four;
+//  * each 1D pass is done by "line owners": a thread holds a whole line of the tile in registers and
+//    applies the 1D operator with the even-odd (centro-symmetry) decomposition, which replaces an
+//    n x n product by two (n/2) x (n/2) products plus n folds/unfolds (48 instead of 64 operations
+//    for n = 8) -- on GB300 the FP64 pipe is the limit of the FP64 operator, so this is the lever;
+//  * tiles are stored with row pitch Q+1 so the three access patterns (r-lines, s-lines, t-columns)
+//    are free of shared-memory bank conflicts for 4- and 8-byte words;
+//  * the FP32 operator converts FP64 L-vector values to FP32 and back with integer instructions and
+//    accumulates across colours in FP32, so it issues no FP64-pipe instruction at all;
+//  * elements of one colour share no node: the scatter is a plain store for the first writer of a
+//    node and a load-add-store for later colours (old value loaded up front): deterministic and
+//    atomic-free.
 #pragma once
 
 #include <cuda_bf16.h>
@@ -20,251 +32,417 @@
 
 namespace ceedgb {
 
-__device__ __forceinline__ double ld_q(const double *p) { return __ldg(p); }
-__device__ __forceinline__ float ld_q(const float *p) { return __ldg(p); }
-__device__ __forceinline__ float ld_q(const __nv_bfloat16 *p) { return __bfloat162float(__ldg(p)); }
-__device__ __forceinline__ float ld_q(const __half *p) { return __half2float(__ldg(p)); }
+// ------------------------------------------------------------------ storage conversions
+__device__ __forceinline__ double q_to(double v, double) { return v; }
+__device__ __forceinline__ float q_to(float v, float) { return v; }
+__device__ __forceinline__ float q_to(__nv_bfloat16 v, float) { return __bfloat162float(v); }
+__device__ __forceinline__ float q_to(__half v, float) { return __half2float(v); }
+
+// FP64 -> FP32, round to nearest even, with integer instructions only.  Magnitudes below 2^-126
+// flush to signed zero; Inf/NaN map to Inf/NaN; finite values beyond the float range are not
+// expected here (L-vector entries of a PDE solve).
+__device__ __forceinline__ float d2f_int(double d) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(d);
+  const unsigned hi = (unsigned)(b >> 32), lo = (unsigned)b;
+  const unsigned sign = hi & 0x80000000u;
+  const int e = (int)((hi >> 20) & 0x7ffu);
+  if (e == 0x7ff) return __uint_as_float(sign | 0x7f800000u | ((hi & 0xfffffu) ? 0x400000u : 0u));
+  if (e < 1023 - 126) return __uint_as_float(sign);
+  const unsigned mant = ((hi & 0xfffffu) << 3) | (lo >> 29);
+  const unsigned rest = lo & 0x1fffffffu;
+  unsigned f = ((unsigned)(e - 1023 + 127) << 23) | mant;
+  f += (rest > 0x10000000u || (rest == 0x10000000u && (mant & 1u))) ? 1u : 0u;
+  return __uint_as_float(sign | f);
+}
+
+// FP32 -> FP64 (exact), integer instructions only; FP32 denormals flush to zero.
+__device__ __forceinline__ double f2d_int(float f) {
+  const unsigned u = __float_as_uint(f);
+  const unsigned sign = u & 0x80000000u;
+  const unsigned e = (u >> 23) & 0xffu, m = u & 0x7fffffu;
+  unsigned hi;
+  if (e == 0) hi = sign;
+  else if (e == 0xff) hi = sign | 0x7ff00000u | (m >> 3) | (m ? 0x80000u : 0u);
+  else hi = sign | ((e + (1023 - 127)) << 20) | (m >> 3);
+  const unsigned lo = (e == 0) ? 0u : (m << 29);
+  return __hiloint2double((int)hi, (int)lo);
+}
+
+template <typename T>
+struct LVec;
+template <>
+struct LVec<double> {  // FP64 operator: native
+  static __device__ __forceinline__ double in(double v) { return v; }
+  static __device__ __forceinline__ double out(double v) { return v; }
+  static __device__ __forceinline__ double add(double old, double v) { return old + v; }
+};
+template <>
+struct LVec<float> {   // FP32 operator: integer conversions, FP32 accumulation across colours
+  static __device__ __forceinline__ float in(double v) { return d2f_int(v); }
+  static __device__ __forceinline__ double out(float v) { return f2d_int(v); }
+  static __device__ __forceinline__ double add(double old, float v) { return f2d_int(d2f_int(old) + v); }
+};
+
+// ------------------------------------------------------------------ TMA bulk copy + mbarrier
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void tma_bulk_load(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   smem_u32(dst)),
+               "l"(src), "r"(bytes), "r"(smem_u32(bar))
+               : "memory");
+}
+
+// Bounded wait on phase `parity`: returns false if the copy did not land within the limit.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
+  const uint32_t a = smem_u32(bar);
+  for (int it = 0; it < (1 << 22); ++it) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(a), "r"(parity)
+        : "memory");
+    if (ok) return true;
+  }
+  return false;
+}
+
+// ------------------------------------------------------------------ even-odd 1D operator
+// out = M v for an NO x NI matrix with M[NO-1-i][NI-1-j] = S M[i][j] (S = +1 centro-symmetric,
+// S = -1 centro-antisymmetric).  With e_j = v_j + v_{NI-1-j}, o_j = v_j - v_{NI-1-j} (j < NI/2):
+//   out_i        =      sum_j E_ij e_j + sum_j O_ij o_j + M[i][mid] v_mid
+//   out_{NO-1-i} = S * (sum_j E_ij e_j - sum_j O_ij o_j + M[i][mid] v_mid)
+// with E = (M[i][j] + M[i][NI-1-j]) / 2, O = (M[i][j] - M[i][NI-1-j]) / 2; odd NO adds the middle row.
+template <int NO, int NI, int S, typename T>
+__device__ __forceinline__ void eo_apply(const EOMat<T> &M, const T *v, T *out) {
+  constexpr int HI = NI / 2, HO = NO / 2;
+  T e[HI > 0 ? HI : 1], o[HI > 0 ? HI : 1];
+#pragma unroll
+  for (int j = 0; j < HI; ++j) {
+    e[j] = v[j] + v[NI - 1 - j];
+    o[j] = v[j] - v[NI - 1 - j];
+  }
+#pragma unroll
+  for (int i = 0; i < HO; ++i) {
+    T a = (NI & 1) ? M.cmid[i] * v[HI] : (T)0;
+    T b = 0;
+#pragma unroll
+    for (int j = 0; j < HI; ++j) {
+      a += M.E[i * EO_H + j] * e[j];
+      b += M.O[i * EO_H + j] * o[j];
+    }
+    out[i] = a + b;
+    out[NO - 1 - i] = (S > 0) ? (a - b) : (b - a);
+  }
+  if constexpr (NO & 1) {
+    T c = (NI & 1) ? M.cc * v[HI] : (T)0;
+#pragma unroll
+    for (int j = 0; j < HI; ++j) c += M.rmid[j] * ((S > 0) ? e[j] : o[j]);
+    out[HO] = c;
+  }
+}
 
 template <int Q>
 constexpr int elems_per_block() {
   return (Q * Q >= 128) ? 1 : (128 / (Q * Q));
 }
 
+template <int Q>
+constexpr int tile_words() {
+  return Q * Q * (Q + 1);
+}
+
+template <int P, int Q, int OP, typename T, typename TQ>
+constexpr size_t apply_smem_bytes() {
+  constexpr int NE = elems_per_block<Q>();
+  constexpr int NCQ = (OP == CEED_OP_DIFFUSION) ? 6 : 1;
+  constexpr size_t qbytes = ((size_t)NCQ * Q * Q * Q * sizeof(TQ) + 16 + 127) & ~(size_t)127;
+  constexpr int ntiles = (OP == CEED_OP_DIFFUSION) ? 3 : 2;
+  constexpr size_t tbytes = ((size_t)ntiles * tile_words<Q>() * sizeof(T) + 127) & ~(size_t)127;
+  return NE * (qbytes + tbytes);
+}
+
+// Tile index: (t, s, r) -> (t * Q + s) * (Q + 1) + r.
+template <int Q>
+__device__ __forceinline__ int tix(int t, int s, int r) {
+  return (t * Q + s) * (Q + 1) + r;
+}
+
+struct ApplyArgs {
+  const uint32_t *emap;
+  const void *qdata;
+  const double *x;
+  double *y;
+  int64_t e_begin, e_count;
+  int64_t estride;  // quadrature data per element, in TQ units (16-byte multiple)
+  int ncol, masked;
+  int *err;
+};
+
 template <int P, int Q, int OP, typename T, typename TQ>
 __global__ void __launch_bounds__(Q * Q * elems_per_block<Q>())
-apply_kernel(const uint32_t *__restrict__ emap, const TQ *__restrict__ qdata, const double *__restrict__ x,
-             double *__restrict__ y, int64_t e_begin, int64_t e_count, int ncol, int masked, const OpTab<T> tab) {
+apply_kernel(const ApplyArgs a, const OpTab<T> tab) {
   constexpr int NE = elems_per_block<Q>();
   constexpr int NPT = Q * Q;
   constexpr bool COLLOC = (P == Q);
   constexpr int ND = P * P * P;
   constexpr int NQ = Q * Q * Q;
   constexpr int NCQ = (OP == CEED_OP_DIFFUSION) ? 6 : 1;
-  __shared__ T smem[NE][2][NQ];
+  constexpr size_t QB = ((size_t)NCQ * NQ * sizeof(TQ) + 16 + 127) & ~(size_t)127;
+  constexpr int NT = (OP == CEED_OP_DIFFUSION) ? 3 : 2;
+  constexpr size_t TB = ((size_t)NT * tile_words<Q>() * sizeof(T) + 127) & ~(size_t)127;
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  __shared__ uint64_t bar[NE];
 
   const int tid = threadIdx.x;
   const int el = tid / NPT;
   const int ij = tid - el * NPT;
   const int i = ij % Q, j = ij / Q;
-  const int64_t e = e_begin + (int64_t)blockIdx.x * NE + el;
-  const bool active = e < e_begin + e_count;
+  const int64_t e = a.e_begin + (int64_t)blockIdx.x * NE + el;
+  const bool active = e < a.e_begin + a.e_count;
   const bool node_thread = (i < P) && (j < P);
-  T *s0 = smem[el][0];
-  T *s1 = smem[el][1];
+  TQ *sq = (TQ *)(smem_raw + el * (QB + TB));
+  T *sa = (T *)(smem_raw + el * (QB + TB) + QB);
+  T *sb = sa + tile_words<Q>();
+  T *sc = sb + tile_words<Q>();  // diffusion only
 
+  // ---- quadrature data: one bulk copy per element, in flight during the gather and the forward passes
+  if (ij == 0) {
+    mbar_init(&bar[el], 1);
+    if (active)
+      tma_bulk_load(sq, (const TQ *)a.qdata + e * a.estride, (uint32_t)(a.estride * sizeof(TQ)), &bar[el]);
+  }
+  __syncthreads();  // barrier initialised before any thread waits on it
+
+  // ---- restriction of my node column (a = i, b = j, c = 0..P-1)
   uint32_t idx[P];
 #pragma unroll
   for (int c = 0; c < P; ++c) idx[c] = 0;
   if (active && node_thread) {
-    const uint32_t *em = emap + e * ND + j * P + i;
+    const uint32_t *em = a.emap + e * ND + j * P + i;
 #pragma unroll
     for (int c = 0; c < P; ++c) idx[c] = __ldg(em + c * P * P);
   }
-  const TQ *qd = qdata + (active ? e : e_begin) * (int64_t)(NCQ * NQ) + ij;
+  bool have_q = false;
 
-  for (int col = 0; col < ncol; ++col) {
-    // ---------------- gather (L -> E)
-    T u[P];
+  for (int col = 0; col < a.ncol; ++col) {
+    // ---- all global loads of the column up front: x at my nodes, old y where an earlier colour wrote
+    double xv[P], yold[P];
 #pragma unroll
     for (int c = 0; c < P; ++c) {
-      double xv = 0.0;
+      xv[c] = 0.0;
+      yold[c] = 0.0;
       if (active && node_thread) {
         const uint32_t v = idx[c];
-        if (!(masked && (v & FLAG_DIR))) xv = __ldg(x + (int64_t)(v & DOF_MASK) * ncol + col);
+        const int64_t o = (int64_t)(v & DOF_MASK) * a.ncol + col;
+        const bool dir = a.masked && (v & FLAG_DIR);
+        if (!dir) xv[c] = __ldg(a.x + o);
+        if (!dir && !(v & FLAG_FIRST)) yold[c] = a.y[o];
       }
-      u[c] = (T)xv;
     }
+    T u[P];
+#pragma unroll
+    for (int c = 0; c < P; ++c) u[c] = LVec<T>::in(xv[c]);
 
-    // ---------------- interpolate to the quadrature points (identity when collocated)
+    // ---- interpolate to the quadrature points (identity when collocated)
     T uq[Q];
     if constexpr (COLLOC) {
 #pragma unroll
       for (int k = 0; k < Q; ++k) uq[k] = u[k];
     } else {
-      if (node_thread) {
+      if (node_thread) {  // t: column owners (r = i, s = j) hold the line in registers
+        T w[Q];
+        eo_apply<Q, P, 1>(tab.eB, u, w);
 #pragma unroll
-        for (int k = 0; k < Q; ++k) {
-          T a = 0;
-#pragma unroll
-          for (int c = 0; c < P; ++c) a += tab.B[k * P + c] * u[c];
-          s0[(k * Q + j) * Q + i] = a;
-        }
+        for (int k = 0; k < Q; ++k) sa[tix<Q>(k, j, i)] = w[k];
       }
       __syncthreads();
-      if (i < P) {
-        T Bj[P];
+      if (i < P) {        // s: owners (r = i, t = j)
+        T v[P], w[Q];
 #pragma unroll
-        for (int b = 0; b < P; ++b) Bj[b] = tab.B[j * P + b];
+        for (int m = 0; m < P; ++m) v[m] = sa[tix<Q>(j, m, i)];
+        eo_apply<Q, P, 1>(tab.eB, v, w);
 #pragma unroll
-        for (int k = 0; k < Q; ++k) {
-          T a = 0;
-#pragma unroll
-          for (int b = 0; b < P; ++b) a += Bj[b] * s0[(k * Q + b) * Q + i];
-          s1[(k * Q + j) * Q + i] = a;
-        }
+        for (int n = 0; n < Q; ++n) sb[tix<Q>(j, n, i)] = w[n];
       }
       __syncthreads();
-      T Bi[P];
+      {                   // r: owners (s = i, t = j)
+        T v[P], w[Q];
 #pragma unroll
-      for (int a = 0; a < P; ++a) Bi[a] = tab.B[i * P + a];
+        for (int m = 0; m < P; ++m) v[m] = sb[tix<Q>(j, i, m)];
+        eo_apply<Q, P, 1>(tab.eB, v, w);
 #pragma unroll
-      for (int k = 0; k < Q; ++k) {
-        T a = 0;
-#pragma unroll
-        for (int m = 0; m < P; ++m) a += Bi[m] * s1[(k * Q + j) * Q + m];
-        uq[k] = a;
+        for (int n = 0; n < Q; ++n) sa[tix<Q>(j, i, n)] = w[n];
       }
+      __syncthreads();
+#pragma unroll
+      for (int k = 0; k < Q; ++k) uq[k] = sa[tix<Q>(k, j, i)];
     }
 
-    // ---------------- quadrature-point operator
+    // ---- quadrature-point operator
     T w[Q];
+    if (!have_q) {  // elements past the end issued no copy and do not wait
+      if (active && !mbar_wait(&bar[el], 0)) {
+        if (ij == 0) *a.err = CEED_ERR_TIMEOUT;
+      }
+      have_q = true;
+    }
     if constexpr (OP == CEED_OP_MASS) {
 #pragma unroll
-      for (int k = 0; k < Q; ++k) w[k] = active ? (T)ld_q(qd + k * NPT) * uq[k] : (T)0;
+      for (int k = 0; k < Q; ++k) w[k] = q_to(sq[(k * Q + j) * Q + i], T()) * uq[k];
     } else {
+      T ut[Q];
+      eo_apply<Q, Q, -1>(tab.eD, uq, ut);
+      if constexpr (COLLOC) {
 #pragma unroll
-      for (int k = 0; k < Q; ++k) s0[(k * Q + j) * Q + i] = uq[k];
-      __syncthreads();
-      T ur[Q], us[Q], ut[Q];
-      {
-        T Di[Q], Dj[Q];
+        for (int k = 0; k < Q; ++k) sa[tix<Q>(k, j, i)] = uq[k];
+        __syncthreads();
+      }  // non-collocated: sa already holds uq at these positions
+      {  // r: owners (s = i, t = j)
+        T v[Q], g[Q];
 #pragma unroll
-        for (int m = 0; m < Q; ++m) {
-          Di[m] = tab.D[i * Q + m];
-          Dj[m] = tab.D[j * Q + m];
-        }
+        for (int m = 0; m < Q; ++m) v[m] = sa[tix<Q>(j, i, m)];
+        eo_apply<Q, Q, -1>(tab.eD, v, g);
 #pragma unroll
-        for (int k = 0; k < Q; ++k) {
-          T a = 0, b = 0, c = 0;
-#pragma unroll
-          for (int m = 0; m < Q; ++m) {
-            a += Di[m] * s0[(k * Q + j) * Q + m];
-            b += Dj[m] * s0[(k * Q + m) * Q + i];
-            c += tab.D[k * Q + m] * uq[m];
-          }
-          ur[k] = a;
-          us[k] = b;
-          ut[k] = c;
-        }
+        for (int n = 0; n < Q; ++n) sb[tix<Q>(j, i, n)] = g[n];
       }
+      {  // s: owners (r = i, t = j)
+        T v[Q], g[Q];
 #pragma unroll
-      for (int k = 0; k < Q; ++k) {
-        T vr = 0, vs = 0, vt = 0;
-        if (active) {
-          const TQ *g = qd + k * NPT;
-          const T grr = (T)ld_q(g), grs = (T)ld_q(g + NQ), grt = (T)ld_q(g + 2 * NQ);
-          const T gss = (T)ld_q(g + 3 * NQ), gst = (T)ld_q(g + 4 * NQ), gtt = (T)ld_q(g + 5 * NQ);
-          vr = grr * ur[k] + grs * us[k] + grt * ut[k];
-          vs = grs * ur[k] + gss * us[k] + gst * ut[k];
-          vt = grt * ur[k] + gst * us[k] + gtt * ut[k];
-        }
-        ur[k] = vr;
-        us[k] = vs;
-        ut[k] = vt;
+        for (int m = 0; m < Q; ++m) v[m] = sa[tix<Q>(j, m, i)];
+        eo_apply<Q, Q, -1>(tab.eD, v, g);
+#pragma unroll
+        for (int n = 0; n < Q; ++n) sc[tix<Q>(j, n, i)] = g[n];
       }
       __syncthreads();
+      // pointwise v = G grad u at my column, in place
+      T vt[Q];
 #pragma unroll
       for (int k = 0; k < Q; ++k) {
-        s0[(k * Q + j) * Q + i] = ur[k];
-        s1[(k * Q + j) * Q + i] = us[k];
+        const int q = (k * Q + j) * Q + i;
+        const T grr = q_to(sq[q], T()), grs = q_to(sq[NQ + q], T()), grt = q_to(sq[2 * NQ + q], T());
+        const T gss = q_to(sq[3 * NQ + q], T()), gst = q_to(sq[4 * NQ + q], T()), gtt = q_to(sq[5 * NQ + q], T());
+        const T ur = sb[tix<Q>(k, j, i)], us = sc[tix<Q>(k, j, i)];
+        sb[tix<Q>(k, j, i)] = grr * ur + grs * us + grt * ut[k];
+        sc[tix<Q>(k, j, i)] = grs * ur + gss * us + gst * ut[k];
+        vt[k] = grt * ur + gst * us + gtt * ut[k];
       }
       __syncthreads();
-      T DTi[Q], DTj[Q];
+      {  // r transposed: owners (s = i, t = j)
+        T v[Q], g[Q];
 #pragma unroll
-      for (int m = 0; m < Q; ++m) {
-        DTi[m] = tab.D[m * Q + i];
-        DTj[m] = tab.D[m * Q + j];
+        for (int m = 0; m < Q; ++m) v[m] = sb[tix<Q>(j, i, m)];
+        eo_apply<Q, Q, -1>(tab.eDT, v, g);
+#pragma unroll
+        for (int n = 0; n < Q; ++n) sa[tix<Q>(j, i, n)] = g[n];
       }
+      {  // s transposed: owners (r = i, t = j), in place on their own line
+        T v[Q], g[Q];
 #pragma unroll
-      for (int k = 0; k < Q; ++k) {
-        T a = 0;
+        for (int m = 0; m < Q; ++m) v[m] = sc[tix<Q>(j, m, i)];
+        eo_apply<Q, Q, -1>(tab.eDT, v, g);
 #pragma unroll
-        for (int m = 0; m < Q; ++m) {
-          a += DTi[m] * s0[(k * Q + j) * Q + m];
-          a += DTj[m] * s1[(k * Q + m) * Q + i];
-          a += tab.D[m * Q + k] * ut[m];
-        }
-        w[k] = a;
+        for (int n = 0; n < Q; ++n) sc[tix<Q>(j, n, i)] = g[n];
       }
+      T yt[Q];
+      eo_apply<Q, Q, -1>(tab.eDT, vt, yt);
+      __syncthreads();
+#pragma unroll
+      for (int k = 0; k < Q; ++k) w[k] = yt[k] + sa[tix<Q>(k, j, i)] + sc[tix<Q>(k, j, i)];
     }
 
-    // ---------------- transposed interpolation back to the nodes
+    // ---- transposed interpolation back to the nodes
     T yv[P];
     if constexpr (COLLOC) {
 #pragma unroll
       for (int c = 0; c < P; ++c) yv[c] = w[c];
     } else {
+      {  // t: column owners, registers
+        T z[P];
+        eo_apply<P, Q, 1>(tab.eBT, w, z);
+        if constexpr (OP == CEED_OP_MASS) __syncthreads();  // sa was last read as the uq column
+#pragma unroll
+        for (int c = 0; c < P; ++c) sa[tix<Q>(c, j, i)] = z[c];
+      }
       __syncthreads();
+      if (j < P) {  // s: owners (r = i, t = j)
+        T v[Q], z[P];
 #pragma unroll
-      for (int k = 0; k < Q; ++k) s0[(k * Q + j) * Q + i] = w[k];
+        for (int m = 0; m < Q; ++m) v[m] = sa[tix<Q>(j, m, i)];
+        eo_apply<P, Q, 1>(tab.eBT, v, z);
+#pragma unroll
+        for (int n = 0; n < P; ++n) sb[tix<Q>(j, n, i)] = z[n];
+      }
       __syncthreads();
-      if (i < P) {
-        T BTa[Q];
+      if (node_thread) {  // r: owners (s = i, t = j)
+        T v[Q], z[P];
 #pragma unroll
-        for (int m = 0; m < Q; ++m) BTa[m] = tab.B[m * P + i];
+        for (int m = 0; m < Q; ++m) v[m] = sb[tix<Q>(j, i, m)];
+        eo_apply<P, Q, 1>(tab.eBT, v, z);
 #pragma unroll
-        for (int k = 0; k < Q; ++k) {
-          T a = 0;
-#pragma unroll
-          for (int m = 0; m < Q; ++m) a += BTa[m] * s0[(k * Q + j) * Q + m];
-          s1[(k * Q + j) * Q + i] = a;
-        }
+        for (int n = 0; n < P; ++n) sa[tix<Q>(j, i, n)] = z[n];
       }
       __syncthreads();
 #pragma unroll
-      for (int c = 0; c < P; ++c) yv[c] = 0;
-      if (node_thread) {
-        T BTb[Q];
-#pragma unroll
-        for (int m = 0; m < Q; ++m) BTb[m] = tab.B[m * P + j];
-        T t[Q];
-#pragma unroll
-        for (int k = 0; k < Q; ++k) {
-          T a = 0;
-#pragma unroll
-          for (int m = 0; m < Q; ++m) a += BTb[m] * s1[(k * Q + m) * Q + i];
-          t[k] = a;
-        }
-#pragma unroll
-        for (int c = 0; c < P; ++c) {
-          T a = 0;
-#pragma unroll
-          for (int k = 0; k < Q; ++k) a += tab.B[k * P + c] * t[k];
-          yv[c] = a;
-        }
-      }
+      for (int c = 0; c < P; ++c) yv[c] = node_thread ? sa[tix<Q>(c, j, i)] : (T)0;
     }
 
-    // ---------------- scatter-add (E -> L), atomic-free
+    // ---- scatter-add (E -> L), atomic-free
     if (active && node_thread) {
 #pragma unroll
       for (int c = 0; c < P; ++c) {
         const uint32_t v = idx[c];
-        const int64_t o = (int64_t)(v & DOF_MASK) * ncol + col;
-        if (masked && (v & FLAG_DIR)) {
-          if (v & FLAG_FIRST) y[o] = x[o];
+        const int64_t o = (int64_t)(v & DOF_MASK) * a.ncol + col;
+        if (a.masked && (v & FLAG_DIR)) {
+          if (v & FLAG_FIRST) a.y[o] = a.x[o];
         } else if (v & FLAG_FIRST) {
-          y[o] = (double)yv[c];
+          a.y[o] = LVec<T>::out(yv[c]);
         } else {
-          y[o] += (double)yv[c];
+          a.y[o] = LVec<T>::add(yold[c], yv[c]);
         }
       }
     }
-    if (col + 1 < ncol) __syncthreads();
+    if (col + 1 < a.ncol) __syncthreads();
   }
+  // an element that never reached the pointwise step (cannot happen today) must not leave its copy in flight
+  if (!have_q && ij == 0 && active) mbar_wait(&bar[el], 0);
 }
 
 // Launch one kernel per colour for a fixed (P, Q, op, T, TQ).
 template <int P, int Q, int OP, typename T, typename TQ>
 int launch_colours(ceed_mesh_t m, const OpTab<T> &tab, const ApplyReq &r, cudaStream_t s) {
   constexpr int NE = elems_per_block<Q>();
+  constexpr size_t SMEM = apply_smem_bytes<P, Q, OP, T, TQ>();
+  static bool configured = false;  // per instantiation; the attribute is per function, any device
+  if (!configured) {
+    CEED_CUDA_CHECK(cudaFuncSetAttribute(apply_kernel<P, Q, OP, T, TQ>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)SMEM));
+    configured = true;
+  }
   const dim3 block(Q * Q * NE);
+  ApplyArgs a;
+  a.emap = m->d_emap;
+  a.qdata = r.qdata;
+  a.x = r.x;
+  a.y = r.y;
+  a.ncol = r.ncol;
+  a.masked = r.masked;
+  a.err = m->d_err + 1;
+  a.estride = qdata_estride(OP, sizeof(TQ), Q);
   for (int c = 0; c < m->n_colors; ++c) {
-    const int64_t b = m->color_start[c], n = m->color_start[c + 1] - b;
+    a.e_begin = m->color_start[c];
+    const int64_t n = m->color_start[c + 1] - a.e_begin;
     if (n == 0) continue;
+    a.e_count = n;
     const dim3 grid((unsigned)((n + NE - 1) / NE));
-    apply_kernel<P, Q, OP, T, TQ><<<grid, block, 0, s>>>(m->d_emap, (const TQ *)r.qdata, r.x, r.y, b, n, r.ncol,
-                                                         r.masked, tab);
+    apply_kernel<P, Q, OP, T, TQ><<<grid, block, SMEM, s>>>(a, tab);
   }
   CEED_CUDA_CHECK(cudaGetLastError());
   return CEED_OK;
@@ -273,6 +451,7 @@ int launch_colours(ceed_mesh_t m, const OpTab<T> &tab, const ApplyReq &r, cudaSt
 // Dispatch on (P, collocated?, op) for one (T, TQ) pair.
 template <typename T, typename TQ>
 int dispatch_apply(ceed_mesh_t m, const OpTab<T> &tab, const ApplyReq &r, cudaStream_t s) {
+  if (((uintptr_t)r.qdata & 15) != 0) return fail(CEED_ERR_INVALID, "qdata must be 16-byte aligned");
   const bool colloc = (m->Q == m->P);
 #define CEEDGB_CASE(PP)                                                                                   \
   case PP:                                                                                               \

@@ -20,13 +20,35 @@ constexpr uint32_t FLAG_FIRST = 1u << 31;
 constexpr uint32_t FLAG_DIR = 1u << 30;
 constexpr uint32_t DOF_MASK = (1u << 30) - 1u;
 
+// Even-odd split of a centro-(anti)symmetric NO x NI matrix M (M[NO-1-i][NI-1-j] = +-M[i][j]):
+// E/O are the (NO/2) x (NI/2) blocks acting on folded inputs, cmid the middle input column
+// (odd NI), rmid the middle output row (odd NO), cc the centre entry.
+constexpr int EO_H = 5;
+template <typename T>
+struct EOMat {
+  T E[EO_H * EO_H];
+  T O[EO_H * EO_H];
+  T cmid[EO_H];
+  T rmid[EO_H];
+  T cc;
+};
+
 // 1D operators passed to kernels by value (kernel parameters live in the constant bank, so
 // compile-time indices become constant operands of the FMAs).
 template <typename T>
 struct OpTab {
   T B[MAX_Q * MAX_P];   // B[q * P + a] = l_a(xi_q): GLL Lagrange basis at the quadrature points
   T D[MAX_Q * MAX_Q];   // D[i * Q + m] = derivative at xi_i of the Lagrange basis on the Q points
+  EOMat<T> eB, eBT, eD, eDT;  // even-odd forms of B (Q x P), B^T, D (Q x Q), D^T
 };
+
+// Quadrature data layout: [colour-sorted element][component][Q^3], each element block padded to a
+// multiple of 16 bytes so that it can be moved by one TMA bulk copy.
+__host__ __device__ inline int64_t qdata_estride(int op, size_t elem_bytes, int Q) {
+  const int64_t nc = (op == CEED_OP_DIFFUSION) ? 6 : 1;
+  const int64_t b = nc * Q * Q * Q * (int64_t)elem_bytes;
+  return ((b + 15) / 16) * 16 / (int64_t)elem_bytes;
+}
 
 struct QRule {
   double x[MAX_Q];
@@ -65,6 +87,7 @@ int cuda_fail(cudaError_t e, const char *where);
 
 int check_mesh(ceed_mesh_t m);
 int nq_of(const ceed_mesh_t m);
+size_t prec_size(int prec);
 
 // host-side 1D bases (mesh.cu)
 void gll_rule(int n, double *x, double *w);

@@ -64,6 +64,12 @@ void gauss_rule(int n, double *x, double *w) {
     x[i] = t;
     w[i] = 2.0 / ((1.0 - t * t) * dp * dp);
   }
+  // exact mirror symmetry (the even-odd kernels rely on it)
+  for (int i = 0; i < n / 2; ++i) {
+    x[n - 1 - i] = -x[i];
+    w[n - 1 - i] = w[i];
+  }
+  if (n & 1) x[n / 2] = 0.0;
 }
 
 void gll_rule(int n, double *x, double *w) {
@@ -87,6 +93,11 @@ void gll_rule(int n, double *x, double *w) {
     x[i] = t;
     w[i] = 2.0 / (n * m * p * p);
   }
+  for (int i = 0; i < n / 2; ++i) {
+    x[n - 1 - i] = -x[i];
+    w[n - 1 - i] = w[i];
+  }
+  if (n & 1) x[n / 2] = 0.0;
 }
 
 // Barycentric weights lambda_j = 1 / prod_{m != j} (x_j - x_m).
@@ -134,6 +145,29 @@ static void deriv_matrix(int n, const double *x, double *D) {
   }
 }
 
+// Even-odd blocks of an NO x NI matrix with M[NO-1-i][NI-1-j] = S M[i][j] (symmetry enforced:
+// the blocks are built from the upper half only).
+static void make_eo(const double *M, int NO, int NI, int S, EOMat<double> *d, EOMat<float> *f) {
+  std::memset(d, 0, sizeof(*d));
+  std::memset(f, 0, sizeof(*f));
+  const int HO = NO / 2, HI = NI / 2;
+  for (int i = 0; i < HO; ++i) {
+    for (int j = 0; j < HI; ++j) {
+      const double a = M[i * NI + j], b = M[i * NI + (NI - 1 - j)];
+      d->E[i * EO_H + j] = 0.5 * (a + b);
+      d->O[i * EO_H + j] = 0.5 * (a - b);
+    }
+    if (NI & 1) d->cmid[i] = M[i * NI + HI];
+  }
+  if (NO & 1) {
+    for (int j = 0; j < HI; ++j) d->rmid[j] = M[HO * NI + j];
+    if (NI & 1) d->cc = (S > 0) ? M[HO * NI + HI] : 0.0;
+  }
+  const double *src = &d->E[0];
+  float *dst = &f->E[0];
+  for (size_t k = 0; k < sizeof(*d) / sizeof(double); ++k) dst[k] = (float)src[k];
+}
+
 static void build_tables(ceed_mesh_s *m) {
   double w_gll[MAX_P];
   gll_rule(m->P, m->gll_x, w_gll);
@@ -158,6 +192,16 @@ static void build_tables(ceed_mesh_s *m) {
     m->tab64.D[k] = D[k];
     m->tab32.D[k] = (float)D[k];
   }
+  const int P = m->P, Q = m->Q;
+  double BT[MAX_P * MAX_Q], DT[MAX_Q * MAX_Q];
+  for (int q = 0; q < Q; ++q)
+    for (int a = 0; a < P; ++a) BT[a * Q + q] = B[q * P + a];
+  for (int i = 0; i < Q; ++i)
+    for (int k = 0; k < Q; ++k) DT[k * Q + i] = D[i * Q + k];
+  make_eo(B, Q, P, +1, &m->tab64.eB, &m->tab32.eB);
+  make_eo(BT, P, Q, +1, &m->tab64.eBT, &m->tab32.eBT);
+  make_eo(D, Q, Q, -1, &m->tab64.eD, &m->tab32.eD);
+  make_eo(DT, Q, Q, -1, &m->tab64.eDT, &m->tab32.eDT);
 }
 
 int launch_apply(ceed_mesh_t m, const ApplyReq &r, cudaStream_t s);
@@ -359,7 +403,7 @@ extern "C" int ceed_mesh_info(ceed_mesh_t m, int32_t *n_colors, int32_t *Q, int3
   return CEED_OK;
 }
 
-static size_t prec_size(int prec) {
+size_t ceedgb::prec_size(int prec) {
   switch (prec) {
     case CEED_F64: return 8;
     case CEED_F32: return 4;
@@ -371,7 +415,7 @@ static size_t prec_size(int prec) {
 
 extern "C" size_t ceed_qdata_bytes(ceed_mesh_t m, int op, int prec) {
   if (!m || prec_size(prec) == 0 || (op != CEED_OP_MASS && op != CEED_OP_DIFFUSION)) return 0;
-  return (size_t)m->E * (op == CEED_OP_DIFFUSION ? 6 : 1) * nq_of(m) * prec_size(prec);
+  return (size_t)m->E * qdata_estride(op, prec_size(prec), m->Q) * prec_size(prec);
 }
 
 static int apply_common(ceed_mesh_t m, int op, const void *qdata, int prec, const double *x, double *y, int nrhs,

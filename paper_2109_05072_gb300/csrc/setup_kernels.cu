@@ -24,7 +24,7 @@ __device__ __forceinline__ __half to_store<__half>(double v) { return __float2ha
 template <typename TQ>
 __global__ void qdata_kernel(int64_t E, int Q, const double *__restrict__ vert, const int32_t *__restrict__ perm,
                              int op, int coeff_kind, double cconst, const double *__restrict__ coeff, QRule rule,
-                             TQ *__restrict__ out, int *err) {
+                             TQ *__restrict__ out, int64_t estride, int *err) {
   const int nq = Q * Q * Q;
   const int64_t total = E * nq;
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
@@ -42,10 +42,10 @@ __global__ void qdata_kernel(int64_t E, int Q, const double *__restrict__ vert, 
     else if (coeff_kind == CEED_COEFF_SINE) kq = sine_coefficient(X);
     else if (coeff_kind == CEED_COEFF_PER_QPT) kq = coeff[(int64_t)perm[s] * nq + q];
     if (op == CEED_OP_MASS) {
-      out[s * nq + q] = to_store<TQ>(w * fabs(det) * kq);
+      out[s * estride + q] = to_store<TQ>(w * fabs(det) * kq);
     } else {
       const double f = w * kq / det;
-      TQ *o = out + s * 6 * nq + q;
+      TQ *o = out + s * estride + q;
       o[0 * nq] = to_store<TQ>(f * (A[0][0] * A[0][0] + A[0][1] * A[0][1] + A[0][2] * A[0][2]));
       o[1 * nq] = to_store<TQ>(f * (A[0][0] * A[1][0] + A[0][1] * A[1][1] + A[0][2] * A[1][2]));
       o[2 * nq] = to_store<TQ>(f * (A[0][0] * A[2][0] + A[0][1] * A[2][1] + A[0][2] * A[2][2]));
@@ -94,7 +94,7 @@ __global__ void elemvec_kernel(ElemVecArgs a) {
     }
     __syncthreads();
   }
-  const double *qd = a.qd ? a.qd + e * (int64_t)(a.mode == 2 ? 6 : 1) * nq : nullptr;
+  const double *qd = a.qd ? a.qd + e * qdata_estride(a.mode == 2 ? CEED_OP_DIFFUSION : CEED_OP_MASS, 8, Q) : nullptr;
   for (int n = threadIdx.x; n < nd; n += blockDim.x) {
     const int ia = n % P, ib = (n / P) % P, ic = n / (P * P);
     double val = 0.0;
@@ -195,7 +195,8 @@ static int build_qdata_impl(ceed_mesh_t m, int op, int coeff_kind, const double 
   const unsigned blocks = (unsigned)std::min<int64_t>((total + threads - 1) / threads, 152 * 64);
 #define CEEDGB_Q(TQ)                                                                                      \
   qdata_kernel<TQ><<<blocks, threads, 0, s>>>(m->E, m->Q, m->d_vertices, m->d_perm, op, coeff_kind, cconst, \
-                                              coeff, m->rule, (TQ *)qdata, m->d_err)
+                                              coeff, m->rule, (TQ *)qdata, qdata_estride(op, sizeof(TQ), m->Q), \
+                                              m->d_err)
   switch (prec) {
     case CEED_F64: CEEDGB_Q(double); break;
     case CEED_F32: CEEDGB_Q(float); break;
