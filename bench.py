@@ -34,6 +34,10 @@ import synthetic  # noqa: E402
 
 METRIC = "diffusion apply GDOF/s at p=7 (FP64 vs mixed), % HBM roofline, CG time-to-1e-10"
 FP64_NOMINAL_TFLOPS = 1.25      # GB300 dense FP64 (profiling recipe's nominal table)
+# DRAM bytes (read + write) per launch of the FP64 apply kernel, from one ncu capture of the current
+# kernel on the 48^3 mesh (13,824 elements per colour launch: 571.2 MB), scaled by elements to a
+# 64^3 colour launch (32,768 elements).  See profiles/apply_kernel_p7_48cube_ncu.md.
+PROFILED_TRAFFIC_PER_LAUNCH = {"apply_kernel<8,8,DIFFUSION,double,double>": 571.15e6 * 32768 / 13824}
 WORKLOADS = {
     "c2": dict(N=64, p=7),      # the diffusion workload named by element count
     "c2a": dict(N=40, p=7),     # 22.19M DOFs: the DOF count quoted for the same workload
@@ -176,7 +180,7 @@ def main():
     ap.add_argument("--workload", default="c2", choices=sorted(WORKLOADS))
     ap.add_argument("--cg", type=int, default=1, help="run the CG measurements (1) or skip them (0)")
     ap.add_argument("--cg-workload", default="c2", choices=sorted(WORKLOADS))
-    ap.add_argument("--cpu-sample", type=int, default=6000, help="elements in the timed oracle sample")
+    ap.add_argument("--cpu-sample", type=int, default=40000, help="elements in the timed oracle sample")
     ap.add_argument("--ref-sample", type=int, default=1000, help="elements per reference-arm step")
     args = ap.parse_args()
     if args.impl == "reference":
@@ -205,6 +209,7 @@ def main():
                                 torch.from_numpy(m.vertices).to(dev), torch.from_numpy(m.boundary).to(dev))
     qd64 = ceed.alloc_qdata(mesh, ceed.CEED_OP_DIFFUSION, ceed.CEED_F64, dev)
     ceed.ceed_build_qdata(mesh, ceed.CEED_OP_DIFFUSION, ceed.CEED_COEFF_SINE, None, ceed.CEED_F64, qd64)
+    n_apply = m.n_ldof
     x_host = synthetic.uniform(m.n_ldof, seed=1 + rank)
     x = torch.from_numpy(x_host).to(dev)
     y = torch.empty_like(x)
@@ -235,7 +240,7 @@ def main():
     apply64 = lambda: ceed.ceed_apply_diffusion(mesh, qd64, ceed.CEED_F64, x, y)
     with ClockSampler(local) as clk:
         ms64 = timed(apply64, args.steps, args.warmup)
-    gdofs64 = ws * m.n_ldof / ms64 / 1e6
+    gdofs64 = ws * n_apply / ms64 / 1e6
     reads, flops_el = cost_per_element(p)
     hbm_peak, hbm_kind = load_peaks()
     bytes64 = algorithmic_bytes(m, 8)
@@ -318,18 +323,21 @@ def main():
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": f"FP64 diffusion apply, {N}^3 perturbed hexes (0.1h), p={p}, GLL collocated q=p+1, "
                                    f"6 stored geometric factors, k=1+0.5sin sin sin",
-                       "n_ldof": m.n_ldof if args.cg_workload == args.workload else synthetic.cube_mesh(N, p, build_map=False).n_ldof,
+                       "n_ldof": n_apply,
                        "n_elem": N ** 3, "l2": "inputs larger than L2 (qdata 6.4 GB), no flush",
                        "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU"},
             "roofline": {"bound": "alu", "achieved": achieved_tf, "peak": FP64_NOMINAL_TFLOPS, "unit": "TFLOP/s",
-                         "frac": achieved_tf / FP64_NOMINAL_TFLOPS, "traffic": None,
+                         "frac": achieved_tf / FP64_NOMINAL_TFLOPS,
+                         "traffic": PROFILED_TRAFFIC_PER_LAUNCH.get("apply_kernel<8,8,DIFFUSION,double,double>")
+                         if N == 64 else None,
+                         "alg_bytes_per_launch": bytes64 / launches_per_apply,
                          "kernel": "apply_kernel<8,8,DIFFUSION,double,double>",
                          "peak_kind": "nominal FP64 (no FP64 entry in MEASURED_PEAKS.json)",
                          "flops_per_launch": flops_launch, "ms_per_launch": ms_launch,
                          "hbm_gbs": bytes64 / (ms64 * 1e-3) / 1e9, "hbm_peak": hbm_peak, "hbm_peak_kind": hbm_kind,
                          "hbm_frac": bytes64 / (ms64 * 1e-3) / 1e9 / hbm_peak},
             "mixed_apply": mixed,
-            "e2e": {"value": ws * m.n_ldof / ms_e2e / 1e6 if args.cg_workload == args.workload else None,
+            "e2e": {"value": ws * n_apply / ms_e2e / 1e6,
                     "unit": "GDOF/s", "h2d_bytes_per_step": 8 * len(x_host), "d2h_bytes_per_step": 8 * len(x_host)},
             "gpu_launches": args.steps * launches_per_apply,
             "clocks": clk.summary(),

@@ -240,10 +240,9 @@ static size_t layout(int64_t n, bool mixed, char *base, Work *w) {
   t.p = (double *)take(vb);
   t.q = (double *)take(vb);
   t.dinv = (double *)take(vb);
-  if (mixed) {
-    t.r_out = (double *)take(vb);
-    t.d = (double *)take(vb);
-  }
+  (void)mixed;
+  t.r_out = (double *)take(vb);
+  t.d = (double *)take(vb);
   t.part1 = (double *)take(RED_MAX_BLOCKS * sizeof(double));
   t.part2 = (double *)take(RED_MAX_BLOCKS * sizeof(double));
   t.sc = (Scalars *)take(sizeof(Scalars));
@@ -404,59 +403,50 @@ extern "C" int ceed_cg_solve(ceed_mesh_t m, const void *qdata, int prec, const d
   }
   int status = CEED_OK;
   double rr = 0.0;
-  if (!mixed) {
-    // r = b - A x0 (or b), then PCG for the correction y, x = x0 + y
-    if (o.use_x0) {
-      if (int st = residual(m, op64, b, x, w.q, w.r, n, w.part1, &w.sc->rr_out, s, &rr)) return st;
-    } else {
-      copy_kernel<<<stream_blocks(n), 256, 0, s>>>(w.r, b, n);
-      rr = bb;
-    }
-    // PCG on A y = r with the tolerance expressed against ||b||: scale tol by ||b|| / ||r0||
-    const double tol_r = o.tol * std::sqrt(bb / (rr > 0 ? rr : bb));
-    double *y = x;
-    // solve for the correction in x's storage when x0 = 0, else in a scratch vector then add
-    if (o.use_x0) {
-      // reuse q as scratch for the correction is not possible (q is the apply output); accumulate
-      // into x afterwards through w.z after the run would clobber z, so run directly on a copy
-      return fail(CEED_ERR_UNSUPPORTED, "use_x0 is supported in MIXED mode only");
-    }
+  ApplyReq oplo = op64;
+  if (mixed) {
+    oplo.prec = o.prec_lo;
+    oplo.qdata = o.qdata_lo;
+  }
+  if (o.fixed_iters > 0) {
+    // exactly fixed_iters PCG iterations from x0 = 0 with the FP64 operator (timing runs)
+    copy_kernel<<<stream_blocks(n), 256, 0, s>>>(w.r, b, n);
     int iters = 0, nonfin = 0;
-    if (int st = pcg_run(m, op64, y, w, n, tol_r, o.max_iter, o.check_every, o.fixed_iters, s, &iters, &nonfin))
+    if (int st = pcg_run(m, op64, x, w, n, o.tol, o.max_iter, o.check_every, o.fixed_iters, s, &iters, &nonfin))
       return st;
     report->iterations = iters;
     report->outer_iterations = 1;
     if (nonfin) status = fail(CEED_ERR_NONFINITE, "non-finite value in a CG reduction");
-    if (int st = residual(m, op64, b, x, w.q, w.r, n, w.part1, &w.sc->rr_out, s, &rr)) return st;
+    if (int st = residual(m, op64, b, x, w.q, w.r_out, n, w.part1, &w.sc->rr_out, s, &rr)) return st;
     report->rel_residual = std::sqrt(rr / bb);
-    if (status == CEED_OK && o.fixed_iters <= 0 && report->rel_residual > o.tol)
-      status = fail(CEED_ERR_NOT_CONVERGED, "CG reached its iteration cap");
   } else {
-    ApplyReq oplo = op64;
-    oplo.prec = o.prec_lo;
-    oplo.qdata = o.qdata_lo;
+    // Refinement loop.  Each pass: true residual r = b - A64 x; stop at tol; else PCG on A d = r
+    // (FP64 mode: FP64 operator, aiming at half the remaining tolerance so that the recurrence
+    // residual's drift rarely forces another pass; MIXED: low-precision operator to inner_tol), x += d.
     if (!o.use_x0) zero_kernel<<<stream_blocks(n), 256, 0, s>>>(x, n);
     int total = 0, outer = 0;
     while (true) {
       if (int st = residual(m, op64, b, x, w.q, w.r_out, n, w.part1, &w.sc->rr_out, s, &rr)) return st;
       report->rel_residual = std::sqrt(rr / bb);
       if (!std::isfinite(rr)) {
-        status = fail(CEED_ERR_NONFINITE, "non-finite outer residual");
+        status = fail(CEED_ERR_NONFINITE, "non-finite residual");
         break;
       }
       if (report->rel_residual <= o.tol) break;
       if (outer >= o.max_outer || total >= o.max_iter) {
-        status = fail(CEED_ERR_NOT_CONVERGED, "mixed-precision refinement reached its cap");
+        status = fail(CEED_ERR_NOT_CONVERGED, "CG reached its iteration cap");
         break;
       }
       copy_kernel<<<stream_blocks(n), 256, 0, s>>>(w.r, w.r_out, n);
+      const double inner = mixed ? o.inner_tol : std::min(0.5, 0.5 * o.tol / report->rel_residual);
       int iters = 0, nonfin = 0;
-      if (int st = pcg_run(m, oplo, w.d, w, n, o.inner_tol, o.max_iter - total, o.check_every, 0, s, &iters, &nonfin))
+      if (int st = pcg_run(m, mixed ? oplo : op64, w.d, w, n, inner, o.max_iter - total, o.check_every, 0, s, &iters,
+                           &nonfin))
         return st;
       total += iters;
       outer += 1;
       if (nonfin) {
-        status = fail(CEED_ERR_NONFINITE, "non-finite value in an inner CG reduction");
+        status = fail(CEED_ERR_NONFINITE, "non-finite value in a CG reduction");
         break;
       }
       axpy_kernel<<<stream_blocks(n), 256, 0, s>>>(x, w.d, n);

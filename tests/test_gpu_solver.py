@@ -56,8 +56,10 @@ def test_cg_fp64_matches_direct_solve(ceed, N, p):
     # the oracle's own PCG on the same system takes a comparable number of iterations
     d = fem.jacobi_diagonal(fem.Space(p, "gll"), m.elem_dofs, fem.qdata_diffusion(fem.Space(p, "gll"), m.vertices, "sine"),
                             fem.DIFFUSION, m.n_ldof, mask=m.boundary)
-    _, it_ref, _, _ = fem.pcg(lambda v: A @ v, bref, 1.0 / d, tol=1e-10, maxit=5000)
+    # the library's FP64 pass aims at half the tolerance (residual-replacement restarts absorb drift)
+    _, it_ref, _, _ = fem.pcg(lambda v: A @ v, bref, 1.0 / d, tol=5e-11, maxit=5000)
     assert abs(rep["iterations"] - it_ref) <= max(3, 0.05 * it_ref)
+    assert rep["outer_iterations"] == 1
     mesh.close()
 
 
