@@ -146,6 +146,13 @@ def ceed_setup_mesh(n_elem, n_ldof, p, elem_dofs, vertices, dirichlet=None, q_ru
     return Mesh(h, n_elem, n_ldof, p, q_rule, ncomp)
 
 
+def ceed_mesh_info(mesh: Mesh):
+    """(n_colors, Q, P) of a mesh handle."""
+    nc, Q, P = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+    _check(_lib.ceed_mesh_info(mesh.handle, ctypes.byref(nc), ctypes.byref(Q), ctypes.byref(P)))
+    return nc.value, Q.value, P.value
+
+
 def ceed_destroy_mesh(mesh: Mesh):
     mesh.close()
 
