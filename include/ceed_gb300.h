@@ -193,6 +193,25 @@ int ceed_apply_diffusion_adjoint(ceed_mesh_t mesh, const double *k, const void *
 size_t ceed_dot_workspace_bytes(int64_t n);
 int ceed_dot(const double *x, const double *y, int64_t n, double *out, void *work, void *stream);
 
+/* Dot product that performs no device allocation and needs no workspace argument.
+ * The paper has no counterpart; this entry point exists for callers that cannot allocate
+ * device memory: a solver library that receives only vector pointers from a host application
+ * which owns all device memory through its own pool, or an iteration loop where cudaMalloc and
+ * cudaFree are unacceptable because they can stall or synchronize the device, or can fail midway
+ * through a solve when memory is tight.
+ * Scratch: a static device array of 32768 FP64 partial sums (256 KiB) that every GPU which loads
+ * the library holds until the process exits.  Each block sums a fixed chunk of 8192 entries, so
+ * n may be at most ceed_dot_noalloc_max_n() = 268,435,456; larger n returns CEED_ERR_INVALID
+ * (use ceed_dot with a workspace instead).  The result is deterministic for a given n; it can
+ * differ from ceed_dot's in the last bits because the chunking differs.
+ * The first call on a device looks up the scratch address on that device (cudaGetSymbolAddress
+ * with the device current); make that first call before any stream capture.  All calls share the
+ * one array and each call overwrites the slots it reads, so nothing has to be cleared, but calls
+ * that may overlap on the GPU (different streams, no ordering between them) race on the scratch
+ * and must be serialized by the caller.  x, y: device FP64 [n]; out: device FP64 scalar. */
+int64_t ceed_dot_noalloc_max_n(void);
+int ceed_dot_noalloc(const double *x, const double *y, int64_t n, double *out, void *stream);
+
 /* Thread-local message for the last failing call on this thread ("" if none). */
 const char *ceed_last_error(void);
 

@@ -77,6 +77,8 @@ def _load():
         "ceed_apply_diffusion_adjoint": (ctypes.c_int, [vp, vp, vp, vp, vp, vp, vp, vp]),
         "ceed_dot_workspace_bytes": (sz, [i64]),
         "ceed_dot": (ctypes.c_int, [vp, vp, i64, vp, vp, vp]),
+        "ceed_dot_noalloc_max_n": (i64, []),
+        "ceed_dot_noalloc": (ctypes.c_int, [vp, vp, i64, vp, vp]),
         "ceed_last_error": (ctypes.c_char_p, []),
     }
     for name, (res, args) in sig.items():
@@ -241,6 +243,19 @@ def ceed_dot_workspace_bytes(n: int) -> int:
 
 def ceed_dot(x, y, out, work, stream=None):
     _check(_lib.ceed_dot(_ptr(x), _ptr(y), x.numel(), _ptr(out), _ptr(work), _stream(stream)))
+
+
+def ceed_dot_noalloc_max_n() -> int:
+    return int(_lib.ceed_dot_noalloc_max_n())
+
+
+def ceed_dot_noalloc(x, y, out, stream=None):
+    """Dot product with no device allocation and no workspace (static scratch inside the library).
+
+    For callers that cannot allocate device memory themselves; see include/ceed_gb300.h for the
+    size limit (n <= ceed_dot_noalloc_max_n()) and the rule that calls must not overlap on the GPU.
+    """
+    _check(_lib.ceed_dot_noalloc(_ptr(x), _ptr(y), x.numel(), _ptr(out), _stream(stream)))
 
 
 def ceed_last_error() -> str:

@@ -8,6 +8,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <mutex>
 
 #include "internal.h"
 
@@ -462,4 +463,69 @@ extern "C" int ceed_cg_solve(ceed_mesh_t m, const void *qdata, int prec, const d
   cudaEventDestroy(ev0);
   cudaEventDestroy(ev1);
   return status;
+}
+
+// ---------------------------------------------------------------------------------------------
+// Dot product that allocates nothing.  The per-block partial sums live in a file-scope device
+// array instead of caller-provided or library-allocated memory.  Each block sums a fixed chunk of
+// CEED_DOT_NOALLOC_CHUNK entries, so the grid (and therefore the rounding order) depends only on n.
+namespace {
+constexpr int64_t NOALLOC_CHUNK = 8192;
+constexpr int NOALLOC_MAX_BLOCKS = 32768;          // 256 KiB of FP64 partial sums
+constexpr int NOALLOC_MAX_DEVICES = 64;
+std::mutex g_noalloc_mu;
+double *g_noalloc_ptr[NOALLOC_MAX_DEVICES] = {};  // device address of the scratch, per device
+}  // namespace
+
+// Present on every device that loads the library, until the process exits.
+static __device__ __align__(256) double g_dot_noalloc_scratch[NOALLOC_MAX_BLOCKS];
+
+namespace ceedgb {
+__global__ void dot_chunk_kernel(const double *__restrict__ x, const double *__restrict__ y, int64_t n,
+                                 double *__restrict__ part) {
+  __shared__ double sh[RED_THREADS];
+  const int64_t base = (int64_t)blockIdx.x * NOALLOC_CHUNK;
+  double a = 0.0;
+  for (int k = threadIdx.x; k < NOALLOC_CHUNK; k += RED_THREADS) {
+    const int64_t i = base + k;
+    if (i < n) a += x[i] * y[i];
+  }
+  a = block_sum(a, sh);
+  if (threadIdx.x == 0) part[blockIdx.x] = a;
+}
+}  // namespace ceedgb
+
+// Host code may not use g_dot_noalloc_scratch as a pointer (that name is a host-side shadow); the
+// device address is looked up once per device, with that device current, and cached.
+static int noalloc_scratch(double **out) {
+  int dev = 0;
+  CEED_CUDA_CHECK(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= NOALLOC_MAX_DEVICES) return fail(CEED_ERR_UNSUPPORTED, "device index beyond 63");
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
+  if (!g_noalloc_ptr[dev]) {
+    void *p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_dot_noalloc_scratch);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(g_dot_noalloc_scratch)");
+    g_noalloc_ptr[dev] = (double *)p;
+  }
+  *out = g_noalloc_ptr[dev];
+  return CEED_OK;
+}
+
+extern "C" int64_t ceed_dot_noalloc_max_n(void) { return (int64_t)NOALLOC_MAX_BLOCKS * NOALLOC_CHUNK; }
+
+extern "C" int ceed_dot_noalloc(const double *x, const double *y, int64_t n, double *out, void *stream) {
+  if (!x || !y || !out || n < 0) return fail(CEED_ERR_INVALID, "bad ceed_dot_noalloc arguments");
+  if (n > ceed_dot_noalloc_max_n())
+    return fail(CEED_ERR_INVALID, "ceed_dot_noalloc: n = " + std::to_string(n) + " exceeds the static scratch limit of " +
+                                      std::to_string(ceed_dot_noalloc_max_n()) + " entries; use ceed_dot");
+  double *scratch = nullptr;
+  if (int st = noalloc_scratch(&scratch)) return st;
+  cudaStream_t s = (cudaStream_t)stream;
+  const int nb = (int)std::max<int64_t>(1, (n + NOALLOC_CHUNK - 1) / NOALLOC_CHUNK);
+  // every block writes its slot before the sum reads it: no clearing is needed between calls
+  dot_chunk_kernel<<<nb, RED_THREADS, 0, s>>>(x, y, n, scratch);
+  sum_partials_kernel<<<1, RED_THREADS, 0, s>>>(scratch, nb, out);
+  CEED_CUDA_CHECK(cudaGetLastError());
+  return CEED_OK;
 }

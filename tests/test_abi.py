@@ -42,3 +42,4 @@ def test_last_error_without_gpu():
     # a call that fails on argument validation touches no device
     assert ceed._lib.ceed_setup_mesh(None, None, None) == ceed.CEED_ERR_INVALID
     assert "null" in ceed.ceed_last_error()
+    assert ceed.ceed_dot_noalloc_max_n() == 32768 * 8192
