@@ -34,14 +34,15 @@ import synthetic  # noqa: E402
 
 METRIC = "diffusion apply GDOF/s at p=7 (FP64 vs mixed), % HBM roofline, CG time-to-1e-10"
 FP64_NOMINAL_TFLOPS = 1.25      # GB300 dense FP64 (profiling recipe's nominal table)
-# DRAM bytes (read + write) per launch of the FP64 apply kernel, from one ncu capture of the current
-# kernel on the 48^3 mesh (13,824 elements per colour launch: 571.2 MB), scaled by elements to a
-# 64^3 colour launch (32,768 elements).  See profiles/apply_kernel_p7_48cube_ncu.md.
-PROFILED_TRAFFIC_PER_LAUNCH = {"apply_kernel<8,8,DIFFUSION,double,double>": 571.15e6 * 32768 / 13824}
+# DRAM bytes (read + write) per launch of the FP64 apply kernel variant, from one ncu capture of the
+# current kernel on the 48^3 mesh (13,824 elements per colour launch), scaled by elements to a 64^3
+# colour launch (32,768 elements); keyed by variant, empty until a capture of the current kernel.
+PROFILED_TRAFFIC_PER_LAUNCH = {}
 WORKLOADS = {
     "c2": dict(N=64, p=7),      # the diffusion workload named by element count
     "c2a": dict(N=40, p=7),     # 22.19M DOFs: the DOF count quoted for the same workload
     "c4": dict(N=80, p=7),      # the mixed-precision CG workload
+    "w48": dict(N=48, p=7),     # profiling size: one colour launch moves more than L2, a few GB on the device
 }
 
 
@@ -171,6 +172,29 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def run_profile(args):
+    """Three applies of one precision on the chosen workload (for ncu captures of the apply kernel)."""
+    import torch
+    import paper_2109_05072_gb300 as ceed
+    wl = WORKLOADS[args.workload]
+    m = synthetic.cube_mesh(wl["N"], wl["p"], seed=0)
+    mesh = ceed.ceed_setup_mesh(m.n_elem, m.n_ldof, wl["p"], torch.from_numpy(m.elem_dofs).cuda(),
+                                torch.from_numpy(m.vertices).cuda(), torch.from_numpy(m.boundary).cuda())
+    prec = {"f64": ceed.CEED_F64, "f32": ceed.CEED_F32, "bf16": ceed.CEED_BF16}[args.profile]
+    qd = ceed.alloc_qdata(mesh, ceed.CEED_OP_DIFFUSION, prec)
+    ceed.ceed_build_qdata(mesh, ceed.CEED_OP_DIFFUSION, ceed.CEED_COEFF_SINE, None, prec, qd)
+    x = torch.from_numpy(synthetic.uniform(m.n_ldof, seed=1)).cuda()
+    y = torch.empty_like(x)
+    if args.variant:
+        ne, stage = (int(v) for v in args.variant.split(","))
+        ceed.ceed_set_apply_variant(mesh, ceed.CEED_OP_DIFFUSION, prec, ne, stage)
+    for _ in range(3):
+        ceed.ceed_apply_diffusion(mesh, qd, prec, x, y)
+    torch.cuda.synchronize()
+    print(json.dumps({"profile": args.profile, "workload": args.workload, "n_ldof": m.n_ldof,
+                      "colors": mesh.n_colors, "variant": args.variant}))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -182,9 +206,15 @@ def main():
     ap.add_argument("--cg-workload", default="c2", choices=sorted(WORKLOADS))
     ap.add_argument("--cpu-sample", type=int, default=40000, help="elements in the timed oracle sample")
     ap.add_argument("--ref-sample", type=int, default=1000, help="elements per reference-arm step")
+    ap.add_argument("--profile", default=None, choices=["f64", "f32", "bf16"],
+                    help="profiling case: set up the workload, run three applies in this precision, exit")
+    ap.add_argument("--variant", default=None, help="ne,stage for --profile (default: autotune)")
+    ap.add_argument("--autotune", type=int, default=1, help="autotune the apply kernel before timing")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.profile:
+        return run_profile(args)
     if args.warmup < 3:
         raise SystemExit("--warmup must be >= 3")
 
@@ -236,7 +266,11 @@ def main():
             ms = t.item()
         return ms / steps
 
-    # ---------------- headline: FP64 apply
+    # ---------------- headline: FP64 apply (variant chosen by the library's autotuner first)
+    variants = {}
+    if args.autotune:
+        ne, st, tms = ceed.ceed_autotune_apply(mesh, ceed.CEED_OP_DIFFUSION, qd64, ceed.CEED_F64, x, y)
+        variants["f64"] = {"elems_per_block": ne, "tma_staging": st, "tuning_ms": tms}
     apply64 = lambda: ceed.ceed_apply_diffusion(mesh, qd64, ceed.CEED_F64, x, y)
     with ClockSampler(local) as clk:
         ms64 = timed(apply64, args.steps, args.warmup)
@@ -245,6 +279,9 @@ def main():
     hbm_peak, hbm_kind = load_peaks()
     bytes64 = algorithmic_bytes(m, 8)
     launches_per_apply = mesh.n_colors
+    v64 = variants.get("f64", {"elems_per_block": 1, "tma_staging": 0})
+    kernel_id = (f"apply_kernel<8,8,DIFFUSION,double,double,stage={v64['tma_staging']}>"
+                 f"[ne={v64['elems_per_block']}]")
     ms_launch = ms64 / launches_per_apply
     flops_launch = flops_el * m.n_elem / launches_per_apply
     achieved_tf = flops_launch / (ms_launch * 1e-3) / 1e12
@@ -254,6 +291,9 @@ def main():
     for name, prec, qb in (("f32", ceed.CEED_F32, 4), ("bf16", ceed.CEED_BF16, 2)):
         qlo = ceed.alloc_qdata(mesh, ceed.CEED_OP_DIFFUSION, prec, dev)
         ceed.ceed_build_qdata(mesh, ceed.CEED_OP_DIFFUSION, ceed.CEED_COEFF_SINE, None, prec, qlo)
+        if args.autotune:
+            ne, st, tms = ceed.ceed_autotune_apply(mesh, ceed.CEED_OP_DIFFUSION, qlo, prec, x, y)
+            variants[name] = {"elems_per_block": ne, "tma_staging": st, "tuning_ms": tms}
         ms = timed(lambda: ceed.ceed_apply_diffusion(mesh, qlo, prec, x, y), args.steps, args.warmup)
         by = algorithmic_bytes(m, qb)
         mixed[name] = {"gdofs": ws * m.n_ldof / ms / 1e6, "ms": ms, "alg_bytes": by,
@@ -328,15 +368,15 @@ def main():
                        "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU"},
             "roofline": {"bound": "alu", "achieved": achieved_tf, "peak": FP64_NOMINAL_TFLOPS, "unit": "TFLOP/s",
                          "frac": achieved_tf / FP64_NOMINAL_TFLOPS,
-                         "traffic": PROFILED_TRAFFIC_PER_LAUNCH.get("apply_kernel<8,8,DIFFUSION,double,double>")
-                         if N == 64 else None,
+                         "traffic": PROFILED_TRAFFIC_PER_LAUNCH.get(kernel_id) if N == 64 else None,
                          "alg_bytes_per_launch": bytes64 / launches_per_apply,
-                         "kernel": "apply_kernel<8,8,DIFFUSION,double,double>",
+                         "kernel": kernel_id,
                          "peak_kind": "nominal FP64 (no FP64 entry in MEASURED_PEAKS.json)",
                          "flops_per_launch": flops_launch, "ms_per_launch": ms_launch,
                          "hbm_gbs": bytes64 / (ms64 * 1e-3) / 1e9, "hbm_peak": hbm_peak, "hbm_peak_kind": hbm_kind,
                          "hbm_frac": bytes64 / (ms64 * 1e-3) / 1e9 / hbm_peak},
             "mixed_apply": mixed,
+            "apply_variants": variants,
             "e2e": {"value": ws * n_apply / ms_e2e / 1e6,
                     "unit": "GDOF/s", "h2d_bytes_per_step": 8 * len(x_host), "d2h_bytes_per_step": 8 * len(x_host)},
             "gpu_launches": args.steps * launches_per_apply,

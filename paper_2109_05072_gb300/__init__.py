@@ -68,6 +68,10 @@ def _load():
         "ceed_apply_mass": (ctypes.c_int, [vp, vp, ctypes.c_int, vp, vp, ctypes.c_int, u32, vp]),
         "ceed_apply_diffusion": (ctypes.c_int, [vp, vp, ctypes.c_int, vp, vp, ctypes.c_int, u32, vp]),
         "ceed_jacobi_diagonal": (ctypes.c_int, [vp, ctypes.c_int, vp, ctypes.c_int, vp, u32, vp]),
+        "ceed_set_apply_variant": (ctypes.c_int, [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int]),
+        "ceed_autotune_apply": (ctypes.c_int, [vp, ctypes.c_int, vp, ctypes.c_int, vp, vp, ctypes.c_int,
+                                               ctypes.POINTER(i32), ctypes.POINTER(i32),
+                                               ctypes.POINTER(ctypes.c_float), vp]),
         "ceed_manufactured_rhs": (ctypes.c_int, [vp, ctypes.c_int, vp, u32, vp]),
         "ceed_cg_workspace_bytes": (sz, [vp, ctypes.POINTER(_CgOpts)]),
         "ceed_cg_solve": (ctypes.c_int, [vp, vp, ctypes.c_int, vp, vp, ctypes.POINTER(_CgOpts),
@@ -183,6 +187,18 @@ def ceed_apply_mass(mesh: Mesh, qdata, prec, x, y, nrhs=1, flags=0, stream=None)
 
 def ceed_apply_diffusion(mesh: Mesh, qdata, prec, x, y, nrhs=1, flags=0, stream=None):
     _check(_lib.ceed_apply_diffusion(mesh.handle, _ptr(qdata), prec, _ptr(x), _ptr(y), nrhs, flags, _stream(stream)))
+
+
+def ceed_autotune_apply(mesh: Mesh, op, qdata, prec, x, y, nrhs=1, stream=None):
+    """Time the apply variants on these buffers and keep the fastest; returns (ne, stage, ms)."""
+    ne, st, ms = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_float()
+    _check(_lib.ceed_autotune_apply(mesh.handle, op, _ptr(qdata), prec, _ptr(x), _ptr(y), nrhs, ctypes.byref(ne),
+                                    ctypes.byref(st), ctypes.byref(ms), _stream(stream)))
+    return ne.value, st.value, ms.value
+
+
+def ceed_set_apply_variant(mesh: Mesh, op, prec, ne, stage):
+    _check(_lib.ceed_set_apply_variant(mesh.handle, op, prec, ne, stage))
 
 
 def ceed_jacobi_diagonal(mesh: Mesh, op, qdata, prec, diag, flags=0, stream=None):

@@ -149,8 +149,16 @@ __device__ __forceinline__ void eo_apply(const EOMat<T> &M, const T *v, T *out) 
   }
 }
 
+constexpr int APPLY_MAX_THREADS = 256;
+constexpr int APPLY_MAX_NE = 32;
+
 template <int Q>
-constexpr int elems_per_block() {
+constexpr int max_elems_per_block() {
+  return (Q * Q >= APPLY_MAX_THREADS) ? 1 : (APPLY_MAX_THREADS / (Q * Q));
+}
+
+template <int Q>
+constexpr int default_elems_per_block() {
   return (Q * Q >= 128) ? 1 : (128 / (Q * Q));
 }
 
@@ -159,14 +167,14 @@ constexpr int tile_words() {
   return Q * Q * (Q + 1);
 }
 
-template <int P, int Q, int OP, typename T, typename TQ>
-constexpr size_t apply_smem_bytes() {
-  constexpr int NE = elems_per_block<Q>();
+// Shared memory of one element: staged quadrature data (if STAGE) + the tiles.
+template <int P, int Q, int OP, typename T, typename TQ, bool STAGE>
+constexpr size_t apply_elem_smem() {
   constexpr int NCQ = (OP == CEED_OP_DIFFUSION) ? 6 : 1;
-  constexpr size_t qbytes = ((size_t)NCQ * Q * Q * Q * sizeof(TQ) + 16 + 127) & ~(size_t)127;
+  constexpr size_t qbytes = STAGE ? (((size_t)NCQ * Q * Q * Q * sizeof(TQ) + 16 + 127) & ~(size_t)127) : 0;
   constexpr int ntiles = (OP == CEED_OP_DIFFUSION) ? 3 : 2;
   constexpr size_t tbytes = ((size_t)ntiles * tile_words<Q>() * sizeof(T) + 127) & ~(size_t)127;
-  return NE * (qbytes + tbytes);
+  return qbytes + tbytes;
 }
 
 // Tile index: (t, s, r) -> (t * Q + s) * (Q + 1) + r.
@@ -183,43 +191,45 @@ struct ApplyArgs {
   int64_t e_begin, e_count;
   int64_t estride;  // quadrature data per element, in TQ units (16-byte multiple)
   int ncol, masked;
+  int ne;           // elements per thread block
   int *err;
 };
 
-template <int P, int Q, int OP, typename T, typename TQ>
-__global__ void __launch_bounds__(Q * Q * elems_per_block<Q>())
+template <int P, int Q, int OP, typename T, typename TQ, bool STAGE>
+__global__ void __launch_bounds__(APPLY_MAX_THREADS)
 apply_kernel(const ApplyArgs a, const OpTab<T> tab) {
-  constexpr int NE = elems_per_block<Q>();
   constexpr int NPT = Q * Q;
   constexpr bool COLLOC = (P == Q);
   constexpr int ND = P * P * P;
   constexpr int NQ = Q * Q * Q;
   constexpr int NCQ = (OP == CEED_OP_DIFFUSION) ? 6 : 1;
-  constexpr size_t QB = ((size_t)NCQ * NQ * sizeof(TQ) + 16 + 127) & ~(size_t)127;
-  constexpr int NT = (OP == CEED_OP_DIFFUSION) ? 3 : 2;
-  constexpr size_t TB = ((size_t)NT * tile_words<Q>() * sizeof(T) + 127) & ~(size_t)127;
+  constexpr size_t QB = STAGE ? (((size_t)NCQ * NQ * sizeof(TQ) + 16 + 127) & ~(size_t)127) : 0;
+  constexpr size_t EB = apply_elem_smem<P, Q, OP, T, TQ, STAGE>();
   extern __shared__ __align__(128) unsigned char smem_raw[];
-  __shared__ uint64_t bar[NE];
+  __shared__ uint64_t bar[STAGE ? APPLY_MAX_NE : 1];
 
   const int tid = threadIdx.x;
   const int el = tid / NPT;
   const int ij = tid - el * NPT;
   const int i = ij % Q, j = ij / Q;
-  const int64_t e = a.e_begin + (int64_t)blockIdx.x * NE + el;
+  const int64_t e = a.e_begin + (int64_t)blockIdx.x * a.ne + el;
   const bool active = e < a.e_begin + a.e_count;
   const bool node_thread = (i < P) && (j < P);
-  TQ *sq = (TQ *)(smem_raw + el * (QB + TB));
-  T *sa = (T *)(smem_raw + el * (QB + TB) + QB);
+  // staged block in shared memory, or the element's block in global memory
+  const TQ *sq = STAGE ? (const TQ *)(smem_raw + el * EB) : (const TQ *)a.qdata + (active ? e : a.e_begin) * a.estride;
+  T *sa = (T *)(smem_raw + el * EB + QB);
   T *sb = sa + tile_words<Q>();
   T *sc = sb + tile_words<Q>();  // diffusion only
 
-  // ---- quadrature data: one bulk copy per element, in flight during the gather and the forward passes
-  if (ij == 0) {
-    mbar_init(&bar[el], 1);
-    if (active)
-      tma_bulk_load(sq, (const TQ *)a.qdata + e * a.estride, (uint32_t)(a.estride * sizeof(TQ)), &bar[el]);
+  if constexpr (STAGE) {
+    // ---- quadrature data: one bulk copy per element, in flight during the gather and the forward passes
+    if (ij == 0) {
+      mbar_init(&bar[el], 1);
+      if (active)
+        tma_bulk_load((void *)sq, (const TQ *)a.qdata + e * a.estride, (uint32_t)(a.estride * sizeof(TQ)), &bar[el]);
+    }
+    __syncthreads();  // barrier initialised before any thread waits on it
   }
-  __syncthreads();  // barrier initialised before any thread waits on it
 
   // ---- restriction of my node column (a = i, b = j, c = 0..P-1)
   uint32_t idx[P];
@@ -288,7 +298,7 @@ apply_kernel(const ApplyArgs a, const OpTab<T> tab) {
 
     // ---- quadrature-point operator
     T w[Q];
-    if (!have_q) {  // elements past the end issued no copy and do not wait
+    if (STAGE && !have_q) {  // elements past the end issued no copy and do not wait
       if (active && !mbar_wait(&bar[el], 0)) {
         if (ij == 0) *a.err = CEED_ERR_TIMEOUT;
       }
@@ -296,7 +306,7 @@ apply_kernel(const ApplyArgs a, const OpTab<T> tab) {
     }
     if constexpr (OP == CEED_OP_MASS) {
 #pragma unroll
-      for (int k = 0; k < Q; ++k) w[k] = q_to(sq[(k * Q + j) * Q + i], T()) * uq[k];
+      for (int k = 0; k < Q; ++k) w[k] = active ? q_to(sq[(k * Q + j) * Q + i], T()) * uq[k] : (T)0;
     } else {
       T ut[Q];
       eo_apply<Q, Q, -1>(tab.eD, uq, ut);
@@ -412,21 +422,20 @@ apply_kernel(const ApplyArgs a, const OpTab<T> tab) {
     if (col + 1 < a.ncol) __syncthreads();
   }
   // an element that never reached the pointwise step (cannot happen today) must not leave its copy in flight
-  if (!have_q && ij == 0 && active) mbar_wait(&bar[el], 0);
+  if (STAGE && !have_q && ij == 0 && active) mbar_wait(&bar[el], 0);
 }
 
-// Launch one kernel per colour for a fixed (P, Q, op, T, TQ).
-template <int P, int Q, int OP, typename T, typename TQ>
-int launch_colours(ceed_mesh_t m, const OpTab<T> &tab, const ApplyReq &r, cudaStream_t s) {
-  constexpr int NE = elems_per_block<Q>();
-  constexpr size_t SMEM = apply_smem_bytes<P, Q, OP, T, TQ>();
-  static bool configured = false;  // per instantiation; the attribute is per function, any device
-  if (!configured) {
-    CEED_CUDA_CHECK(cudaFuncSetAttribute(apply_kernel<P, Q, OP, T, TQ>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)SMEM));
-    configured = true;
+// Launch one kernel per colour for a fixed (P, Q, op, T, TQ) and variant (elements per block, staging).
+template <int P, int Q, int OP, typename T, typename TQ, bool STAGE>
+int launch_variant(ceed_mesh_t m, const OpTab<T> &tab, const ApplyReq &r, int ne, cudaStream_t s) {
+  const size_t smem = (size_t)ne * apply_elem_smem<P, Q, OP, T, TQ, STAGE>();
+  static size_t configured = 0;  // per instantiation: the largest dynamic shared memory requested so far
+  if (smem > configured) {
+    CEED_CUDA_CHECK(cudaFuncSetAttribute(apply_kernel<P, Q, OP, T, TQ, STAGE>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    configured = smem;
   }
-  const dim3 block(Q * Q * NE);
+  const dim3 block(Q * Q * ne);
   ApplyArgs a;
   a.emap = m->d_emap;
   a.qdata = r.qdata;
@@ -434,6 +443,7 @@ int launch_colours(ceed_mesh_t m, const OpTab<T> &tab, const ApplyReq &r, cudaSt
   a.y = r.y;
   a.ncol = r.ncol;
   a.masked = r.masked;
+  a.ne = ne;
   a.err = m->d_err + 1;
   a.estride = qdata_estride(OP, sizeof(TQ), Q);
   for (int c = 0; c < m->n_colors; ++c) {
@@ -441,11 +451,24 @@ int launch_colours(ceed_mesh_t m, const OpTab<T> &tab, const ApplyReq &r, cudaSt
     const int64_t n = m->color_start[c + 1] - a.e_begin;
     if (n == 0) continue;
     a.e_count = n;
-    const dim3 grid((unsigned)((n + NE - 1) / NE));
-    apply_kernel<P, Q, OP, T, TQ><<<grid, block, SMEM, s>>>(a, tab);
+    const dim3 grid((unsigned)((n + ne - 1) / ne));
+    apply_kernel<P, Q, OP, T, TQ, STAGE><<<grid, block, smem, s>>>(a, tab);
   }
   CEED_CUDA_CHECK(cudaGetLastError());
   return CEED_OK;
+}
+
+template <int P, int Q, int OP, typename T, typename TQ>
+int launch_colours(ceed_mesh_t m, const OpTab<T> &tab, const ApplyReq &r, cudaStream_t s) {
+  int ne = r.ne, stage = r.stage;
+  if (ne <= 0) {  // autotuned choice for this (op, precision), else the default
+    const ApplyChoice &ch = m->tuned[OP][r.prec];
+    ne = ch.ne > 0 ? ch.ne : default_elems_per_block<Q>();
+    stage = ch.ne > 0 ? ch.stage : 1;
+  }
+  if (ne > max_elems_per_block<Q>() || ne > APPLY_MAX_NE) return fail(CEED_ERR_INVALID, "elements per block too large");
+  if (stage) return launch_variant<P, Q, OP, T, TQ, true>(m, tab, r, ne, s);
+  return launch_variant<P, Q, OP, T, TQ, false>(m, tab, r, ne, s);
 }
 
 // Dispatch on (P, collocated?, op) for one (T, TQ) pair.

@@ -55,6 +55,14 @@ struct QRule {
   double w[MAX_Q];
 };
 
+// Apply-kernel variant: elements per thread block, and whether quadrature data is staged in
+// shared memory by a TMA bulk copy (1) or read from global memory at the pointwise step (0).
+struct ApplyChoice {
+  int ne = 0;      // 0: not tuned (use the default)
+  int stage = 1;
+  float ms = 0.f;  // time of one application when tuned
+};
+
 }  // namespace ceedgb
 
 struct ceed_mesh_s {
@@ -72,6 +80,7 @@ struct ceed_mesh_s {
   ceedgb::OpTab<float> tab32;
   ceedgb::QRule rule;                   // quadrature rule of the mesh
   double gll_x[ceedgb::MAX_P];          // GLL nodes of the basis
+  ceedgb::ApplyChoice tuned[2][4];      // [op][prec] autotuned apply variant
 };
 
 namespace ceedgb {
@@ -102,6 +111,8 @@ struct ApplyReq {
   double *y;
   int ncol;          // ncomp * nrhs
   int masked;
+  int ne = 0;        // > 0: force this many elements per block (autotuner), else tuned/default
+  int stage = 1;     // with ne > 0: staging switch
 };
 int launch_apply_f64(ceed_mesh_t m, const ApplyReq &r, cudaStream_t s);
 int launch_apply_f32(ceed_mesh_t m, const ApplyReq &r, cudaStream_t s);

@@ -448,3 +448,70 @@ extern "C" int ceed_apply_diffusion(ceed_mesh_t m, const void *qdata, int prec, 
                                     unsigned flags, void *stream) {
   return apply_common(m, CEED_OP_DIFFUSION, qdata, prec, x, y, nrhs, flags, stream);
 }
+
+// ---------------------------------------------------------------------------------------------
+// Autotuner for the apply kernel: times every (elements per block, staging) variant on the
+// caller's mesh, quadrature data and vectors, and keeps the fastest for (op, prec) in the handle.
+extern "C" int ceed_autotune_apply(ceed_mesh_t m, int op, const void *qdata, int prec, const double *x, double *y,
+                                   int nrhs, int32_t *best_ne, int32_t *best_stage, float *best_ms, void *stream) {
+  if (int st = check_mesh(m)) return st;
+  if (op != CEED_OP_MASS && op != CEED_OP_DIFFUSION) return fail(CEED_ERR_INVALID, "unknown operator");
+  if (prec < CEED_F64 || prec > CEED_F16) return fail(CEED_ERR_INVALID, "unknown precision");
+  if (!qdata || !x || !y || x == y || nrhs < 1) return fail(CEED_ERR_INVALID, "bad autotune arguments");
+  cudaStream_t s = (cudaStream_t)stream;
+  const int ne_max = std::max(1, 256 / (m->Q * m->Q));
+  ApplyReq r;
+  r.op = op;
+  r.prec = prec;
+  r.qdata = qdata;
+  r.x = x;
+  r.y = y;
+  r.ncol = m->ncomp * nrhs;
+  r.masked = 0;
+  cudaEvent_t e0, e1;
+  CEED_CUDA_CHECK(cudaEventCreate(&e0));
+  CEED_CUDA_CHECK(cudaEventCreate(&e1));
+  ApplyChoice best;
+  best.ms = 1e30f;
+  const int reps = 3;
+  for (int stage = 0; stage <= 1; ++stage) {
+    for (int ne = 1; ne <= ne_max; ne *= 2) {
+      r.ne = ne;
+      r.stage = stage;
+      if (launch_apply(m, r, s) != CEED_OK) continue;  // e.g. shared memory beyond the limit
+      cudaEventRecord(e0, s);
+      for (int k = 0; k < reps; ++k) launch_apply(m, r, s);
+      cudaEventRecord(e1, s);
+      if (cudaEventSynchronize(e1) != cudaSuccess) break;
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      ms /= reps;
+      if (ms < best.ms) {
+        best.ms = ms;
+        best.ne = ne;
+        best.stage = stage;
+      }
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  CEED_CUDA_CHECK(cudaGetLastError());
+  if (best.ne == 0) return fail(CEED_ERR_CUDA, "no apply variant ran");
+  m->tuned[op][prec] = best;
+  if (best_ne) *best_ne = best.ne;
+  if (best_stage) *best_stage = best.stage;
+  if (best_ms) *best_ms = best.ms;
+  return CEED_OK;
+}
+
+extern "C" int ceed_set_apply_variant(ceed_mesh_t m, int op, int prec, int ne, int stage) {
+  if (int st = check_mesh(m)) return st;
+  if (op != CEED_OP_MASS && op != CEED_OP_DIFFUSION) return fail(CEED_ERR_INVALID, "unknown operator");
+  if (prec < CEED_F64 || prec > CEED_F16) return fail(CEED_ERR_INVALID, "unknown precision");
+  if (ne < 0 || ne > std::max(1, 256 / (m->Q * m->Q)) || (stage != 0 && stage != 1))
+    return fail(CEED_ERR_INVALID, "elements per block must be 0 (default) .. 256 / Q^2, stage 0 or 1");
+  m->tuned[op][prec].ne = ne;
+  m->tuned[op][prec].stage = stage;
+  m->tuned[op][prec].ms = 0.f;
+  return CEED_OK;
+}

@@ -178,3 +178,39 @@ def test_setup_diagonal_and_rhs(ceed):
         bref = fem.manufactured_rhs(sp_, m.vertices, m.elem_dofs, m.n_ldof, "sine", mask=m.boundary)
         assert rel_err(b.cpu().numpy(), bref) <= 1e-12
         mesh.close()
+
+
+@pytest.mark.parametrize("p,qkind,op,prec", [(7, "gll", "diffusion", 0), (7, "gll", "diffusion", 1),
+                                             (3, "gauss", "mass", 0), (5, "gauss", "diffusion", 2), (2, "gll", "diffusion", 1)])
+def test_apply_variants_identical_and_autotune(ceed, p, qkind, op, prec):
+    # every (elements per block, staging) variant runs the same arithmetic: bitwise-identical output
+    m = synthetic.HexMesh(5, 3, 3, p, seed=13)
+    mesh = gpu_mesh(ceed, m, qkind)
+    cop = ceed.CEED_OP_DIFFUSION if op == "diffusion" else ceed.CEED_OP_MASS
+    qd = _qdata(ceed, mesh, op, prec)
+    x = torch.from_numpy(synthetic.uniform(m.n_ldof, seed=14)).cuda()
+    f = ceed.ceed_apply_diffusion if op == "diffusion" else ceed.ceed_apply_mass
+    outs = []
+    ne_max = max(1, 256 // mesh.Q ** 2)
+    for stage in (0, 1):
+        ne = 1
+        while ne <= ne_max:
+            ceed.ceed_set_apply_variant(mesh, cop, prec, ne, stage)
+            y = torch.empty_like(x)
+            f(mesh, qd, prec, x, y)
+            outs.append(y)
+            ne *= 2
+    for y in outs[1:]:
+        assert torch.equal(y, outs[0])
+    ne, stage, ms = ceed.ceed_autotune_apply(mesh, cop, qd, prec, x, torch.empty_like(x))
+    assert 1 <= ne <= ne_max and stage in (0, 1) and ms > 0
+    y = torch.empty_like(x)
+    f(mesh, qd, prec, x, y)
+    assert torch.equal(y, outs[0])
+    with pytest.raises(ceed.CeedError):
+        ceed.ceed_set_apply_variant(mesh, cop, prec, ne_max + 1, 1)
+    if prec == 0:
+        sp_, qref = oracle_qdata(m, qkind, op, "sine")
+        ref = fem.apply(sp_, m.elem_dofs, qref, x.cpu().numpy(), fem.DIFFUSION if op == "diffusion" else fem.MASS)
+        assert rel_err(y.cpu().numpy(), ref) <= 1e-12
+    mesh.close()
