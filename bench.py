@@ -52,9 +52,14 @@ def cost_per_element(p):
     return 7 * P ** 3, 12 * P ** 4 + 15 * P ** 3
 
 
-def algorithmic_bytes(m, qbytes):
-    """x read + y write once per L-node (8 B each), the quadrature data, the int32 restriction."""
-    return 16 * m.n_ldof + 6 * qbytes * m.n_elem * (m.p + 1) ** 3 + 4 * m.n_elem * (m.p + 1) ** 3
+def algorithmic_bytes(m, qbytes, geo=False):
+    """x read + y write once per L-node (8 B each), the quadrature data, the int32 restriction.
+
+    Stored geometry: 6 factors per point.  On-the-fly geometry (geo): 24 FP32 map coefficients per
+    element and one w k value per point."""
+    nd = (m.p + 1) ** 3
+    qd = (24 * 4 + qbytes * nd) * m.n_elem if geo else 6 * qbytes * m.n_elem * nd
+    return 16 * m.n_ldof + qd + 4 * m.n_elem * nd
 
 
 def load_peaks():
@@ -288,14 +293,14 @@ def main():
 
     # ---------------- FP32-arithmetic operator (mixed), FP32 and BF16 quadrature data
     mixed = {}
-    for name, prec, qb in (("f32", ceed.CEED_F32, 4), ("bf16", ceed.CEED_BF16, 2)):
+    for name, prec, qb in (("f32", ceed.CEED_F32, 4), ("bf16", ceed.CEED_BF16, 2), ("f32geo", ceed.CEED_F32_GEO, 4)):
         qlo = ceed.alloc_qdata(mesh, ceed.CEED_OP_DIFFUSION, prec, dev)
         ceed.ceed_build_qdata(mesh, ceed.CEED_OP_DIFFUSION, ceed.CEED_COEFF_SINE, None, prec, qlo)
         if args.autotune:
             ne, st, tms = ceed.ceed_autotune_apply(mesh, ceed.CEED_OP_DIFFUSION, qlo, prec, x, y)
             variants[name] = {"elems_per_block": ne, "tma_staging": st, "tuning_ms": tms}
         ms = timed(lambda: ceed.ceed_apply_diffusion(mesh, qlo, prec, x, y), args.steps, args.warmup)
-        by = algorithmic_bytes(m, qb)
+        by = algorithmic_bytes(m, qb, geo=(prec == ceed.CEED_F32_GEO))
         mixed[name] = {"gdofs": ws * m.n_ldof / ms / 1e6, "ms": ms, "alg_bytes": by,
                        "hbm_gbs": by / (ms * 1e-3) / 1e9, "hbm_frac": by / (ms * 1e-3) / 1e9 / hbm_peak}
         del qlo
@@ -335,7 +340,7 @@ def main():
         st, rep64 = ceed.ceed_cg_solve(mesh, qd64, ceed.CEED_F64, b, xs, mode=ceed.CEED_CG_FP64, tol=1e-10,
                                        max_iter=20000, op=ceed.CEED_OP_DIFFUSION, raise_on_error=False)
         cg["fp64_to_1e-10"] = dict(rep64, status=st)
-        for name, prec in (("f32", ceed.CEED_F32), ("bf16", ceed.CEED_BF16)):
+        for name, prec in (("f32", ceed.CEED_F32), ("bf16", ceed.CEED_BF16), ("f32geo", ceed.CEED_F32_GEO)):
             qlo = ceed.alloc_qdata(mesh, ceed.CEED_OP_DIFFUSION, prec, dev)
             ceed.ceed_build_qdata(mesh, ceed.CEED_OP_DIFFUSION, ceed.CEED_COEFF_SINE, None, prec, qlo)
             st, repm = ceed.ceed_cg_solve(mesh, qd64, ceed.CEED_F64, b, xs, mode=ceed.CEED_CG_MIXED, tol=1e-10,

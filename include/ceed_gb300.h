@@ -46,8 +46,11 @@ typedef enum {
 } ceed_status;
 
 /* Precision of stored quadrature data; it also selects the operator arithmetic:
- * F64 -> FP64 contractions; F32/BF16/F16 -> FP32 contractions (FP64 L-vectors in and out). */
-typedef enum { CEED_F64 = 0, CEED_F32 = 1, CEED_BF16 = 2, CEED_F16 = 3 } ceed_prec;
+ * F64 -> FP64 contractions; F32/BF16/F16 -> FP32 contractions (FP64 L-vectors in and out).
+ * F32_GEO (diffusion only) -> FP32 contractions with the geometric factors recomputed from the
+ * trilinear element map at every application: the quadrature data holds only the map's 8
+ * coefficient vectors per element and w k per point (FP32), about 1/6 of the F32 bytes. */
+typedef enum { CEED_F64 = 0, CEED_F32 = 1, CEED_BF16 = 2, CEED_F16 = 3, CEED_F32_GEO = 4 } ceed_prec;
 
 /* Quadrature: GLL = collocated on the p+1 Gauss-Lobatto nodes (BP5 style, Q = p+1);
  * GAUSS = Q Gauss-Legendre points per direction (BP1/BP3 style, default Q = p+2). */
@@ -155,7 +158,7 @@ typedef struct {
   double tol;             /* stop when ||b - A x||_2 <= tol ||b||_2; 0 -> 1e-10 */
   double inner_tol;       /* MIXED: inner relative reduction; 0 -> 1e-4 */
   const void *qdata_lo;   /* MIXED: quadrature data for the inner operator */
-  int32_t prec_lo;        /* MIXED: its precision (F32, BF16 or F16) */
+  int32_t prec_lo;        /* MIXED: its precision (F32, BF16, F16 or F32_GEO) */
   int32_t use_x0;         /* nonzero: x holds the initial guess; else x0 = 0 */
 } ceed_cg_opts;
 

@@ -167,12 +167,18 @@ constexpr int tile_words() {
   return Q * Q * (Q + 1);
 }
 
+// Quadrature data of one element, in bytes (16-byte multiple; the layout of qdata_estride).
+template <int Q, int OP, typename TQ>
+constexpr size_t qblock_bytes() {
+  constexpr size_t n = (OP == CEED_OP_DIFFUSION) ? 6 * Q * Q * Q : (OP == OP_DIFF_GEO) ? GEO_COEFFS + Q * Q * Q : Q * Q * Q;
+  return (n * sizeof(TQ) + 15) & ~(size_t)15;
+}
+
 // Shared memory of one element: staged quadrature data (if STAGE) + the tiles.
 template <int P, int Q, int OP, typename T, typename TQ, bool STAGE>
 constexpr size_t apply_elem_smem() {
-  constexpr int NCQ = (OP == CEED_OP_DIFFUSION) ? 6 : 1;
-  constexpr size_t qbytes = STAGE ? (((size_t)NCQ * Q * Q * Q * sizeof(TQ) + 16 + 127) & ~(size_t)127) : 0;
-  constexpr int ntiles = (OP == CEED_OP_DIFFUSION) ? 3 : 2;
+  constexpr size_t qbytes = STAGE ? ((qblock_bytes<Q, OP, TQ>() + 127) & ~(size_t)127) : 0;
+  constexpr int ntiles = (OP == CEED_OP_MASS) ? 2 : 3;
   constexpr size_t tbytes = ((size_t)ntiles * tile_words<Q>() * sizeof(T) + 127) & ~(size_t)127;
   return qbytes + tbytes;
 }
@@ -202,8 +208,7 @@ apply_kernel(const ApplyArgs a, const OpTab<T> tab) {
   constexpr bool COLLOC = (P == Q);
   constexpr int ND = P * P * P;
   constexpr int NQ = Q * Q * Q;
-  constexpr int NCQ = (OP == CEED_OP_DIFFUSION) ? 6 : 1;
-  constexpr size_t QB = STAGE ? (((size_t)NCQ * NQ * sizeof(TQ) + 16 + 127) & ~(size_t)127) : 0;
+  constexpr size_t QB = STAGE ? ((qblock_bytes<Q, OP, TQ>() + 127) & ~(size_t)127) : 0;
   constexpr size_t EB = apply_elem_smem<P, Q, OP, T, TQ, STAGE>();
   extern __shared__ __align__(128) unsigned char smem_raw[];
   __shared__ uint64_t bar[STAGE ? APPLY_MAX_NE : 1];
@@ -334,11 +339,55 @@ apply_kernel(const ApplyArgs a, const OpTab<T> tab) {
       __syncthreads();
       // pointwise v = G grad u at my column, in place
       T vt[Q];
+      // on-the-fly geometry: the trilinear map x = a0 + a1 r + a2 s + a3 t + a4 rs + a5 rt + a6 st + a7 rst
+      // gives dx/dr = (a1 + a4 s) + (a5 + a7 s) t, dx/ds = (a2 + a4 r) + (a6 + a7 r) t and
+      // dx/dt = a3 + a5 r + a6 s + a7 rs, so along my column only t varies: 6 FMAs per point for J
+      T c1[3], c1t[3], c2[3], c2t[3], c3[3];
+      if constexpr (OP == OP_DIFF_GEO) {
+        const T xr = tab.qx[i], xs = tab.qx[j];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          const T a1 = q_to(sq[c], T()), a2 = q_to(sq[3 + c], T()), a3 = q_to(sq[6 + c], T());
+          const T a4 = q_to(sq[9 + c], T()), a5 = q_to(sq[12 + c], T()), a6 = q_to(sq[15 + c], T());
+          const T a7 = q_to(sq[18 + c], T());
+          c1[c] = a1 + a4 * xs;
+          c1t[c] = a5 + a7 * xs;
+          c2[c] = a2 + a4 * xr;
+          c2t[c] = a6 + a7 * xr;
+          c3[c] = a3 + a5 * xr + a6 * xs + a7 * xr * xs;
+        }
+      }
 #pragma unroll
       for (int k = 0; k < Q; ++k) {
         const int q = (k * Q + j) * Q + i;
-        const T grr = q_to(sq[q], T()), grs = q_to(sq[NQ + q], T()), grt = q_to(sq[2 * NQ + q], T());
-        const T gss = q_to(sq[3 * NQ + q], T()), gst = q_to(sq[4 * NQ + q], T()), gtt = q_to(sq[5 * NQ + q], T());
+        T grr, grs, grt, gss, gst, gtt;
+        if constexpr (OP == OP_DIFF_GEO) {
+          const T xt = tab.qx[k];
+          T J[3][3];
+#pragma unroll
+          for (int c = 0; c < 3; ++c) {
+            J[c][0] = c1[c] + c1t[c] * xt;
+            J[c][1] = c2[c] + c2t[c] * xt;
+            J[c][2] = c3[c];
+          }
+          // adjugate rows A_a (A J = det I) and G = (w k / det) A A^T
+          const T A00 = J[1][1] * J[2][2] - J[1][2] * J[2][1], A01 = J[0][2] * J[2][1] - J[0][1] * J[2][2];
+          const T A02 = J[0][1] * J[1][2] - J[0][2] * J[1][1], A10 = J[1][2] * J[2][0] - J[1][0] * J[2][2];
+          const T A11 = J[0][0] * J[2][2] - J[0][2] * J[2][0], A12 = J[0][2] * J[1][0] - J[0][0] * J[1][2];
+          const T A20 = J[1][0] * J[2][1] - J[1][1] * J[2][0], A21 = J[0][1] * J[2][0] - J[0][0] * J[2][1];
+          const T A22 = J[0][0] * J[1][1] - J[0][1] * J[1][0];
+          const T det = J[0][0] * A00 + J[0][1] * A10 + J[0][2] * A20;
+          const T f = active ? q_to(sq[GEO_COEFFS + q], T()) / det : (T)0;
+          grr = f * (A00 * A00 + A01 * A01 + A02 * A02);
+          grs = f * (A00 * A10 + A01 * A11 + A02 * A12);
+          grt = f * (A00 * A20 + A01 * A21 + A02 * A22);
+          gss = f * (A10 * A10 + A11 * A11 + A12 * A12);
+          gst = f * (A10 * A20 + A11 * A21 + A12 * A22);
+          gtt = f * (A20 * A20 + A21 * A21 + A22 * A22);
+        } else {
+          grr = q_to(sq[q], T()), grs = q_to(sq[NQ + q], T()), grt = q_to(sq[2 * NQ + q], T());
+          gss = q_to(sq[3 * NQ + q], T()), gst = q_to(sq[4 * NQ + q], T()), gtt = q_to(sq[5 * NQ + q], T());
+        }
         const T ur = sb[tix<Q>(k, j, i)], us = sc[tix<Q>(k, j, i)];
         sb[tix<Q>(k, j, i)] = grr * ur + grs * us + grt * ut[k];
         sc[tix<Q>(k, j, i)] = grs * ur + gss * us + gst * ut[k];
@@ -462,7 +511,7 @@ template <int P, int Q, int OP, typename T, typename TQ>
 int launch_colours(ceed_mesh_t m, const OpTab<T> &tab, const ApplyReq &r, cudaStream_t s) {
   int ne = r.ne, stage = r.stage;
   if (ne <= 0) {  // autotuned choice for this (op, precision), else the default
-    const ApplyChoice &ch = m->tuned[OP][r.prec];
+    const ApplyChoice &ch = m->tuned[r.op][r.prec];
     ne = ch.ne > 0 ? ch.ne : default_elems_per_block<Q>();
     stage = ch.ne > 0 ? ch.stage : 1;
   }

@@ -362,8 +362,9 @@ extern "C" int ceed_cg_solve(ceed_mesh_t m, const void *qdata, int prec, const d
   ceed_cg_opts o;
   fill_defaults(opts_in, &o);
   const bool mixed = o.mode == CEED_CG_MIXED;
-  if (mixed && (!o.qdata_lo || (o.prec_lo != CEED_F32 && o.prec_lo != CEED_BF16 && o.prec_lo != CEED_F16)))
-    return fail(CEED_ERR_INVALID, "MIXED mode needs qdata_lo in F32, BF16 or F16");
+  if (mixed && (!o.qdata_lo || (o.prec_lo != CEED_F32 && o.prec_lo != CEED_BF16 && o.prec_lo != CEED_F16 &&
+                                 o.prec_lo != CEED_F32_GEO)))
+    return fail(CEED_ERR_INVALID, "MIXED mode needs qdata_lo in F32, BF16, F16 or F32_GEO");
   if (o.op != CEED_OP_MASS && o.op != CEED_OP_DIFFUSION) return fail(CEED_ERR_INVALID, "unknown operator");
   const int64_t n = m->n_ldof;
   if (work_bytes < layout(n, mixed, nullptr, nullptr)) return fail(CEED_ERR_INVALID, "workspace too small");

@@ -40,13 +40,19 @@ struct OpTab {
   T B[MAX_Q * MAX_P];   // B[q * P + a] = l_a(xi_q): GLL Lagrange basis at the quadrature points
   T D[MAX_Q * MAX_Q];   // D[i * Q + m] = derivative at xi_i of the Lagrange basis on the Q points
   EOMat<T> eB, eBT, eD, eDT;  // even-odd forms of B (Q x P), B^T, D (Q x Q), D^T
+  T qx[MAX_Q];                 // quadrature points (reference coordinates)
 };
+
+// Internal operator id of the diffusion operator whose geometric factors are recomputed from the
+// trilinear map at every application (quadrature data: 24 map coefficients + w k per point).
+constexpr int OP_DIFF_GEO = 2;
+constexpr int GEO_COEFFS = 24;   // a1..a7 (21 floats) + 3 pad
 
 // Quadrature data layout: [colour-sorted element][component][Q^3], each element block padded to a
 // multiple of 16 bytes so that it can be moved by one TMA bulk copy.
 __host__ __device__ inline int64_t qdata_estride(int op, size_t elem_bytes, int Q) {
-  const int64_t nc = (op == CEED_OP_DIFFUSION) ? 6 : 1;
-  const int64_t b = nc * Q * Q * Q * (int64_t)elem_bytes;
+  const int64_t n = (op == CEED_OP_DIFFUSION) ? 6 * Q * Q * Q : (op == OP_DIFF_GEO) ? GEO_COEFFS + Q * Q * Q : Q * Q * Q;
+  const int64_t b = n * (int64_t)elem_bytes;
   return ((b + 15) / 16) * 16 / (int64_t)elem_bytes;
 }
 
@@ -80,7 +86,7 @@ struct ceed_mesh_s {
   ceedgb::OpTab<float> tab32;
   ceedgb::QRule rule;                   // quadrature rule of the mesh
   double gll_x[ceedgb::MAX_P];          // GLL nodes of the basis
-  ceedgb::ApplyChoice tuned[2][4];      // [op][prec] autotuned apply variant
+  ceedgb::ApplyChoice tuned[3][5];      // [op][prec] autotuned apply variant
 };
 
 namespace ceedgb {
@@ -116,6 +122,7 @@ struct ApplyReq {
 };
 int launch_apply_f64(ceed_mesh_t m, const ApplyReq &r, cudaStream_t s);
 int launch_apply_f32(ceed_mesh_t m, const ApplyReq &r, cudaStream_t s);
+int launch_apply_qf32geo(ceed_mesh_t m, const ApplyReq &r, cudaStream_t s);
 int launch_apply(ceed_mesh_t m, const ApplyReq &r, cudaStream_t s);
 
 }  // namespace ceedgb

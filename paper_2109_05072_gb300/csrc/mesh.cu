@@ -202,6 +202,10 @@ static void build_tables(ceed_mesh_s *m) {
   make_eo(BT, P, Q, +1, &m->tab64.eBT, &m->tab32.eBT);
   make_eo(D, Q, Q, -1, &m->tab64.eD, &m->tab32.eD);
   make_eo(DT, Q, Q, -1, &m->tab64.eDT, &m->tab32.eDT);
+  for (int i = 0; i < Q; ++i) {
+    m->tab64.qx[i] = m->rule.x[i];
+    m->tab32.qx[i] = (float)m->rule.x[i];
+  }
 }
 
 int launch_apply(ceed_mesh_t m, const ApplyReq &r, cudaStream_t s);
@@ -220,6 +224,10 @@ int launch_apply_f32(ceed_mesh_t m, const ApplyReq &r, cudaStream_t s) {
 
 int launch_apply(ceed_mesh_t m, const ApplyReq &r, cudaStream_t s) {
   if (r.prec == CEED_F64) return launch_apply_f64(m, r, s);
+  if (r.prec == CEED_F32_GEO) {
+    if (r.op != CEED_OP_DIFFUSION) return fail(CEED_ERR_UNSUPPORTED, "F32_GEO quadrature data is for diffusion");
+    return launch_apply_qf32geo(m, r, s);
+  }
   return launch_apply_f32(m, r, s);
 }
 
@@ -406,7 +414,8 @@ extern "C" int ceed_mesh_info(ceed_mesh_t m, int32_t *n_colors, int32_t *Q, int3
 size_t ceedgb::prec_size(int prec) {
   switch (prec) {
     case CEED_F64: return 8;
-    case CEED_F32: return 4;
+    case CEED_F32:
+    case CEED_F32_GEO: return 4;
     case CEED_BF16:
     case CEED_F16: return 2;
     default: return 0;
@@ -415,6 +424,10 @@ size_t ceedgb::prec_size(int prec) {
 
 extern "C" size_t ceed_qdata_bytes(ceed_mesh_t m, int op, int prec) {
   if (!m || prec_size(prec) == 0 || (op != CEED_OP_MASS && op != CEED_OP_DIFFUSION)) return 0;
+  if (prec == CEED_F32_GEO) {
+    if (op != CEED_OP_DIFFUSION) return 0;
+    op = OP_DIFF_GEO;
+  }
   return (size_t)m->E * qdata_estride(op, prec_size(prec), m->Q) * prec_size(prec);
 }
 
@@ -425,8 +438,7 @@ static int apply_common(ceed_mesh_t m, int op, const void *qdata, int prec, cons
   if (x == y) return fail(CEED_ERR_INVALID, "x and y must not alias");
   if (nrhs < 1) return fail(CEED_ERR_INVALID, "nrhs must be >= 1");
   if (prec_size(prec) == 0) return fail(CEED_ERR_INVALID, "unknown precision");
-  if (prec != CEED_F64 && prec != CEED_F32 && prec != CEED_BF16 && prec != CEED_F16)
-    return fail(CEED_ERR_INVALID, "unknown precision");
+  if (prec < CEED_F64 || prec > CEED_F32_GEO) return fail(CEED_ERR_INVALID, "unknown precision");
   ApplyReq r;
   r.op = op;
   r.prec = prec;
@@ -456,7 +468,7 @@ extern "C" int ceed_autotune_apply(ceed_mesh_t m, int op, const void *qdata, int
                                    int nrhs, int32_t *best_ne, int32_t *best_stage, float *best_ms, void *stream) {
   if (int st = check_mesh(m)) return st;
   if (op != CEED_OP_MASS && op != CEED_OP_DIFFUSION) return fail(CEED_ERR_INVALID, "unknown operator");
-  if (prec < CEED_F64 || prec > CEED_F16) return fail(CEED_ERR_INVALID, "unknown precision");
+  if (prec < CEED_F64 || prec > CEED_F32_GEO) return fail(CEED_ERR_INVALID, "unknown precision");
   if (!qdata || !x || !y || x == y || nrhs < 1) return fail(CEED_ERR_INVALID, "bad autotune arguments");
   cudaStream_t s = (cudaStream_t)stream;
   const int ne_max = std::max(1, 256 / (m->Q * m->Q));
@@ -507,7 +519,7 @@ extern "C" int ceed_autotune_apply(ceed_mesh_t m, int op, const void *qdata, int
 extern "C" int ceed_set_apply_variant(ceed_mesh_t m, int op, int prec, int ne, int stage) {
   if (int st = check_mesh(m)) return st;
   if (op != CEED_OP_MASS && op != CEED_OP_DIFFUSION) return fail(CEED_ERR_INVALID, "unknown operator");
-  if (prec < CEED_F64 || prec > CEED_F16) return fail(CEED_ERR_INVALID, "unknown precision");
+  if (prec < CEED_F64 || prec > CEED_F32_GEO) return fail(CEED_ERR_INVALID, "unknown precision");
   if (ne < 0 || ne > std::max(1, 256 / (m->Q * m->Q)) || (stage != 0 && stage != 1))
     return fail(CEED_ERR_INVALID, "elements per block must be 0 (default) .. 256 / Q^2, stage 0 or 1");
   m->tuned[op][prec].ne = ne;

@@ -56,6 +56,49 @@ __global__ void qdata_kernel(int64_t E, int Q, const double *__restrict__ vert, 
   }
 }
 
+// Quadrature data for the on-the-fly-geometry FP32 diffusion operator: per element the
+// coefficients a1..a7 of the trilinear map x = a0 + a1 r + a2 s + a3 t + a4 rs + a5 rt + a6 st +
+// a7 rst (computed in FP64 from the 8 vertices, stored FP32), then w_q k_q at every point.
+__global__ void geo_qdata_kernel(int64_t E, int Q, const double *__restrict__ vert, const int32_t *__restrict__ perm,
+                                 int coeff_kind, double cconst, const double *__restrict__ coeff, QRule rule,
+                                 float *__restrict__ out, int64_t estride, int *err) {
+  const int nq = Q * Q * Q;
+  const int64_t total = E * nq;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t s = t / nq;
+    const int q = (int)(t - s * nq);
+    const int i = q % Q, j = (q / Q) % Q, k = q / (Q * Q);
+    const double *V = vert + s * 24;
+    if (q == 0) {
+      for (int c = 0; c < 3; ++c) {
+        double a[7] = {0, 0, 0, 0, 0, 0, 0};
+        for (int v = 0; v < 8; ++v) {
+          const double sr = (v & 1) ? 1.0 : -1.0, ss = (v & 2) ? 1.0 : -1.0, st = (v & 4) ? 1.0 : -1.0;
+          const double xv = 0.125 * V[v * 3 + c];
+          a[0] += sr * xv;
+          a[1] += ss * xv;
+          a[2] += st * xv;
+          a[3] += sr * ss * xv;
+          a[4] += sr * st * xv;
+          a[5] += ss * st * xv;
+          a[6] += sr * ss * st * xv;
+        }
+        for (int n = 0; n < 7; ++n) out[s * estride + n * 3 + c] = (float)a[n];
+      }
+      for (int n = 21; n < GEO_COEFFS; ++n) out[s * estride + n] = 0.f;
+    }
+    double X[3], J[3][3], A[3][3];
+    trilinear_map(V, rule.x[i], rule.x[j], rule.x[k], X, J);
+    const double det = adjugate(J, A);
+    if (!(det > 0.0)) *err = CEED_ERR_BAD_GEOMETRY;
+    double kq = 1.0;
+    if (coeff_kind == CEED_COEFF_CONST) kq = cconst;
+    else if (coeff_kind == CEED_COEFF_SINE) kq = sine_coefficient(X);
+    else if (coeff_kind == CEED_COEFF_PER_QPT) kq = coeff[(int64_t)perm[s] * nq + q];
+    out[s * estride + GEO_COEFFS + q] = (float)(rule.w[i] * rule.w[j] * rule.w[k] * kq);
+  }
+}
+
 // Per-element vector assembled with the same atomic-free colour scheme as the apply.
 // mode 0: manufactured RHS b_i = sum_q w |det J| f(x_q) phi_i(x_q)
 // mode 1: Jacobi diagonal of the mass operator, sum_q qd_q phi_i(x_q)^2
@@ -193,6 +236,11 @@ static int build_qdata_impl(ceed_mesh_t m, int op, int coeff_kind, const double 
   const int threads = 256;
   const int64_t total = m->E * nq_of(m);
   const unsigned blocks = (unsigned)std::min<int64_t>((total + threads - 1) / threads, 152 * 64);
+  if (prec == CEED_F32_GEO) {
+    if (op != CEED_OP_DIFFUSION) return fail(CEED_ERR_UNSUPPORTED, "F32_GEO quadrature data is for diffusion");
+    geo_qdata_kernel<<<blocks, threads, 0, s>>>(m->E, m->Q, m->d_vertices, m->d_perm, coeff_kind, cconst, coeff, m->rule,
+                                                (float *)qdata, qdata_estride(OP_DIFF_GEO, 4, m->Q), m->d_err);
+  } else {
 #define CEEDGB_Q(TQ)                                                                                      \
   qdata_kernel<TQ><<<blocks, threads, 0, s>>>(m->E, m->Q, m->d_vertices, m->d_perm, op, coeff_kind, cconst, \
                                               coeff, m->rule, (TQ *)qdata, qdata_estride(op, sizeof(TQ), m->Q), \
@@ -205,6 +253,7 @@ static int build_qdata_impl(ceed_mesh_t m, int op, int coeff_kind, const double 
     default: return fail(CEED_ERR_INVALID, "unknown precision");
   }
 #undef CEEDGB_Q
+  }
   CEED_CUDA_CHECK(cudaGetLastError());
   int err = 0;
   CEED_CUDA_CHECK(cudaMemcpyAsync(&err, m->d_err, sizeof(int), cudaMemcpyDeviceToHost, s));

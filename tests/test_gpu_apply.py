@@ -60,7 +60,9 @@ def test_apply_fp64_matches_oracle(ceed, p, qkind, op):
 
 @pytest.mark.parametrize("p,qkind,op,prec,bound", [
     (7, "gll", "diffusion", 1, 64 * 8 * 2 ** -24), (3, "gauss", "mass", 1, 64 * 4 * 2 ** -24),
-    (7, "gll", "diffusion", 2, 2e-2), (7, "gll", "diffusion", 3, 2e-3), (4, "gauss", "diffusion", 1, 64 * 5 * 2 ** -24)])
+    (7, "gll", "diffusion", 2, 2e-2), (7, "gll", "diffusion", 3, 2e-3), (4, "gauss", "diffusion", 1, 64 * 5 * 2 ** -24),
+    (7, "gll", "diffusion", 4, 64 * 8 * 2 ** -24), (3, "gauss", "diffusion", 4, 64 * 4 * 2 ** -24),
+    (1, "gll", "diffusion", 4, 64 * 2 * 2 ** -24), (8, "gauss", "diffusion", 4, 64 * 9 * 2 ** -24)])
 def test_apply_lowprec_error_bound(ceed, p, qkind, op, prec, bound):
     m = synthetic.HexMesh(3, 3, 2, p, seed=3)
     mesh = gpu_mesh(ceed, m, qkind)
@@ -181,7 +183,8 @@ def test_setup_diagonal_and_rhs(ceed):
 
 
 @pytest.mark.parametrize("p,qkind,op,prec", [(7, "gll", "diffusion", 0), (7, "gll", "diffusion", 1),
-                                             (3, "gauss", "mass", 0), (5, "gauss", "diffusion", 2), (2, "gll", "diffusion", 1)])
+                                             (3, "gauss", "mass", 0), (5, "gauss", "diffusion", 2), (2, "gll", "diffusion", 1),
+                                             (7, "gll", "diffusion", 4), (4, "gauss", "diffusion", 4)])
 def test_apply_variants_identical_and_autotune(ceed, p, qkind, op, prec):
     # every (elements per block, staging) variant runs the same arithmetic: bitwise-identical output
     m = synthetic.HexMesh(5, 3, 3, p, seed=13)

@@ -63,7 +63,7 @@ def test_cg_fp64_matches_direct_solve(ceed, N, p):
     mesh.close()
 
 
-@pytest.mark.parametrize("prec_lo", [1, 2, 3])
+@pytest.mark.parametrize("prec_lo", [1, 2, 3, 4])
 def test_mixed_refinement_reaches_fp64_tolerance(ceed, prec_lo):
     N, p = 3, 5
     m, mesh, qd, b = _setup(ceed, N, p)
