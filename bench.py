@@ -200,6 +200,86 @@ def run_profile(args):
                       "colors": mesh.n_colors, "variant": args.variant}))
 
 
+def _time_cuda(fn, steps, warmup):
+    import torch
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(steps):
+        fn()
+    e1.record()
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / steps
+
+
+def run_batched(ceed, dev, args):
+    """Three independent meshes of order 3, 5, 7 (Gauss q = p+2: 5, 7, 9 points) on 48^3, 40^3, 32^3
+    elements, 3-component diffusion, FP64, applied by one persistent launch replayed from a CUDA graph."""
+    import torch
+    specs = [(3, 48), (5, 40), (7, 32)]
+    meshes, qds, nodes = [], [], []
+    for p, N in specs:
+        m = synthetic.cube_mesh(N, p, seed=0)
+        mesh = ceed.ceed_setup_mesh(m.n_elem, m.n_ldof, p, torch.from_numpy(m.elem_dofs).to(dev),
+                                    torch.from_numpy(m.vertices).to(dev), None, q_rule=ceed.CEED_QRULE_GAUSS, ncomp=3)
+        qd = ceed.alloc_qdata(mesh, ceed.CEED_OP_DIFFUSION, ceed.CEED_F64, dev)
+        ceed.ceed_build_qdata(mesh, ceed.CEED_OP_DIFFUSION, ceed.CEED_COEFF_SINE, None, ceed.CEED_F64, qd)
+        meshes.append(mesh)
+        qds.append(qd)
+        nodes.append(m.n_ldof)
+    out = {"meshes": [f"p={p}, {N}^3, Gauss q={p + 2}, n_ldof={n}" for (p, N), n in zip(specs, nodes)],
+           "ncomp": 3, "dtype": "f64", "runs": []}
+    for nrhs in (1, 4, 16):
+        xs = [torch.from_numpy(synthetic.uniform(n * 3 * nrhs, seed=7 + k)).to(dev) for k, n in enumerate(nodes)]
+        ys = [torch.empty_like(x) for x in xs]
+        batch = ceed.ceed_batch_create(meshes, qds, ceed.CEED_F64, ceed.CEED_OP_DIFFUSION, xs, ys, nrhs=nrhs)
+        ceed.ceed_batch_autotune(batch)
+        threads, stage, grid = ceed.ceed_batch_info(batch)
+        ms = _time_cuda(lambda: ceed.ceed_batch_apply(batch), 5, 3)
+        ceed.ceed_batch_status(batch)
+        dofs = sum(nodes) * 3 * nrhs
+        out["runs"].append({"nrhs": nrhs, "ms_per_apply": ms, "gdofs": dofs / ms / 1e6, "threads": threads,
+                            "tma_staging": stage, "grid": grid, "launches_per_apply": 1})
+        batch.close()
+        del xs, ys
+        torch.cuda.empty_cache()
+    for mesh in meshes:
+        mesh.close()
+    return out
+
+
+def run_adjoint(ceed, dev, args):
+    """Forward A(k) x and the fused adjoint (dL/dx, dL/dk) with a lognormal per-point k, p = 4 and 8 on
+    32^3 elements (GLL collocated), geometry stored vs recomputed from the vertices."""
+    import torch
+    out = []
+    for p in (4, 8):
+        m = synthetic.cube_mesh(32, p, seed=0)
+        mesh = ceed.ceed_setup_mesh(m.n_elem, m.n_ldof, p, torch.from_numpy(m.elem_dofs).to(dev),
+                                    torch.from_numpy(m.vertices).to(dev), None)
+        nq = (p + 1) ** 3
+        k = torch.from_numpy(synthetic.lognormal(m.n_elem * nq, seed=3, sigma=0.5)).to(dev)
+        x = torch.from_numpy(synthetic.uniform(m.n_ldof, seed=4)).to(dev)
+        r = torch.from_numpy(synthetic.uniform(m.n_ldof, seed=5)).to(dev)
+        y = torch.empty_like(x)
+        dLdk = torch.empty_like(k)
+        geo = ceed.alloc_qdata(mesh, ceed.CEED_OP_DIFFUSION, ceed.CEED_F64, dev)
+        ceed.ceed_build_geometry(mesh, geo)
+        row = {"p": p, "mesh": "32^3", "n_ldof": m.n_ldof, "n_qpts": m.n_elem * nq}
+        for name, g in (("stored", geo), ("recomputed", None)):
+            ms_f = _time_cuda(lambda: ceed.ceed_apply_diffusion_k(mesh, k, g, x, y), 5, 3)
+            ms_a = _time_cuda(lambda: ceed.ceed_apply_diffusion_adjoint(mesh, k, g, x, r, y, dLdk), 5, 3)
+            row[name] = {"forward_ms": ms_f, "adjoint_ms": ms_a, "forward_gdofs": m.n_ldof / ms_f / 1e6,
+                         "adjoint_gdofs": m.n_ldof / ms_a / 1e6}
+        out.append(row)
+        mesh.close()
+        del geo, k, x, r, y, dLdk
+        torch.cuda.empty_cache()
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -215,6 +295,8 @@ def main():
                     help="profiling case: set up the workload, run three applies in this precision, exit")
     ap.add_argument("--variant", default=None, help="ne,stage for --profile (default: autotune)")
     ap.add_argument("--autotune", type=int, default=1, help="autotune the apply kernel before timing")
+    ap.add_argument("--batched", type=int, default=1, help="measure the batched mixed-order apply")
+    ap.add_argument("--adjoint", type=int, default=1, help="measure the adjoint kernels")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -352,6 +434,16 @@ def main():
             del qlo
         cg["workload"] = f"{WORKLOADS[args.cg_workload]['N']}^3, p=7, n_ldof={m.n_ldof}"
 
+    # ---------------- batched apply: p = 3, 5, 7 meshes (Gauss q = p+2), 3 components, 1..16 RHS, one launch
+    batched = None
+    if args.batched:
+        batched = run_batched(ceed, dev, args)
+
+    # ---------------- adjoint: L = 0.5 ||A(k) x - b||^2, p = 4 and 8 on 32^3, geometry stored vs recomputed
+    adjoint = None
+    if args.adjoint:
+        adjoint = run_adjoint(ceed, dev, args)
+
     # ---------------- CPU oracle on a bounded sample (rank 0, N = 1 only)
     cpu = None
     if rank == 0 and ws == 1 and args.cpu_sample > 0:
@@ -387,6 +479,8 @@ def main():
             "gpu_launches": args.steps * launches_per_apply,
             "clocks": clk.summary(),
             "cg": cg,
+            "batched": batched,
+            "adjoint": adjoint,
             "cpu_baseline": cpu,
         }
         print(json.dumps(line), flush=True)

@@ -144,6 +144,33 @@ int ceed_jacobi_diagonal(ceed_mesh_t mesh, int op, const void *qdata, int prec, 
  * b: device FP64 [n_ldof] (ncomp must be 1). */
 int ceed_manufactured_rhs(ceed_mesh_t mesh, int coeff_kind, double *b, unsigned flags, void *stream);
 
+/* ---------------------------------------------------------------- batched apply */
+
+/* Several independent meshes -- polynomial orders may differ -- applied by ONE persistent kernel
+ * launch (multi-right-hand-side batching and mixed order in one launch).  The launch is sized to the
+ * thread blocks that are co-resident on the GPU; each block loops over the colours and over its share
+ * of every mesh's elements of that colour, with a bounded grid-wide barrier between colours (the
+ * atomic-free scatter needs colours in sequence).  The launch is captured once into a CUDA graph and
+ * replayed by ceed_batch_apply.  Buffers are fixed at creation: qdata[k] (built for meshes[k] in
+ * `prec`), x[k], y[k] (FP64, [n_ldof * ncomp * nrhs] of mesh k).  All meshes must use the same
+ * quadrature rule kind (GLL or Gauss).  Supported: F64 mass/diffusion, F32 diffusion.  The batch must
+ * not run concurrently with other kernels on the device (the persistent grid assumes it has the GPU);
+ * if a barrier wait times out, ceed_batch_status returns CEED_ERR_TIMEOUT. */
+typedef struct ceed_batch_s *ceed_batch_t;
+int ceed_batch_create(int n, const ceed_mesh_t *meshes, const void *const *qdata, int prec, int op,
+                      const double *const *x, double *const *y, int nrhs, ceed_batch_t *out);
+/* y[k] = A_k x[k] for every mesh of the batch, one graph launch on `stream`. */
+int ceed_batch_apply(ceed_batch_t batch, void *stream);
+/* Autotuner: times threads per block (128, 192, 256; elements per block = threads / Q^2 for each
+ * mesh) x quadrature-data staging on the batch's own buffers, keeps the fastest and re-captures the
+ * graph.  Synchronizes `stream`. */
+int ceed_batch_autotune(ceed_batch_t batch, float *best_ms, void *stream);
+/* Launch shape in use: threads per block, staging, blocks in the persistent grid. */
+int ceed_batch_info(ceed_batch_t batch, int32_t *threads, int32_t *stage, uint32_t *grid);
+/* Synchronizes `stream`; CEED_ERR_TIMEOUT if a bounded device wait of an earlier launch gave up. */
+int ceed_batch_status(ceed_batch_t batch, void *stream);
+int ceed_batch_destroy(ceed_batch_t batch);
+
 /* ---------------------------------------------------------------- CG solver */
 
 typedef enum { CEED_CG_FP64 = 0, CEED_CG_MIXED = 1 } ceed_cg_mode;

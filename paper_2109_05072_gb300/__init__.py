@@ -79,6 +79,14 @@ def _load():
         "ceed_build_geometry": (ctypes.c_int, [vp, vp, vp]),
         "ceed_apply_diffusion_k": (ctypes.c_int, [vp, vp, vp, vp, vp, u32, vp]),
         "ceed_apply_diffusion_adjoint": (ctypes.c_int, [vp, vp, vp, vp, vp, vp, vp, vp]),
+        "ceed_batch_create": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.c_int,
+                                             ctypes.c_int, ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.c_int,
+                                             ctypes.POINTER(vp)]),
+        "ceed_batch_apply": (ctypes.c_int, [vp, vp]),
+        "ceed_batch_autotune": (ctypes.c_int, [vp, ctypes.POINTER(ctypes.c_float), vp]),
+        "ceed_batch_info": (ctypes.c_int, [vp, ctypes.POINTER(i32), ctypes.POINTER(i32), ctypes.POINTER(ctypes.c_uint32)]),
+        "ceed_batch_status": (ctypes.c_int, [vp, vp]),
+        "ceed_batch_destroy": (ctypes.c_int, [vp]),
         "ceed_dot_workspace_bytes": (sz, [i64]),
         "ceed_dot": (ctypes.c_int, [vp, vp, i64, vp, vp, vp]),
         "ceed_dot_noalloc_max_n": (i64, []),
@@ -238,6 +246,58 @@ def ceed_cg_solve(mesh: Mesh, qdata, prec, b, x, work=None, stream=None, raise_o
     if raise_on_error and st not in (CEED_OK,):
         raise CeedError(st, _lib.ceed_last_error().decode())
     return st, report
+
+
+class Batch:
+    """Owns a ceed_batch_t and keeps its meshes and buffers alive."""
+
+    def __init__(self, handle, keep):
+        self.handle, self._keep = handle, keep
+
+    def close(self):
+        if self.handle:
+            _lib.ceed_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def ceed_batch_create(meshes, qdata, prec, op, xs, ys, nrhs=1) -> Batch:
+    n = len(meshes)
+    arr = lambda items: (ctypes.c_void_p * n)(*items)
+    h = ctypes.c_void_p()
+    _check(_lib.ceed_batch_create(n, arr([m.handle for m in meshes]), arr([_ptr(q).value for q in qdata]), prec, op,
+                                  arr([_ptr(x).value for x in xs]), arr([_ptr(y).value for y in ys]), nrhs,
+                                  ctypes.byref(h)))
+    return Batch(h, (list(meshes), list(qdata), list(xs), list(ys)))
+
+
+def ceed_batch_apply(batch: Batch, stream=None):
+    _check(_lib.ceed_batch_apply(batch.handle, _stream(stream)))
+
+
+def ceed_batch_autotune(batch: Batch, stream=None) -> float:
+    ms = ctypes.c_float()
+    _check(_lib.ceed_batch_autotune(batch.handle, ctypes.byref(ms), _stream(stream)))
+    return ms.value
+
+
+def ceed_batch_info(batch: Batch):
+    t, st, g = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_uint32()
+    _check(_lib.ceed_batch_info(batch.handle, ctypes.byref(t), ctypes.byref(st), ctypes.byref(g)))
+    return t.value, st.value, g.value
+
+
+def ceed_batch_status(batch: Batch, stream=None):
+    _check(_lib.ceed_batch_status(batch.handle, _stream(stream)))
+
+
+def ceed_batch_destroy(batch: Batch):
+    batch.close()
 
 
 def ceed_build_geometry(mesh: Mesh, geo, stream=None):

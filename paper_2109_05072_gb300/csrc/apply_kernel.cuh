@@ -201,24 +201,25 @@ struct ApplyArgs {
   int *err;
 };
 
+// One thread block's share of a colour: elements e_begin + blk * ne + (0 .. ne-1).  Threads past
+// ne * Q^2 (a block shape that does not divide evenly) act as an inactive element; the caller
+// provides shared memory for ceil(blockDim / Q^2) elements and the mbarrier array.
 template <int P, int Q, int OP, typename T, typename TQ, bool STAGE>
-__global__ void __launch_bounds__(APPLY_MAX_THREADS)
-apply_kernel(const ApplyArgs a, const OpTab<T> tab) {
+__device__ __forceinline__ void apply_block(const ApplyArgs &a, const OpTab<T> &tab, int64_t blk,
+                                            unsigned char *smem_raw, uint64_t *bar) {
   constexpr int NPT = Q * Q;
   constexpr bool COLLOC = (P == Q);
   constexpr int ND = P * P * P;
   constexpr int NQ = Q * Q * Q;
   constexpr size_t QB = STAGE ? ((qblock_bytes<Q, OP, TQ>() + 127) & ~(size_t)127) : 0;
   constexpr size_t EB = apply_elem_smem<P, Q, OP, T, TQ, STAGE>();
-  extern __shared__ __align__(128) unsigned char smem_raw[];
-  __shared__ uint64_t bar[STAGE ? APPLY_MAX_NE : 1];
 
   const int tid = threadIdx.x;
   const int el = tid / NPT;
   const int ij = tid - el * NPT;
   const int i = ij % Q, j = ij / Q;
-  const int64_t e = a.e_begin + (int64_t)blockIdx.x * a.ne + el;
-  const bool active = e < a.e_begin + a.e_count;
+  const int64_t e = a.e_begin + blk * a.ne + el;
+  const bool active = (el < a.ne) && (e < a.e_begin + a.e_count);
   const bool node_thread = (i < P) && (j < P);
   // staged block in shared memory, or the element's block in global memory
   const TQ *sq = STAGE ? (const TQ *)(smem_raw + el * EB) : (const TQ *)a.qdata + (active ? e : a.e_begin) * a.estride;
@@ -259,7 +260,7 @@ apply_kernel(const ApplyArgs a, const OpTab<T> tab) {
         const int64_t o = (int64_t)(v & DOF_MASK) * a.ncol + col;
         const bool dir = a.masked && (v & FLAG_DIR);
         if (!dir) xv[c] = __ldg(a.x + o);
-        if (!dir && !(v & FLAG_FIRST)) yold[c] = a.y[o];
+        if (!dir && !(v & FLAG_FIRST)) yold[c] = __ldcg(a.y + o);  // L2: written by an earlier colour
       }
     }
     T u[P];
@@ -472,6 +473,18 @@ apply_kernel(const ApplyArgs a, const OpTab<T> tab) {
   }
   // an element that never reached the pointwise step (cannot happen today) must not leave its copy in flight
   if (STAGE && !have_q && ij == 0 && active) mbar_wait(&bar[el], 0);
+  if constexpr (STAGE) {  // retire the barrier so the slot can be initialised again by the next block
+    __syncthreads();
+    if (ij == 0) asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(smem_u32(&bar[el])) : "memory");
+  }
+}
+
+template <int P, int Q, int OP, typename T, typename TQ, bool STAGE>
+__global__ void __launch_bounds__(APPLY_MAX_THREADS)
+apply_kernel(const ApplyArgs a, const OpTab<T> tab) {
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  __shared__ uint64_t bar[STAGE ? APPLY_MAX_NE : 1];
+  apply_block<P, Q, OP, T, TQ, STAGE>(a, tab, blockIdx.x, smem_raw, bar);
 }
 
 // Launch one kernel per colour for a fixed (P, Q, op, T, TQ) and variant (elements per block, staging).

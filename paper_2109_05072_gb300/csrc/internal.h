@@ -71,6 +71,15 @@ struct ApplyChoice {
 
 }  // namespace ceedgb
 
+namespace ceedgb {
+// Launch shape of the persistent batched apply.
+struct BatchLaunch {
+  int threads;     // threads per block
+  int stage;       // TMA staging of quadrature data
+  unsigned grid;   // 0: as many blocks as are co-resident
+};
+}  // namespace ceedgb
+
 struct ceed_mesh_s {
   int device = 0;
   int64_t E = 0, n_ldof = 0;
