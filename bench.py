@@ -37,7 +37,10 @@ FP64_NOMINAL_TFLOPS = 1.25      # GB300 dense FP64 (profiling recipe's nominal t
 # DRAM bytes (read + write) per launch of the FP64 apply kernel variant, from one ncu capture of the
 # current kernel on the 48^3 mesh (13,824 elements per colour launch), scaled by elements to a 64^3
 # colour launch (32,768 elements); keyed by variant, empty until a capture of the current kernel.
-PROFILED_TRAFFIC_PER_LAUNCH = {}
+PROFILED_TRAFFIC_PER_LAUNCH = {
+    # profiles/apply_kernel_p7_48cube_ncu.md: 503.70 MB read + 66.40 MB written per 13,824-element launch
+    "apply_kernel<8,8,DIFFUSION,double,double,stage=0>[ne=1]": 570.09e6 * 32768 / 13824,
+}
 WORKLOADS = {
     "c2": dict(N=64, p=7),      # the diffusion workload named by element count
     "c2a": dict(N=40, p=7),     # 22.19M DOFs: the DOF count quoted for the same workload
