@@ -68,6 +68,30 @@ __device__ __forceinline__ double f2d_int(float f) {
   return __hiloint2double((int)hi, (int)lo);
 }
 
+// Cheaper FP64 -> FP32 for the gather: a funnel shift brings the low 8 exponent bits and the top 23
+// mantissa bits into float position; for the float range the double exponent is the float one plus
+// 896 (= 3*256 + 128), so its low 8 bits differ from the float exponent only in the top bit (XOR).
+// Rounds half up on the first dropped bit.  Magnitudes below 2^-126 give signed zero, Inf/NaN stay
+// Inf/NaN; values beyond the float range are not expected (L-vector entries).
+__device__ __forceinline__ float d2f_fast(double d) {
+  const unsigned hi = (unsigned)__double2hiint(d), lo = (unsigned)__double2loint(d);
+  const unsigned sign = hi & 0x80000000u, mag = hi & 0x7fffffffu;
+  unsigned f = ((__funnelshift_l(lo, hi, 3) & 0x7fffffffu) ^ 0x40000000u) | sign;
+  f += (lo >> 28) & 1u;
+  f = (mag < 0x38100000u) ? sign : f;
+  f = (mag >= 0x7ff00000u) ? (sign | 0x7f800000u | ((mag & 0xfffffu) | lo ? 0x400000u : 0u)) : f;
+  return __uint_as_float(f);
+}
+
+// FP64 -> FP32 for a value that is exactly a float (written by f2d_int): no rounding, no range checks
+// beyond zero.
+__device__ __forceinline__ float d2f_exact(double d) {
+  const unsigned hi = (unsigned)__double2hiint(d), lo = (unsigned)__double2loint(d);
+  const unsigned sign = hi & 0x80000000u;
+  const unsigned f = ((__funnelshift_l(lo, hi, 3) & 0x7fffffffu) ^ 0x40000000u) | sign;
+  return __uint_as_float((hi & 0x7fffffffu) ? f : sign);
+}
+
 template <typename T>
 struct LVec;
 template <>
@@ -78,9 +102,9 @@ struct LVec<double> {  // FP64 operator: native
 };
 template <>
 struct LVec<float> {   // FP32 operator: integer conversions, FP32 accumulation across colours
-  static __device__ __forceinline__ float in(double v) { return d2f_int(v); }
+  static __device__ __forceinline__ float in(double v) { return d2f_fast(v); }
   static __device__ __forceinline__ double out(float v) { return f2d_int(v); }
-  static __device__ __forceinline__ double add(double old, float v) { return f2d_int(d2f_int(old) + v); }
+  static __device__ __forceinline__ double add(double old, float v) { return f2d_int(d2f_exact(old) + v); }
 };
 
 // ------------------------------------------------------------------ TMA bulk copy + mbarrier
@@ -199,6 +223,8 @@ struct ApplyArgs {
   int ncol, masked;
   int ne;           // elements per thread block
   int *err;
+  double *dot_part;  // optional: partial sums of x_i y_i over the nodes whose final y this block writes
+  int64_t dot_base;  // index of this launch's first block in dot_part
 };
 
 // One thread block's share of a colour: elements e_begin + blk * ne + (0 .. ne-1).  Threads past
@@ -455,18 +481,53 @@ __device__ __forceinline__ void apply_block(const ApplyArgs &a, const OpTab<T> &
     }
 
     // ---- scatter-add (E -> L), atomic-free
-    if (active && node_thread) {
+    if (!a.dot_part) {
+      if (active && node_thread) {
 #pragma unroll
-      for (int c = 0; c < P; ++c) {
-        const uint32_t v = idx[c];
-        const int64_t o = (int64_t)(v & DOF_MASK) * a.ncol + col;
-        if (a.masked && (v & FLAG_DIR)) {
-          if (v & FLAG_FIRST) a.y[o] = a.x[o];
-        } else if (v & FLAG_FIRST) {
-          a.y[o] = LVec<T>::out(yv[c]);
-        } else {
-          a.y[o] = LVec<T>::add(yold[c], yv[c]);
+        for (int c = 0; c < P; ++c) {
+          const uint32_t v = idx[c];
+          const int64_t o = (int64_t)(v & DOF_MASK) * a.ncol + col;
+          if (a.masked && (v & FLAG_DIR)) {
+            if (v & FLAG_FIRST) a.y[o] = a.x[o];
+          } else if (v & FLAG_FIRST) {
+            a.y[o] = LVec<T>::out(yv[c]);
+          } else {
+            a.y[o] = LVec<T>::add(yold[c], yv[c]);
+          }
         }
+      }
+    } else {
+      // same scatter, and x . y over the nodes whose final value this thread writes (fused CG dot:
+      // the last writer of a node adds x_i y_i; a masked Dirichlet node's first writer adds x_i^2)
+      double dot = 0.0;
+      if (active && node_thread) {
+#pragma unroll
+        for (int c = 0; c < P; ++c) {
+          const uint32_t v = idx[c];
+          const int64_t o = (int64_t)(v & DOF_MASK) * a.ncol + col;
+          if (a.masked && (v & FLAG_DIR)) {
+            if (v & FLAG_FIRST) {
+              const double out = a.x[o];
+              a.y[o] = out;
+              dot += out * out;
+            }
+          } else {
+            const double out = (v & FLAG_FIRST) ? LVec<T>::out(yv[c]) : LVec<T>::add(yold[c], yv[c]);
+            a.y[o] = out;
+            if (v & FLAG_LAST) dot += __ldg(a.x + o) * out;  // reloaded (cache hit): keeps xv dead early
+          }
+        }
+      }
+      // fixed-order block reduction: warp shuffles, then the warps in order
+      __shared__ double dsum[APPLY_MAX_THREADS / 32];
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1) dot += __shfl_down_sync(0xffffffffu, dot, off);
+      if ((tid & 31) == 0) dsum[tid >> 5] = dot;
+      __syncthreads();
+      if (tid == 0) {
+        double t = 0.0;
+        for (int w = 0; w < (int)((blockDim.x + 31) >> 5); ++w) t += dsum[w];
+        a.dot_part[a.dot_base + blk] = t;
       }
     }
     if (col + 1 < a.ncol) __syncthreads();
@@ -508,6 +569,8 @@ int launch_variant(ceed_mesh_t m, const OpTab<T> &tab, const ApplyReq &r, int ne
   a.ne = ne;
   a.err = m->d_err + 1;
   a.estride = qdata_estride(OP, sizeof(TQ), Q);
+  a.dot_part = (r.ncol == 1) ? r.dot_part : nullptr;
+  a.dot_base = 0;
   for (int c = 0; c < m->n_colors; ++c) {
     a.e_begin = m->color_start[c];
     const int64_t n = m->color_start[c + 1] - a.e_begin;
@@ -515,7 +578,9 @@ int launch_variant(ceed_mesh_t m, const OpTab<T> &tab, const ApplyReq &r, int ne
     a.e_count = n;
     const dim3 grid((unsigned)((n + ne - 1) / ne));
     apply_kernel<P, Q, OP, T, TQ, STAGE><<<grid, block, smem, s>>>(a, tab);
+    a.dot_base += grid.x;
   }
+  if (r.dot_n) *r.dot_n = a.dot_part ? a.dot_base : 0;
   CEED_CUDA_CHECK(cudaGetLastError());
   return CEED_OK;
 }

@@ -167,6 +167,8 @@ int launch_batch(int n, ceed_mesh_t const *meshes, const ApplyReq *reqs, const O
     if (bm.a.ne < 1) return fail(CEED_ERR_INVALID, "block too small for this order");
     bm.a.err = err;
     bm.a.estride = qdata_estride(OP, sizeof(TQ), m->Q);
+    bm.a.dot_part = nullptr;
+    bm.a.dot_base = 0;
     b.tab[k] = *tabs[k];
     b.max_colors = std::max(b.max_colors, m->n_colors);
     const size_t sm = L.stage ? batch_smem_for<OP, T, TQ, true>(m->P, m->Q, L.threads)

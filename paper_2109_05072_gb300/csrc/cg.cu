@@ -44,15 +44,29 @@ __device__ __forceinline__ double block_sum(double v, double *sh) {
 
 __device__ __forceinline__ bool finite(double v) { return isfinite(v); }
 
+// Grid-stride loops below take four strided entries per trip (independent loads in flight,
+// independent partial sums); the summation order is fixed by (n, grid) so results are reproducible.
+#define CEEDGB_GRID4(BODY)                                                                     \
+  {                                                                                            \
+    const int64_t stride_ = (int64_t)gridDim.x * blockDim.x;                                   \
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;                                \
+    for (; i + 3 * stride_ < n; i += 4 * stride_) {                                            \
+      { const int u_ = 0; (void)u_; const int64_t k = i; BODY }                                \
+      { const int u_ = 1; (void)u_; const int64_t k = i + stride_; BODY }                      \
+      { const int u_ = 2; (void)u_; const int64_t k = i + 2 * stride_; BODY }                  \
+      { const int u_ = 3; (void)u_; const int64_t k = i + 3 * stride_; BODY }                  \
+    }                                                                                          \
+    for (; i < n; i += stride_) { const int u_ = 0; (void)u_; const int64_t k = i; BODY }      \
+  }
+
 __global__ void dot_partial_kernel(const double *__restrict__ x, const double *__restrict__ y, int64_t n,
                                    double *__restrict__ part, const Scalars *sc) {
   __shared__ double sh[RED_THREADS];
   if (sc && sc->done) return;
-  double a = 0.0;
-  for (int64_t i = blockIdx.x * (int64_t)RED_THREADS + threadIdx.x; i < n; i += (int64_t)gridDim.x * RED_THREADS)
-    a += x[i] * y[i];
-  a = block_sum(a, sh);
-  if (threadIdx.x == 0) part[blockIdx.x] = a;
+  double a[4] = {0.0, 0.0, 0.0, 0.0};
+  CEEDGB_GRID4(a[u_] += x[k] * y[k];)
+  double t = block_sum((a[0] + a[1]) + (a[2] + a[3]), sh);
+  if (threadIdx.x == 0) part[blockIdx.x] = t;
 }
 
 // Sums nb partials in fixed order into *out.
@@ -64,12 +78,26 @@ __global__ void sum_partials_kernel(const double *__restrict__ part, int nb, dou
   if (threadIdx.x == 0) *out = a;
 }
 
-__global__ void finalize_alpha_kernel(const double *__restrict__ part, int nb, Scalars *sc) {
-  __shared__ double sh[RED_THREADS];
+// Launched with 1024 threads: sums nb partials (up to one per element) in a fixed order.
+__global__ void finalize_alpha_kernel(const double *__restrict__ part, int64_t nb, Scalars *sc) {
+  __shared__ double sh[1024];
   if (sc->done) return;
-  double a = 0.0;
-  for (int i = threadIdx.x; i < nb; i += RED_THREADS) a += part[i];
-  a = block_sum(a, sh);
+  double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+  int64_t i = threadIdx.x;
+  for (; i + 3 * 1024 < nb; i += 4 * 1024) {
+    a0 += part[i];
+    a1 += part[i + 1024];
+    a2 += part[i + 2048];
+    a3 += part[i + 3072];
+  }
+  for (; i < nb; i += 1024) a0 += part[i];
+  sh[threadIdx.x] = (a0 + a1) + (a2 + a3);
+  __syncthreads();
+  for (int st = 512; st > 0; st >>= 1) {
+    if (threadIdx.x < st) sh[threadIdx.x] += sh[threadIdx.x + st];
+    __syncthreads();
+  }
+  const double a = sh[0];
   if (threadIdx.x == 0) {
     sc->pq = a;
     sc->alpha = sc->rz / a;
@@ -88,21 +116,21 @@ __global__ void update_kernel(double *__restrict__ x, double *__restrict__ r, do
   __shared__ double sh[RED_THREADS];
   if (sc->done) return;
   const double alpha = sc->alpha;
-  double arz = 0.0, arr = 0.0;
-  for (int64_t i = blockIdx.x * (int64_t)RED_THREADS + threadIdx.x; i < n; i += (int64_t)gridDim.x * RED_THREADS) {
-    x[i] += alpha * p[i];
-    const double ri = r[i] - alpha * q[i];
-    r[i] = ri;
-    const double zi = dinv[i] * ri;
-    z[i] = zi;
-    arz += ri * zi;
-    arr += ri * ri;
-  }
-  arz = block_sum(arz, sh);
-  arr = block_sum(arr, sh);
+  double arz[4] = {0.0, 0.0, 0.0, 0.0}, arr[4] = {0.0, 0.0, 0.0, 0.0};
+  CEEDGB_GRID4({
+    x[k] += alpha * p[k];
+    const double ri = r[k] - alpha * q[k];
+    r[k] = ri;
+    const double zi = dinv[k] * ri;
+    z[k] = zi;
+    arz[u_] += ri * zi;
+    arr[u_] += ri * ri;
+  })
+  const double trz = block_sum((arz[0] + arz[1]) + (arz[2] + arz[3]), sh);
+  const double trr = block_sum((arr[0] + arr[1]) + (arr[2] + arr[3]), sh);
   if (threadIdx.x == 0) {
-    part_rz[blockIdx.x] = arz;
-    part_rr[blockIdx.x] = arr;
+    part_rz[blockIdx.x] = trz;
+    part_rr[blockIdx.x] = trr;
   }
 }
 
@@ -138,8 +166,7 @@ __global__ void finalize_beta_kernel(const double *__restrict__ part_rz, const d
 __global__ void pupdate_kernel(double *__restrict__ p, const double *__restrict__ z, int64_t n, const Scalars *sc) {
   if (sc->done) return;
   const double beta = sc->beta;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-    p[i] = z[i] + beta * p[i];
+  CEEDGB_GRID4(p[k] = z[k] + beta * p[k];)
 }
 
 // CG start from r (already holding the initial residual): z = dinv r, p = z, partials of r.z, r.r
@@ -147,20 +174,20 @@ __global__ void start_kernel(const double *__restrict__ r, double *__restrict__ 
                              const double *__restrict__ dinv, int64_t n, double *__restrict__ part_rz,
                              double *__restrict__ part_rr) {
   __shared__ double sh[RED_THREADS];
-  double arz = 0.0, arr = 0.0;
-  for (int64_t i = blockIdx.x * (int64_t)RED_THREADS + threadIdx.x; i < n; i += (int64_t)gridDim.x * RED_THREADS) {
-    const double ri = r[i];
-    const double zi = dinv[i] * ri;
-    z[i] = zi;
-    p[i] = zi;
-    arz += ri * zi;
-    arr += ri * ri;
-  }
-  arz = block_sum(arz, sh);
-  arr = block_sum(arr, sh);
+  double arz[4] = {0.0, 0.0, 0.0, 0.0}, arr[4] = {0.0, 0.0, 0.0, 0.0};
+  CEEDGB_GRID4({
+    const double ri = r[k];
+    const double zi = dinv[k] * ri;
+    z[k] = zi;
+    p[k] = zi;
+    arz[u_] += ri * zi;
+    arr[u_] += ri * ri;
+  })
+  const double trz = block_sum((arz[0] + arz[1]) + (arz[2] + arz[3]), sh);
+  const double trr = block_sum((arr[0] + arr[1]) + (arr[2] + arr[3]), sh);
   if (threadIdx.x == 0) {
-    part_rz[blockIdx.x] = arz;
-    part_rr[blockIdx.x] = arr;
+    part_rz[blockIdx.x] = trz;
+    part_rr[blockIdx.x] = trr;
   }
 }
 
@@ -190,19 +217,18 @@ __global__ void start_finalize_kernel(const double *__restrict__ part_rz, const 
 __global__ void residual_kernel(const double *__restrict__ b, const double *__restrict__ Ax, double *__restrict__ out,
                                 int64_t n, double *__restrict__ part) {
   __shared__ double sh[RED_THREADS];
-  double a = 0.0;
-  for (int64_t i = blockIdx.x * (int64_t)RED_THREADS + threadIdx.x; i < n; i += (int64_t)gridDim.x * RED_THREADS) {
-    const double v = b[i] - Ax[i];
-    out[i] = v;
-    a += v * v;
-  }
-  a = block_sum(a, sh);
-  if (threadIdx.x == 0) part[blockIdx.x] = a;
+  double a[4] = {0.0, 0.0, 0.0, 0.0};
+  CEEDGB_GRID4({
+    const double v = b[k] - Ax[k];
+    out[k] = v;
+    a[u_] += v * v;
+  })
+  const double t = block_sum((a[0] + a[1]) + (a[2] + a[3]), sh);
+  if (threadIdx.x == 0) part[blockIdx.x] = t;
 }
 
 __global__ void axpy_kernel(double *__restrict__ x, const double *__restrict__ d, int64_t n) {
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-    x[i] += d[i];
+  CEEDGB_GRID4(x[k] += d[k];)
 }
 
 __global__ void invert_kernel(double *__restrict__ d, int64_t n) {
@@ -216,18 +242,18 @@ __global__ void zero_kernel(double *__restrict__ d, int64_t n) {
 }
 
 __global__ void copy_kernel(double *__restrict__ d, const double *__restrict__ s, int64_t n) {
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-    d[i] = s[i];
+  CEEDGB_GRID4(d[k] = s[k];)
 }
 
 static size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
 
 struct Work {
   double *r_out, *d, *r, *z, *p, *q, *dinv, *part1, *part2;
+  double *pq_part;  // per-block partial sums of p . q written by the fused apply
   Scalars *sc;
 };
 
-static size_t layout(int64_t n, bool mixed, char *base, Work *w) {
+static size_t layout(int64_t n, int64_t n_elem, bool mixed, char *base, Work *w) {
   size_t off = 0;
   auto take = [&](size_t bytes) {
     char *ptr = base ? base + off : nullptr;
@@ -244,6 +270,7 @@ static size_t layout(int64_t n, bool mixed, char *base, Work *w) {
   (void)mixed;
   t.r_out = (double *)take(vb);
   t.d = (double *)take(vb);
+  t.pq_part = (double *)take((size_t)n_elem * sizeof(double));
   t.part1 = (double *)take(RED_MAX_BLOCKS * sizeof(double));
   t.part2 = (double *)take(RED_MAX_BLOCKS * sizeof(double));
   t.sc = (Scalars *)take(sizeof(Scalars));
@@ -281,12 +308,23 @@ static int pcg_run(ceed_mesh_t m, const ApplyReq &op, double *y, const Work &w, 
   while (it < cap) {
     const int batch = std::min(cap - it, fixed > 0 ? cap : check_every);
     for (int b = 0; b < batch; ++b) {
+      // q = A p.  FP64 operator: p . q is summed by the apply itself (each node's last writer adds
+      // p_i q_i), saving two vector passes at no cost to the FP64-pipe-bound kernel.  FP32 operators
+      // keep the separate reduction (FP64 products inside them would cost more than the passes).
       ApplyReq a = op;
       a.x = w.p;
       a.y = w.q;
+      const bool fuse = (op.prec == CEED_F64);
+      a.dot_part = fuse ? w.pq_part : nullptr;
+      int64_t npart = 0;
+      a.dot_n = &npart;
       if (int st = launch_apply(m, a, s)) return st;
-      dot_partial_kernel<<<nb, RED_THREADS, 0, s>>>(w.p, w.q, n, w.part1, w.sc);
-      finalize_alpha_kernel<<<1, RED_THREADS, 0, s>>>(w.part1, nb, w.sc);
+      if (fuse) {
+        finalize_alpha_kernel<<<1, 1024, 0, s>>>(w.pq_part, npart, w.sc);
+      } else {
+        dot_partial_kernel<<<nb, RED_THREADS, 0, s>>>(w.p, w.q, n, w.part1, w.sc);
+        finalize_alpha_kernel<<<1, 1024, 0, s>>>(w.part1, nb, w.sc);
+      }
       update_kernel<<<nb, RED_THREADS, 0, s>>>(y, w.r, w.z, w.p, w.q, w.dinv, n, w.part1, w.part2, w.sc);
       finalize_beta_kernel<<<1, RED_THREADS, 0, s>>>(w.part1, w.part2, nb, w.sc, fixed > 0);
       pupdate_kernel<<<stream_blocks(n), 256, 0, s>>>(w.p, w.z, n, w.sc);
@@ -347,7 +385,7 @@ static void fill_defaults(const ceed_cg_opts *in, ceed_cg_opts *o) {
 
 extern "C" size_t ceed_cg_workspace_bytes(ceed_mesh_t m, const ceed_cg_opts *opts) {
   if (!m || !opts) return 0;
-  return layout(m->n_ldof, opts->mode == CEED_CG_MIXED, nullptr, nullptr);
+  return layout(m->n_ldof, m->E, opts->mode == CEED_CG_MIXED, nullptr, nullptr);
 }
 
 extern "C" int ceed_cg_solve(ceed_mesh_t m, const void *qdata, int prec, const double *b, double *x,
@@ -367,9 +405,9 @@ extern "C" int ceed_cg_solve(ceed_mesh_t m, const void *qdata, int prec, const d
     return fail(CEED_ERR_INVALID, "MIXED mode needs qdata_lo in F32, BF16, F16 or F32_GEO");
   if (o.op != CEED_OP_MASS && o.op != CEED_OP_DIFFUSION) return fail(CEED_ERR_INVALID, "unknown operator");
   const int64_t n = m->n_ldof;
-  if (work_bytes < layout(n, mixed, nullptr, nullptr)) return fail(CEED_ERR_INVALID, "workspace too small");
+  if (work_bytes < layout(n, m->E, mixed, nullptr, nullptr)) return fail(CEED_ERR_INVALID, "workspace too small");
   Work w;
-  layout(n, mixed, (char *)work, &w);
+  layout(n, m->E, mixed, (char *)work, &w);
   cudaStream_t s = (cudaStream_t)stream;
   std::memset(report, 0, sizeof(*report));
 

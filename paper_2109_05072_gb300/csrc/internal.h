@@ -14,11 +14,12 @@ namespace ceedgb {
 constexpr int MAX_P = 9;    // nodes per direction (p = 8)
 constexpr int MAX_Q = 10;   // quadrature points per direction (Gauss, p = 8)
 
-// Restriction entries: low 30 bits are the L-vector node; bit 31 marks the first element (in
-// colour order) that writes the node, bit 30 a Dirichlet node.
+// Restriction entries: low 29 bits are the L-vector node; bit 31 marks the first element (in
+// colour order) that writes the node, bit 29 the last one, bit 30 a Dirichlet node.
 constexpr uint32_t FLAG_FIRST = 1u << 31;
 constexpr uint32_t FLAG_DIR = 1u << 30;
-constexpr uint32_t DOF_MASK = (1u << 30) - 1u;
+constexpr uint32_t FLAG_LAST = 1u << 29;
+constexpr uint32_t DOF_MASK = (1u << 29) - 1u;
 
 // Even-odd split of a centro-(anti)symmetric NO x NI matrix M (M[NO-1-i][NI-1-j] = +-M[i][j]):
 // E/O are the (NO/2) x (NI/2) blocks acting on folded inputs, cmid the middle input column
@@ -128,6 +129,8 @@ struct ApplyReq {
   int masked;
   int ne = 0;        // > 0: force this many elements per block (autotuner), else tuned/default
   int stage = 1;     // with ne > 0: staging switch
+  double *dot_part = nullptr;  // non-null (ncol = 1): per-block partial sums of x . y over final node values
+  int64_t *dot_n = nullptr;    // out: number of partial sums written
 };
 int launch_apply_f64(ceed_mesh_t m, const ApplyReq &r, cudaStream_t s);
 int launch_apply_f32(ceed_mesh_t m, const ApplyReq &r, cudaStream_t s);

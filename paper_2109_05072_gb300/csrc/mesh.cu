@@ -254,7 +254,7 @@ extern "C" int ceed_setup_mesh(const ceed_mesh_desc *desc, ceed_mesh_t *out, voi
   if (!desc || !out) return fail(CEED_ERR_INVALID, "null descriptor or output");
   *out = nullptr;
   if (desc->n_elem < 1 || desc->n_ldof < 1) return fail(CEED_ERR_INVALID, "n_elem and n_ldof must be >= 1");
-  if (desc->n_ldof > (int64_t)DOF_MASK) return fail(CEED_ERR_INVALID, "n_ldof must be < 2^30");
+  if (desc->n_ldof > (int64_t)DOF_MASK) return fail(CEED_ERR_INVALID, "n_ldof must be < 2^29");
   if (desc->p < 1 || desc->p > 8) return fail(CEED_ERR_INVALID, "p must be in 1..8");
   if (desc->ncomp < 1) return fail(CEED_ERR_INVALID, "ncomp must be >= 1");
   if (!desc->elem_dofs || !desc->vertices) return fail(CEED_ERR_INVALID, "elem_dofs and vertices are required");
@@ -381,6 +381,18 @@ extern "C" int ceed_setup_mesh(const ceed_mesh_desc *desc, ceed_mesh_t *out, voi
       dst[n] = f;
     }
     std::memcpy(&svert[sidx * 24], &vert[e * 24], 24 * sizeof(double));
+  }
+  // last writer of every node: scan the sorted order backwards
+  std::fill(seen.begin(), seen.end(), 0);
+  for (int64_t sidx = E - 1; sidx >= 0; --sidx) {
+    uint32_t *dst = &emap[sidx * nd];
+    for (int64_t n = 0; n < nd; ++n) {
+      const uint32_t v = dst[n] & DOF_MASK;
+      if (!seen[v]) {
+        dst[n] |= FLAG_LAST;
+        seen[v] = 1;
+      }
+    }
   }
 
   CEED_CUDA_CHECK(cudaMalloc(&m->d_emap, E * nd * 4));

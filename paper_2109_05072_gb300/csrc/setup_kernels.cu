@@ -119,14 +119,17 @@ __global__ void elemvec_kernel(ElemVecArgs a) {
   if (e >= a.e_begin + a.e_count) return;
   const int P = a.P, Q = a.Q, nd = P * P * P, nq = Q * Q * Q;
   extern __shared__ double sh[];
-  double *fq = sh;  // [nq] point values (mode 0)
-  double G1[MAX_Q * MAX_P];  // derivative of the nodal basis at the points: G1 = D B
-  for (int q = 0; q < Q; ++q)
-    for (int c = 0; c < P; ++c) {
+  double *fq = sh;           // [nq] point values (mode 0)
+  double *G1 = sh + nq;      // [Q][P] derivative of the nodal basis at the points, G1 = D B (Gauss only)
+  if (P != Q) {
+    for (int t = threadIdx.x; t < Q * P; t += blockDim.x) {
+      const int q = t / P, c = t % P;
       double s = 0.0;
       for (int m = 0; m < Q; ++m) s += a.tab.D[q * Q + m] * a.tab.B[m * P + c];
-      G1[q * P + c] = s;
+      G1[t] = s;
     }
+    __syncthreads();
+  }
   if (a.mode == 0) {
     for (int q = threadIdx.x; q < nq; q += blockDim.x) {
       const int i = q % Q, j = (q / Q) % Q, k = q / (Q * Q);
@@ -203,7 +206,7 @@ static int run_elemvec(ceed_mesh_t m, ElemVecArgs a, cudaStream_t s) {
   a.Q = m->Q;
   a.rule = m->rule;
   a.tab = m->tab64;
-  const size_t shm = (size_t)nq_of(m) * sizeof(double);
+  const size_t shm = ((size_t)nq_of(m) + MAX_Q * MAX_P) * sizeof(double);
   for (int c = 0; c < m->n_colors; ++c) {
     a.e_begin = m->color_start[c];
     a.e_count = m->color_start[c + 1] - a.e_begin;
