@@ -435,6 +435,40 @@ def main():
             if rep64["seconds"] > 0 and repm["seconds"] > 0:
                 cg[f"mixed_{name}_speedup"] = rep64["seconds"] / repm["seconds"]
             del qlo
+        # p-multigrid-preconditioned (flexible) CG: levels p = 7, 3, 1 on the same elements, Chebyshev-Jacobi
+        # smoothing (degree 3) with FP64 or FP32-arithmetic level operators, Jacobi-PCG on the p = 1 level
+        Nc = WORKLOADS[args.cg_workload]["N"]
+        lv_meshes, lv_q64, lv_q32, keep = [mesh], [qd64], [], []
+        q32f = ceed.alloc_qdata(mesh, ceed.CEED_OP_DIFFUSION, ceed.CEED_F32, dev)
+        ceed.ceed_build_qdata(mesh, ceed.CEED_OP_DIFFUSION, ceed.CEED_COEFF_SINE, None, ceed.CEED_F32, q32f)
+        lv_q32.append(q32f)
+        t0 = time.perf_counter()
+        for pc in (3, 1):
+            mcs = synthetic.cube_mesh(Nc, pc, seed=0)
+            mc = ceed.ceed_setup_mesh(mcs.n_elem, mcs.n_ldof, pc, torch.from_numpy(mcs.elem_dofs).to(dev),
+                                      torch.from_numpy(mcs.vertices).to(dev), torch.from_numpy(mcs.boundary).to(dev))
+            q64c = ceed.alloc_qdata(mc, ceed.CEED_OP_DIFFUSION, ceed.CEED_F64, dev)
+            ceed.ceed_build_qdata(mc, ceed.CEED_OP_DIFFUSION, ceed.CEED_COEFF_SINE, None, ceed.CEED_F64, q64c)
+            q32c = ceed.alloc_qdata(mc, ceed.CEED_OP_DIFFUSION, ceed.CEED_F32, dev)
+            ceed.ceed_build_qdata(mc, ceed.CEED_OP_DIFFUSION, ceed.CEED_COEFF_SINE, None, ceed.CEED_F32, q32c)
+            lv_meshes.append(mc)
+            lv_q64.append(q64c)
+            lv_q32.append(q32c)
+        for name, qlo in (("pmg_fp64_smoothers", None), ("pmg_fp32_smoothers", lv_q32)):
+            t1 = time.perf_counter()
+            pmg = ceed.ceed_pmg_create(lv_meshes, lv_q64, qlo, prec_lo=ceed.CEED_F32)
+            setup_s = time.perf_counter() - t1
+            st, repp = ceed.ceed_cg_solve(mesh, qd64, ceed.CEED_F64, b, xs, mode=ceed.CEED_CG_FP64, tol=1e-10,
+                                          max_iter=2000, op=ceed.CEED_OP_DIFFUSION, pmg=pmg, raise_on_error=False)
+            cg[f"{name}_to_1e-10"] = dict(repp, status=st, setup_s=setup_s,
+                                          lambda_max=[ceed.ceed_pmg_info(pmg, k) for k in range(2)])
+            if rep64["seconds"] > 0 and repp["seconds"] > 0:
+                cg[f"{name}_speedup_vs_fp64_jacobi"] = rep64["seconds"] / repp["seconds"]
+            pmg.close()
+        cg["pmg_levels"] = "p = 7, 3, 1 on the same elements (hierarchy built in %.1f s)" % (time.perf_counter() - t0)
+        for mc in lv_meshes[1:]:
+            mc.close()
+        del lv_q64[1:], lv_q32
         cg["workload"] = f"{WORKLOADS[args.cg_workload]['N']}^3, p=7, n_ldof={m.n_ldof}"
 
     # ---------------- batched apply: p = 3, 5, 7 meshes (Gauss q = p+2), 3 components, 1..16 RHS, one launch

@@ -175,6 +175,8 @@ int ceed_batch_destroy(ceed_batch_t batch);
 
 typedef enum { CEED_CG_FP64 = 0, CEED_CG_MIXED = 1 } ceed_cg_mode;
 
+typedef struct ceed_pmg_s *ceed_pmg_t;
+
 typedef struct {
   int32_t mode;           /* ceed_cg_mode */
   int32_t max_iter;       /* cap on (inner) iterations in total; 0 -> 10000 */
@@ -187,6 +189,8 @@ typedef struct {
   const void *qdata_lo;   /* MIXED: quadrature data for the inner operator */
   int32_t prec_lo;        /* MIXED: its precision (F32, BF16, F16 or F32_GEO) */
   int32_t use_x0;         /* nonzero: x holds the initial guess; else x0 = 0 */
+  ceed_pmg_t pmg;         /* FP64 mode: non-NULL -> flexible CG preconditioned by one p-multigrid
+                             V-cycle per iteration instead of Jacobi */
 } ceed_cg_opts;
 
 typedef struct {
@@ -209,6 +213,39 @@ size_t ceed_cg_workspace_bytes(ceed_mesh_t mesh, const ceed_cg_opts *opts);
 int ceed_cg_solve(ceed_mesh_t mesh, const void *qdata, int prec, const double *b, double *x,
                   const ceed_cg_opts *opts, ceed_cg_report *report, void *work, size_t work_bytes,
                   void *stream);
+
+/* ---------------------------------------------------------------- p-multigrid */
+
+/* p-multigrid preconditioner (paper Section 1: p-multigrid as the usual replacement of low-order
+ * preconditioners for the matrix-free operator).  Levels are meshes of decreasing order on the SAME
+ * elements (meshes[0] finest; all with the same Dirichlet nodes, ncomp = 1, GLL collocated or all
+ * Gauss).  Transfers: prolongation evaluates the coarse element polynomial at the fine nodes,
+ * restriction is its exact transpose.  Smoother: Chebyshev iteration on D^{-1} A over
+ * [lambda_max / smooth_ratio, 1.1 lambda_max] (lambda_max by power iteration at creation), degree
+ * smooth_degree before and after the coarse correction.  Coarsest level: Jacobi-PCG to a relative
+ * residual coarse_tol (at most coarse_max_iter iterations).  qdata64[l]: FP64 diffusion qdata of
+ * level l (Jacobi diagonal, and the smoother unless qdata_lo is given); qdata_lo[l] (may be NULL)
+ * with prec_lo selects an FP32-arithmetic smoothing operator.  The handle allocates its level
+ * vectors at creation (several n_ldof-sized FP64 vectors per level).  Synchronizes `stream`. */
+typedef struct {
+  int32_t smooth_degree;    /* 0 -> 3 */
+  double smooth_ratio;      /* 0 -> 10 */
+  int32_t eig_iters;        /* 0 -> 20 */
+  double coarse_tol;        /* 0 -> 1e-2 */
+  int32_t coarse_max_iter;  /* 0 -> 500 */
+  int32_t prec_lo;          /* precision of qdata_lo (F32, BF16, F16, F32_GEO) */
+} ceed_pmg_opts;
+
+int ceed_pmg_create(int nlevels, const ceed_mesh_t *meshes, const void *const *qdata64, const void *const *qdata_lo,
+                    const ceed_pmg_opts *opts, ceed_pmg_t *out, void *stream);
+/* z = M r: one V-cycle (r, z device FP64 [n_ldof of level 0]). */
+int ceed_pmg_vcycle(ceed_pmg_t pmg, const double *r, double *z, void *stream);
+/* Transfers between levels l+1 (coarse) and l (fine): uf = P uc, rc = P^T rf. */
+int ceed_pmg_prolong(ceed_pmg_t pmg, int level, const double *uc, double *uf, void *stream);
+int ceed_pmg_restrict(ceed_pmg_t pmg, int level, const double *rf, double *rc, void *stream);
+/* lambda_max estimate of D^{-1} A used for level l's smoother. */
+int ceed_pmg_info(ceed_pmg_t pmg, int level, double *lambda_max);
+int ceed_pmg_destroy(ceed_pmg_t pmg);
 
 /* ---------------------------------------------------------------- adjoint */
 

@@ -295,3 +295,50 @@ def cost_model(p: int, collocated: bool = True):
     """
     P = p + 1
     return 7 * P ** 3, (12 if collocated else 24) * P ** 4 + 15 * P ** 3
+
+
+def prolongation_element(p_coarse: int, p_fine: int):
+    """Element interpolation matrix [P_f^3, P_c^3]: the coarse Q_{p_c} basis (Lagrange on its GLL nodes)
+    evaluated at the fine GLL nodes of the same reference element, as the product of 1D values.
+
+    This is the transfer of p-multigrid between orders on one mesh (the p-multigrid the paper names
+    as the usual replacement of low-order preconditioners, Section 1): a coarse finite-element
+    function, evaluated at the fine nodes, is the same function in the fine space.
+    """
+    xc, _ = gll(p_coarse + 1)
+    xf, _ = gll(p_fine + 1)
+    L, _ = lagrange(xc, xf)                       # [Pf, Pc]
+    Pf, Pc = p_fine + 1, p_coarse + 1
+    # M[k, j, i, c, b, a] = L[k, c] L[j, b] L[i, a]: fine node (i, j, k), coarse node (a, b, c)
+    M = L[:, None, None, :, None, None] * L[None, :, None, None, :, None] * L[None, None, :, None, None, :]
+    return M.reshape(Pf ** 3, Pc ** 3)
+
+
+def prolongate(p_coarse, p_fine, dofs_coarse, dofs_fine, u_coarse, n_fine):
+    """u_f = P u_c: interpolate element by element; every element gives the same value at a shared
+    fine node (the coarse function is continuous), so the first element in order sets it."""
+    M = prolongation_element(p_coarse, p_fine)
+    uf = np.full(n_fine, np.nan)
+    vals = np.einsum("fc,ec->ef", M, u_coarse[dofs_coarse])
+    for e in range(dofs_fine.shape[0]):
+        idx = dofs_fine[e]
+        new = np.isnan(uf[idx])
+        uf[idx[new]] = vals[e][new]
+    return uf
+
+
+def restrict(p_coarse, p_fine, dofs_coarse, dofs_fine, r_fine, n_coarse):
+    """r_c = P^T r_f for the assembled interpolation P of `prolongate`: each fine node counted once
+    (by the first element in order that contains it)."""
+    M = prolongation_element(p_coarse, p_fine)
+    w = np.zeros_like(dofs_fine, dtype=np.float64)
+    seen = np.zeros(len(r_fine), dtype=bool)
+    for e in range(dofs_fine.shape[0]):
+        idx = dofs_fine[e]
+        first = ~seen[idx]
+        w[e][first] = 1.0
+        seen[idx] = True
+    rc = np.zeros(n_coarse)
+    contrib = np.einsum("fc,ef->ec", M, w * r_fine[dofs_fine])
+    np.add.at(rc, dofs_coarse.reshape(-1), contrib.reshape(-1))
+    return rc

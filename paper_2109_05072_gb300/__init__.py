@@ -46,7 +46,12 @@ class _CgOpts(ctypes.Structure):
     _fields_ = [("mode", ctypes.c_int32), ("max_iter", ctypes.c_int32), ("max_outer", ctypes.c_int32),
                 ("check_every", ctypes.c_int32), ("fixed_iters", ctypes.c_int32), ("op", ctypes.c_int32),
                 ("tol", ctypes.c_double), ("inner_tol", ctypes.c_double), ("qdata_lo", ctypes.c_void_p),
-                ("prec_lo", ctypes.c_int32), ("use_x0", ctypes.c_int32)]
+                ("prec_lo", ctypes.c_int32), ("use_x0", ctypes.c_int32), ("pmg", ctypes.c_void_p)]
+
+
+class _PmgOpts(ctypes.Structure):
+    _fields_ = [("smooth_degree", ctypes.c_int32), ("smooth_ratio", ctypes.c_double), ("eig_iters", ctypes.c_int32),
+                ("coarse_tol", ctypes.c_double), ("coarse_max_iter", ctypes.c_int32), ("prec_lo", ctypes.c_int32)]
 
 
 class _CgReport(ctypes.Structure):
@@ -77,6 +82,13 @@ def _load():
         "ceed_cg_solve": (ctypes.c_int, [vp, vp, ctypes.c_int, vp, vp, ctypes.POINTER(_CgOpts),
                                          ctypes.POINTER(_CgReport), vp, sz, vp]),
         "ceed_build_geometry": (ctypes.c_int, [vp, vp, vp]),
+        "ceed_pmg_create": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.POINTER(vp),
+                                           ctypes.POINTER(_PmgOpts), ctypes.POINTER(vp), vp]),
+        "ceed_pmg_vcycle": (ctypes.c_int, [vp, vp, vp, vp]),
+        "ceed_pmg_prolong": (ctypes.c_int, [vp, ctypes.c_int, vp, vp, vp]),
+        "ceed_pmg_restrict": (ctypes.c_int, [vp, ctypes.c_int, vp, vp, vp]),
+        "ceed_pmg_info": (ctypes.c_int, [vp, ctypes.c_int, ctypes.POINTER(ctypes.c_double)]),
+        "ceed_pmg_destroy": (ctypes.c_int, [vp]),
         "ceed_apply_diffusion_k": (ctypes.c_int, [vp, vp, vp, vp, vp, u32, vp]),
         "ceed_apply_diffusion_adjoint": (ctypes.c_int, [vp, vp, vp, vp, vp, vp, vp, vp]),
         "ceed_batch_create": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.c_int,
@@ -222,6 +234,8 @@ def _cg_opts(**kw):
     for k, v in kw.items():
         if k == "qdata_lo":
             o.qdata_lo = _ptr(v)
+        elif k == "pmg":
+            o.pmg = v.handle if v is not None else None
         else:
             setattr(o, k, v)
     return o
@@ -298,6 +312,58 @@ def ceed_batch_status(batch: Batch, stream=None):
 
 def ceed_batch_destroy(batch: Batch):
     batch.close()
+
+
+class Pmg:
+    """Owns a ceed_pmg_t and keeps its level meshes and quadrature data alive."""
+
+    def __init__(self, handle, keep):
+        self.handle, self._keep = handle, keep
+
+    def close(self):
+        if self.handle:
+            _lib.ceed_pmg_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def ceed_pmg_create(meshes, qdata64, qdata_lo=None, prec_lo=CEED_F32, smooth_degree=0, smooth_ratio=0.0,
+                    eig_iters=0, coarse_tol=0.0, coarse_max_iter=0, stream=None) -> Pmg:
+    n = len(meshes)
+    arr = lambda items: (ctypes.c_void_p * n)(*items)
+    lo = arr([_ptr(q).value if q is not None else None for q in qdata_lo]) if qdata_lo is not None else None
+    o = _PmgOpts(smooth_degree, smooth_ratio, eig_iters, coarse_tol, coarse_max_iter, prec_lo)
+    h = ctypes.c_void_p()
+    _check(_lib.ceed_pmg_create(n, arr([m.handle for m in meshes]), arr([_ptr(q).value for q in qdata64]), lo,
+                                ctypes.byref(o), ctypes.byref(h), _stream(stream)))
+    return Pmg(h, (list(meshes), list(qdata64), qdata_lo))
+
+
+def ceed_pmg_vcycle(pmg: Pmg, r, z, stream=None):
+    _check(_lib.ceed_pmg_vcycle(pmg.handle, _ptr(r), _ptr(z), _stream(stream)))
+
+
+def ceed_pmg_prolong(pmg: Pmg, level, uc, uf, stream=None):
+    _check(_lib.ceed_pmg_prolong(pmg.handle, level, _ptr(uc), _ptr(uf), _stream(stream)))
+
+
+def ceed_pmg_restrict(pmg: Pmg, level, rf, rc, stream=None):
+    _check(_lib.ceed_pmg_restrict(pmg.handle, level, _ptr(rf), _ptr(rc), _stream(stream)))
+
+
+def ceed_pmg_info(pmg: Pmg, level) -> float:
+    lam = ctypes.c_double()
+    _check(_lib.ceed_pmg_info(pmg.handle, level, ctypes.byref(lam)))
+    return lam.value
+
+
+def ceed_pmg_destroy(pmg: Pmg):
+    pmg.close()
 
 
 def ceed_build_geometry(mesh: Mesh, geo, stream=None):

@@ -9,6 +9,8 @@
 #include <cmath>
 #include <cstring>
 #include <mutex>
+#include <new>
+#include <vector>
 
 #include "internal.h"
 
@@ -249,6 +251,7 @@ static size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
 
 struct Work {
   double *r_out, *d, *r, *z, *p, *q, *dinv, *part1, *part2;
+  double *r_old;    // flexible CG: residual of the previous iteration
   double *pq_part;  // per-block partial sums of p . q written by the fused apply
   Scalars *sc;
 };
@@ -270,6 +273,7 @@ static size_t layout(int64_t n, int64_t n_elem, bool mixed, char *base, Work *w)
   (void)mixed;
   t.r_out = (double *)take(vb);
   t.d = (double *)take(vb);
+  t.r_old = (double *)take(vb);
   t.pq_part = (double *)take((size_t)n_elem * sizeof(double));
   t.part1 = (double *)take(RED_MAX_BLOCKS * sizeof(double));
   t.part2 = (double *)take(RED_MAX_BLOCKS * sizeof(double));
@@ -355,6 +359,218 @@ static int residual(ceed_mesh_t m, const ApplyReq &op, const double *b, const do
   CEED_CUDA_CHECK(cudaGetLastError());
   CEED_CUDA_CHECK(cudaMemcpyAsync(rr, dsum, sizeof(double), cudaMemcpyDeviceToHost, s));
   CEED_CUDA_CHECK(cudaStreamSynchronize(s));
+  return CEED_OK;
+}
+
+
+// ---------------------------------------------------------------- p-multigrid (V-cycle)
+__global__ void cheb_init_kernel(double *__restrict__ x, double *__restrict__ r, double *__restrict__ d,
+                                 const double *__restrict__ b, const double *__restrict__ q,
+                                 const double *__restrict__ dinv, int64_t n, double inv_theta, int zero_x) {
+  CEEDGB_GRID4({
+    const double ri = zero_x ? b[k] : b[k] - q[k];
+    if (zero_x) x[k] = 0.0;
+    r[k] = ri;
+    d[k] = inv_theta * dinv[k] * ri;
+  })
+}
+
+// Chebyshev step (Saad, Iterative Methods, Chebyshev acceleration): x += d; r -= A d; d = c1 d + c2 D^{-1} r
+__global__ void cheb_step_kernel(double *__restrict__ x, double *__restrict__ r, double *__restrict__ d,
+                                 const double *__restrict__ q, const double *__restrict__ dinv, int64_t n, double c1,
+                                 double c2) {
+  CEEDGB_GRID4({
+    const double di = d[k];
+    x[k] += di;
+    const double ri = r[k] - q[k];
+    r[k] = ri;
+    d[k] = c1 * di + c2 * dinv[k] * ri;
+  })
+}
+
+__global__ void scale_kernel(double *__restrict__ v, const double *__restrict__ dinv, const double *__restrict__ w,
+                             int64_t n, double f) {
+  CEEDGB_GRID4(v[k] = f * dinv[k] * w[k];)
+}
+
+__global__ void seed_kernel(double *__restrict__ v, int64_t n) {
+  CEEDGB_GRID4({
+    uint64_t z = (uint64_t)k * 0x9E3779B97F4A7C15ull + 0x632BE59BD9B4E019ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    z ^= z >> 31;
+    v[k] = 0.5 + (double)(z >> 11) * (1.0 / 9007199254740992.0);
+  })
+}
+
+// FCG update: x += alpha p; r_old = r; r -= alpha q; partials of r.r
+__global__ void fcg_update_kernel(double *__restrict__ x, double *__restrict__ r, double *__restrict__ r_old,
+                                  const double *__restrict__ p, const double *__restrict__ q, int64_t n, double alpha,
+                                  double *__restrict__ part) {
+  __shared__ double sh[RED_THREADS];
+  double a[4] = {0.0, 0.0, 0.0, 0.0};
+  CEEDGB_GRID4({
+    x[k] += alpha * p[k];
+    const double ro = r[k];
+    r_old[k] = ro;
+    const double ri = ro - alpha * q[k];
+    r[k] = ri;
+    a[u_] += ri * ri;
+  })
+  const double t = block_sum((a[0] + a[1]) + (a[2] + a[3]), sh);
+  if (threadIdx.x == 0) part[blockIdx.x] = t;
+}
+
+__global__ void xpby_kernel(double *__restrict__ p, const double *__restrict__ z, int64_t n, double beta) {
+  CEEDGB_GRID4(p[k] = z[k] + beta * p[k];)
+}
+
+struct PmgLevel {
+  ceed_mesh_t mesh = nullptr;
+  int64_t n = 0;
+  ApplyReq op;              // smoothing operator (masked)
+  double *x = nullptr, *b = nullptr, *r = nullptr, *d = nullptr, *q = nullptr, *dinv = nullptr;
+  double lam = 1.0;
+};
+
+}  // namespace ceedgb
+
+struct ceed_pmg_s {
+  int L = 0;
+  ceedgb::PmgLevel lv[4];
+  ceed_pmg_opts o{};
+  char *cwork = nullptr;     // coarse-level CG workspace
+  ceedgb::Work cw;
+  double *dsum = nullptr;    // device scalar
+  double *part = nullptr;    // RED_MAX_BLOCKS partial sums
+  std::vector<void *> allocs;
+};
+
+namespace ceedgb {
+
+static double host_dot(const double *x, const double *y, int64_t n, double *part, double *dsum, cudaStream_t s,
+                       int *st) {
+  const int nb = red_blocks(n);
+  dot_partial_kernel<<<nb, RED_THREADS, 0, s>>>(x, y, n, part, nullptr);
+  sum_partials_kernel<<<1, RED_THREADS, 0, s>>>(part, nb, dsum);
+  double h = 0.0;
+  cudaError_t e = cudaMemcpyAsync(&h, dsum, sizeof(double), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) *st = cuda_fail(e, "dot");
+  return h;
+}
+
+// Chebyshev smoothing of A x = b on level l (x0 = 0 or the current x), `degree` products with A.
+static int pmg_cheb(ceed_pmg_s *P, int l, int degree, double lo, double hi, bool zero_x, cudaStream_t s) {
+  PmgLevel &L = P->lv[l];
+  const double theta = 0.5 * (hi + lo), delta = 0.5 * (hi - lo), sigma = theta / delta;
+  double rho = 1.0 / sigma;
+  if (!zero_x) {
+    ApplyReq a = L.op;
+    a.x = L.x;
+    a.y = L.q;
+    if (int st = launch_apply(L.mesh, a, s)) return st;
+  }
+  cheb_init_kernel<<<red_blocks(L.n), RED_THREADS, 0, s>>>(L.x, L.r, L.d, L.b, L.q, L.dinv, L.n, 1.0 / theta, zero_x);
+  for (int k = 0; k < degree; ++k) {
+    if (k == degree - 1) {
+      axpy_kernel<<<stream_blocks(L.n), 256, 0, s>>>(L.x, L.d, L.n);
+      break;
+    }
+    ApplyReq a = L.op;
+    a.x = L.d;
+    a.y = L.q;
+    if (int st = launch_apply(L.mesh, a, s)) return st;
+    const double rho_new = 1.0 / (2.0 * sigma - rho);
+    cheb_step_kernel<<<red_blocks(L.n), RED_THREADS, 0, s>>>(L.x, L.r, L.d, L.q, L.dinv, L.n, rho_new * rho,
+                                                              2.0 * rho_new / delta);
+    rho = rho_new;
+  }
+  CEED_CUDA_CHECK(cudaGetLastError());
+  return CEED_OK;
+}
+
+// V-cycle on level l: lv[l].x approximates A_l^{-1} lv[l].b.
+static int pmg_vcycle(ceed_pmg_s *P, int l, cudaStream_t s) {
+  PmgLevel &L = P->lv[l];
+  if (l == P->L - 1) {  // coarsest: Jacobi-PCG to coarse_tol
+    copy_kernel<<<stream_blocks(L.n), 256, 0, s>>>(P->cw.r, L.b, L.n);
+    int iters = 0, nonfin = 0;
+    if (int st = pcg_run(L.mesh, L.op, L.x, P->cw, L.n, P->o.coarse_tol, P->o.coarse_max_iter, 50, 0, s, &iters,
+                         &nonfin))
+      return st;
+    return CEED_OK;
+  }
+  const double hi = 1.1 * L.lam, lo = hi / P->o.smooth_ratio;
+  if (int st = pmg_cheb(P, l, P->o.smooth_degree, lo, hi, true, s)) return st;
+  {  // residual r = b - A x
+    ApplyReq a = L.op;
+    a.x = L.x;
+    a.y = L.q;
+    if (int st = launch_apply(L.mesh, a, s)) return st;
+    residual_kernel<<<red_blocks(L.n), RED_THREADS, 0, s>>>(L.b, L.q, L.r, L.n, P->part);
+  }
+  PmgLevel &C = P->lv[l + 1];
+  if (int st = launch_restrict(C.mesh, L.mesh, L.r, C.b, s)) return st;
+  if (int st = pmg_vcycle(P, l + 1, s)) return st;
+  if (int st = launch_prolong(C.mesh, L.mesh, C.x, L.x, 1, s)) return st;
+  return pmg_cheb(P, l, P->o.smooth_degree, lo, hi, false, s);
+}
+
+// Flexible CG (Notay): beta = (z_{k+1} . (r_{k+1} - r_k)) / (z_k . r_k), preconditioned by one V-cycle.
+static int fcg_run(ceed_mesh_t m, const ApplyReq &op64, ceed_pmg_s *P, double *x, const double *b, const Work &w,
+                   int64_t n, double tol, int max_iter, cudaStream_t s, int *iters_out, int *nonfin) {
+  int st = CEED_OK;
+  const double bb = host_dot(b, b, n, w.part1, &w.sc->bb_out, s, &st);
+  if (st) return st;
+  zero_kernel<<<stream_blocks(n), 256, 0, s>>>(x, n);
+  copy_kernel<<<stream_blocks(n), 256, 0, s>>>(w.r, b, n);
+  PmgLevel &F = P->lv[0];
+  auto precond = [&](const double *r, double *z) -> int {
+    copy_kernel<<<stream_blocks(n), 256, 0, s>>>(F.b, r, n);
+    if (int e = pmg_vcycle(P, 0, s)) return e;
+    copy_kernel<<<stream_blocks(n), 256, 0, s>>>(z, F.x, n);
+    return CEED_OK;
+  };
+  if ((st = precond(w.r, w.z))) return st;
+  copy_kernel<<<stream_blocks(n), 256, 0, s>>>(w.p, w.z, n);
+  double rz = host_dot(w.r, w.z, n, w.part1, &w.sc->rr_out, s, &st);
+  if (st) return st;
+  int it = 0;
+  *nonfin = 0;
+  while (it < max_iter) {
+    ApplyReq a = op64;
+    a.x = w.p;
+    a.y = w.q;
+    if ((st = launch_apply(m, a, s))) return st;
+    const double pq = host_dot(w.p, w.q, n, w.part1, &w.sc->rr_out, s, &st);
+    if (st) return st;
+    const double alpha = rz / pq;
+    if (!std::isfinite(alpha)) {
+      *nonfin = 1;
+      break;
+    }
+    const int nb = red_blocks(n);
+    fcg_update_kernel<<<nb, RED_THREADS, 0, s>>>(x, w.r, w.r_old, w.p, w.q, n, alpha, w.part1);
+    sum_partials_kernel<<<1, RED_THREADS, 0, s>>>(w.part1, nb, &w.sc->rr_out);
+    double rr = 0.0;
+    CEED_CUDA_CHECK(cudaMemcpyAsync(&rr, &w.sc->rr_out, sizeof(double), cudaMemcpyDeviceToHost, s));
+    CEED_CUDA_CHECK(cudaStreamSynchronize(s));
+    ++it;
+    if (!std::isfinite(rr)) {
+      *nonfin = 1;
+      break;
+    }
+    if (rr <= tol * tol * bb) break;
+    if ((st = precond(w.r, w.z))) return st;
+    const double zr = host_dot(w.z, w.r, n, w.part1, &w.sc->rr_out, s, &st);
+    const double zro = host_dot(w.z, w.r_old, n, w.part1, &w.sc->rr_out, s, &st);
+    if (st) return st;
+    const double beta = (zr - zro) / rz;
+    rz = zr;
+    xpby_kernel<<<red_blocks(n), RED_THREADS, 0, s>>>(w.p, w.z, n, beta);
+  }
+  *iters_out = it;
   return CEED_OK;
 }
 
@@ -480,9 +696,15 @@ extern "C" int ceed_cg_solve(ceed_mesh_t m, const void *qdata, int prec, const d
       copy_kernel<<<stream_blocks(n), 256, 0, s>>>(w.r, w.r_out, n);
       const double inner = mixed ? o.inner_tol : std::min(0.5, 0.5 * o.tol / report->rel_residual);
       int iters = 0, nonfin = 0;
-      if (int st = pcg_run(m, mixed ? oplo : op64, w.d, w, n, inner, o.max_iter - total, o.check_every, 0, s, &iters,
-                           &nonfin))
+      if (!mixed && o.pmg) {
+        // p-multigrid-preconditioned flexible CG on A d = r_out
+        if (int st = fcg_run(m, op64, (ceed_pmg_s *)o.pmg, w.d, w.r_out, w, n, inner, o.max_iter - total, s, &iters,
+                             &nonfin))
+          return st;
+      } else if (int st = pcg_run(m, mixed ? oplo : op64, w.d, w, n, inner, o.max_iter - total, o.check_every, 0, s,
+                                  &iters, &nonfin)) {
         return st;
+      }
       total += iters;
       outer += 1;
       if (nonfin) {
@@ -566,5 +788,131 @@ extern "C" int ceed_dot_noalloc(const double *x, const double *y, int64_t n, dou
   dot_chunk_kernel<<<nb, RED_THREADS, 0, s>>>(x, y, n, scratch);
   sum_partials_kernel<<<1, RED_THREADS, 0, s>>>(scratch, nb, out);
   CEED_CUDA_CHECK(cudaGetLastError());
+  return CEED_OK;
+}
+
+// ---------------------------------------------------------------- p-multigrid API
+static void pmg_free(ceed_pmg_s *P) {
+  if (!P) return;
+  for (void *a : P->allocs) cudaFree(a);
+  delete P;
+}
+
+extern "C" int ceed_pmg_create(int nlevels, const ceed_mesh_t *meshes, const void *const *qdata64,
+                               const void *const *qdata_lo, const ceed_pmg_opts *opts, ceed_pmg_t *out, void *stream) {
+  if (!out || !meshes || !qdata64) return fail(CEED_ERR_INVALID, "null p-multigrid argument");
+  *out = nullptr;
+  if (nlevels < 2 || nlevels > 4) return fail(CEED_ERR_INVALID, "p-multigrid needs 2..4 levels");
+  for (int l = 0; l < nlevels; ++l) {
+    if (!meshes[l] || !qdata64[l]) return fail(CEED_ERR_INVALID, "null mesh or qdata in a level");
+    if (!meshes[l]->has_dirichlet) return fail(CEED_ERR_INVALID, "p-multigrid levels need the Dirichlet mask");
+  }
+  for (int l = 0; l + 1 < nlevels; ++l)
+    if (int st = check_transfer_pair(meshes[l + 1], meshes[l])) return st;
+  cudaStream_t s = (cudaStream_t)stream;
+  ceed_pmg_s *P = new (std::nothrow) ceed_pmg_s();
+  if (!P) return fail(CEED_ERR_OOM, "host allocation");
+  if (opts) P->o = *opts;
+  if (P->o.smooth_degree <= 0) P->o.smooth_degree = 3;
+  if (P->o.smooth_ratio <= 1.0) P->o.smooth_ratio = 10.0;
+  if (P->o.eig_iters <= 0) P->o.eig_iters = 20;
+  if (P->o.coarse_tol <= 0) P->o.coarse_tol = 1e-2;
+  if (P->o.coarse_max_iter <= 0) P->o.coarse_max_iter = 500;
+  P->L = nlevels;
+  auto dalloc = [&](size_t bytes, void **ptr) -> int {
+    cudaError_t e = cudaMalloc(ptr, bytes);
+    if (e != cudaSuccess) return cuda_fail(e, "p-multigrid allocation");
+    P->allocs.push_back(*ptr);
+    return CEED_OK;
+  };
+  int st = CEED_OK;
+  for (int l = 0; l < nlevels && !st; ++l) {
+    PmgLevel &L = P->lv[l];
+    L.mesh = meshes[l];
+    L.n = meshes[l]->n_ldof;
+    L.op.op = CEED_OP_DIFFUSION;
+    const bool lo = qdata_lo && qdata_lo[l];
+    L.op.prec = lo ? P->o.prec_lo : CEED_F64;
+    L.op.qdata = lo ? qdata_lo[l] : qdata64[l];
+    L.op.ncol = 1;
+    L.op.masked = 1;
+    double **vecs[6] = {&L.x, &L.b, &L.r, &L.d, &L.q, &L.dinv};
+    for (double **v : vecs)
+      if (!st) st = dalloc(L.n * sizeof(double), (void **)v);
+    if (!st) st = ceed_jacobi_diagonal(L.mesh, CEED_OP_DIFFUSION, qdata64[l], CEED_F64, L.dinv, CEED_APPLY_DIRICHLET, stream);
+    if (!st) invert_kernel<<<stream_blocks(L.n), 256, 0, s>>>(L.dinv, L.n);
+  }
+  if (!st) st = dalloc(RED_MAX_BLOCKS * sizeof(double), (void **)&P->part);
+  if (!st) st = dalloc(sizeof(double), (void **)&P->dsum);
+  if (!st) {  // coarse CG workspace
+    PmgLevel &C = P->lv[nlevels - 1];
+    const size_t bytes = layout(C.n, C.mesh->E, false, nullptr, nullptr);
+    st = dalloc(bytes, (void **)&P->cwork);
+    if (!st) layout(C.n, C.mesh->E, false, P->cwork, &P->cw);
+    if (!st) copy_kernel<<<stream_blocks(C.n), 256, 0, s>>>(P->cw.dinv, C.dinv, C.n);
+  }
+  // lambda_max of D^{-1} A for every smoothed level (power iteration on the smoothing operator)
+  for (int l = 0; l + 1 < nlevels && !st; ++l) {
+    PmgLevel &L = P->lv[l];
+    seed_kernel<<<red_blocks(L.n), RED_THREADS, 0, s>>>(L.x, L.n);
+    double lam = 1.0;
+    for (int it = 0; it < P->o.eig_iters && !st; ++it) {
+      const double nx = std::sqrt(host_dot(L.x, L.x, L.n, P->part, P->dsum, s, &st));
+      if (st) break;
+      ApplyReq a = L.op;
+      a.x = L.x;
+      a.y = L.q;
+      st = launch_apply(L.mesh, a, s);
+      if (st) break;
+      scale_kernel<<<red_blocks(L.n), RED_THREADS, 0, s>>>(L.d, L.dinv, L.q, L.n, 1.0);
+      const double nd = std::sqrt(host_dot(L.d, L.d, L.n, P->part, P->dsum, s, &st));
+      lam = nd / nx;
+      scale_kernel<<<red_blocks(L.n), RED_THREADS, 0, s>>>(L.x, L.dinv, L.q, L.n, 1.0 / nd);
+    }
+    L.lam = lam;
+  }
+  if (!st) {
+    cudaError_t e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) st = cuda_fail(e, "p-multigrid setup");
+  }
+  if (st) {
+    pmg_free(P);
+    return st;
+  }
+  *out = P;
+  return CEED_OK;
+}
+
+extern "C" int ceed_pmg_vcycle(ceed_pmg_t P, const double *r, double *z, void *stream) {
+  if (!P || !r || !z) return fail(CEED_ERR_INVALID, "bad V-cycle arguments");
+  cudaStream_t s = (cudaStream_t)stream;
+  PmgLevel &F = P->lv[0];
+  copy_kernel<<<stream_blocks(F.n), 256, 0, s>>>(F.b, r, F.n);
+  if (int st = pmg_vcycle(P, 0, s)) return st;
+  copy_kernel<<<stream_blocks(F.n), 256, 0, s>>>(z, F.x, F.n);
+  CEED_CUDA_CHECK(cudaGetLastError());
+  return CEED_OK;
+}
+
+extern "C" int ceed_pmg_prolong(ceed_pmg_t P, int level, const double *uc, double *uf, void *stream) {
+  if (!P || level < 0 || level + 1 >= P->L || !uc || !uf) return fail(CEED_ERR_INVALID, "bad prolongation arguments");
+  return launch_prolong(P->lv[level + 1].mesh, P->lv[level].mesh, uc, uf, 0, (cudaStream_t)stream);
+}
+
+extern "C" int ceed_pmg_restrict(ceed_pmg_t P, int level, const double *rf, double *rc, void *stream) {
+  if (!P || level < 0 || level + 1 >= P->L || !rf || !rc) return fail(CEED_ERR_INVALID, "bad restriction arguments");
+  return launch_restrict(P->lv[level + 1].mesh, P->lv[level].mesh, rf, rc, (cudaStream_t)stream);
+}
+
+extern "C" int ceed_pmg_info(ceed_pmg_t P, int level, double *lambda_max) {
+  if (!P || level < 0 || level >= P->L) return fail(CEED_ERR_INVALID, "bad level");
+  if (lambda_max) *lambda_max = P->lv[level].lam;
+  return CEED_OK;
+}
+
+extern "C" int ceed_pmg_destroy(ceed_pmg_t P) {
+  if (!P) return CEED_OK;
+  cudaDeviceSynchronize();
+  pmg_free(P);
   return CEED_OK;
 }

@@ -137,4 +137,9 @@ int launch_apply_f32(ceed_mesh_t m, const ApplyReq &r, cudaStream_t s);
 int launch_apply_qf32geo(ceed_mesh_t m, const ApplyReq &r, cudaStream_t s);
 int launch_apply(ceed_mesh_t m, const ApplyReq &r, cudaStream_t s);
 
+// p-multigrid transfers (pmg_kernels.cu)
+int check_transfer_pair(ceed_mesh_t coarse, ceed_mesh_t fine);
+int launch_prolong(ceed_mesh_t coarse, ceed_mesh_t fine, const double *uc, double *uf, int add, cudaStream_t s);
+int launch_restrict(ceed_mesh_t coarse, ceed_mesh_t fine, const double *rf, double *rc, cudaStream_t s);
+
 }  // namespace ceedgb

@@ -165,3 +165,30 @@ def test_cost_model_values():
     assert fem.cost_model(7) == (3584, 56832)
     assert fem.cost_model(7, collocated=False) == (3584, 105984)
     assert fem.cost_model(1) == (56, 312)
+
+
+@pytest.mark.parametrize("pc,pf", [(1, 2), (1, 7), (3, 7), (2, 4), (4, 8)])
+def test_prolongation_reproduces_coarse_functions(pc, pf):
+    # a coarse finite-element function evaluated at the fine nodes: on an affine mesh a polynomial of
+    # degree <= pc per direction is reproduced exactly (checked at the fine nodes' physical points)
+    mc = synthetic.HexMesh(2, 2, 1, pc, perturb=0.0)
+    mf = synthetic.HexMesh(2, 2, 1, pf, perturb=0.0)
+    spc, spf = fem.Space(pc, "gll"), fem.Space(pf, "gll")
+    Xc, _ = fem.trilinear_map(mc.vertices, spc.XI)
+    Xf, _ = fem.trilinear_map(mf.vertices, spf.XI)
+    f = lambda X: (X[..., 0] ** pc) * (1 + X[..., 1]) - 2 * X[..., 2] ** min(pc, 2) + 0.5
+    uc = np.zeros(mc.n_ldof)
+    uc[mc.elem_dofs.reshape(-1)] = f(Xc).reshape(-1)
+    uf = fem.prolongate(pc, pf, mc.elem_dofs, mf.elem_dofs, uc, mf.n_ldof)
+    ref = np.zeros(mf.n_ldof)
+    ref[mf.elem_dofs.reshape(-1)] = f(Xf).reshape(-1)
+    np.testing.assert_allclose(uf, ref, atol=1e-13)
+    # the restriction is the exact transpose of the assembled prolongation
+    rf = synthetic.uniform(mf.n_ldof, seed=3)
+    rc = fem.restrict(pc, pf, mc.elem_dofs, mf.elem_dofs, rf, mc.n_ldof)
+    v = synthetic.uniform(mc.n_ldof, seed=4)
+    Pv = fem.prolongate(pc, pf, mc.elem_dofs, mf.elem_dofs, v, mf.n_ldof)
+    assert abs(rc @ v - rf @ Pv) <= 1e-12 * abs(rf @ Pv)
+    # element matrix rows sum to one (partition of unity of the coarse basis)
+    M = fem.prolongation_element(pc, pf)
+    np.testing.assert_allclose(M.sum(1), 1.0, atol=1e-13)
