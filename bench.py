@@ -188,7 +188,7 @@ def run_profile(args):
     m = synthetic.cube_mesh(wl["N"], wl["p"], seed=0)
     mesh = ceed.ceed_setup_mesh(m.n_elem, m.n_ldof, wl["p"], torch.from_numpy(m.elem_dofs).cuda(),
                                 torch.from_numpy(m.vertices).cuda(), torch.from_numpy(m.boundary).cuda())
-    prec = {"f64": ceed.CEED_F64, "f32": ceed.CEED_F32, "bf16": ceed.CEED_BF16}[args.profile]
+    prec = {"f64": ceed.CEED_F64, "f32": ceed.CEED_F32, "bf16": ceed.CEED_BF16, "f64df": ceed.CEED_F64_DF}[args.profile]
     qd = ceed.alloc_qdata(mesh, ceed.CEED_OP_DIFFUSION, prec)
     ceed.ceed_build_qdata(mesh, ceed.CEED_OP_DIFFUSION, ceed.CEED_COEFF_SINE, None, prec, qd)
     x = torch.from_numpy(synthetic.uniform(m.n_ldof, seed=1)).cuda()
@@ -294,12 +294,13 @@ def main():
     ap.add_argument("--cg-workload", default="c2", choices=sorted(WORKLOADS))
     ap.add_argument("--cpu-sample", type=int, default=40000, help="elements in the timed oracle sample")
     ap.add_argument("--ref-sample", type=int, default=1000, help="elements per reference-arm step")
-    ap.add_argument("--profile", default=None, choices=["f64", "f32", "bf16"],
+    ap.add_argument("--profile", default=None, choices=["f64", "f32", "bf16", "f64df"],
                     help="profiling case: set up the workload, run three applies in this precision, exit")
     ap.add_argument("--variant", default=None, help="ne,stage for --profile (default: autotune)")
     ap.add_argument("--autotune", type=int, default=1, help="autotune the apply kernel before timing")
     ap.add_argument("--batched", type=int, default=1, help="measure the batched mixed-order apply")
     ap.add_argument("--adjoint", type=int, default=1, help="measure the adjoint kernels")
+    ap.add_argument("--df", type=int, default=1, help="measure the double-float FP64-accurate operator")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -375,6 +376,30 @@ def main():
     ms_launch = ms64 / launches_per_apply
     flops_launch = flops_el * m.n_elem / launches_per_apply
     achieved_tf = flops_launch / (ms_launch * 1e-3) / 1e12
+
+    # ---------------- FP64-accurate operator on the FP32 pipe (double-float), and its agreement with FP64
+    f64df = None
+    if args.df:
+        qdf = ceed.alloc_qdata(mesh, ceed.CEED_OP_DIFFUSION, ceed.CEED_F64_DF, dev)
+        ceed.ceed_build_qdata(mesh, ceed.CEED_OP_DIFFUSION, ceed.CEED_COEFF_SINE, None, ceed.CEED_F64_DF, qdf)
+        ydf = torch.empty_like(x)
+        if args.autotune:
+            ne, st, tms = ceed.ceed_autotune_apply(mesh, ceed.CEED_OP_DIFFUSION, qdf, ceed.CEED_F64_DF, x, ydf)
+            variants["f64_df"] = {"elems_per_block": ne, "tma_staging": st, "tuning_ms": tms}
+        ms_df = timed(lambda: ceed.ceed_apply_diffusion(mesh, qdf, ceed.CEED_F64_DF, x, ydf), args.steps, args.warmup)
+        ceed.ceed_apply_diffusion(mesh, qd64, ceed.CEED_F64, x, y)
+        ceed.ceed_apply_diffusion(mesh, qdf, ceed.CEED_F64_DF, x, ydf)
+        torch.cuda.synchronize()
+        rel = float(torch.linalg.vector_norm(ydf - y) / torch.linalg.vector_norm(y))
+        relmax = float((ydf - y).abs().max() / y.abs().max())
+        f64df = {"gdofs": ws * n_apply / ms_df / 1e6, "ms": ms_df, "dtype": "f32x2 (double-float, compensated dot)",
+                 "rel_l2_vs_fp64": rel, "rel_max_vs_fp64": relmax,
+                 "flops_tflops_paper_model": flops_el * m.n_elem / (ms_df * 1e-3) / 1e12,
+                 "hbm_gbs": algorithmic_bytes(m, 8) / (ms_df * 1e-3) / 1e9,
+                 "hbm_frac": algorithmic_bytes(m, 8) / (ms_df * 1e-3) / 1e9 / hbm_peak,
+                 "speedup_vs_native_fp64": ms64 / ms_df}
+        del qdf, ydf
+        torch.cuda.empty_cache()
 
     # ---------------- FP32-arithmetic operator (mixed), FP32 and BF16 quadrature data
     mixed = {}
@@ -509,6 +534,7 @@ def main():
                          "flops_per_launch": flops_launch, "ms_per_launch": ms_launch,
                          "hbm_gbs": bytes64 / (ms64 * 1e-3) / 1e9, "hbm_peak": hbm_peak, "hbm_peak_kind": hbm_kind,
                          "hbm_frac": bytes64 / (ms64 * 1e-3) / 1e9 / hbm_peak},
+            "fp64_accurate_fp32_pipe": f64df,
             "mixed_apply": mixed,
             "apply_variants": variants,
             "e2e": {"value": ws * n_apply / ms_e2e / 1e6,

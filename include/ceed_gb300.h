@@ -49,8 +49,12 @@ typedef enum {
  * F64 -> FP64 contractions; F32/BF16/F16 -> FP32 contractions (FP64 L-vectors in and out).
  * F32_GEO (diffusion only) -> FP32 contractions with the geometric factors recomputed from the
  * trilinear element map at every application: the quadrature data holds only the map's 8
- * coefficient vectors per element and w k per point (FP32), about 1/6 of the F32 bytes. */
-typedef enum { CEED_F64 = 0, CEED_F32 = 1, CEED_BF16 = 2, CEED_F16 = 3, CEED_F32_GEO = 4 } ceed_prec;
+ * coefficient vectors per element and w k per point (FP32), about 1/6 of the F32 bytes.
+ * F64_DF (GLL-collocated diffusion only) -> an FP64-accurate operator computed on the FP32 pipe:
+ * values and quadrature data carried as double-float pairs (hi + lo, about 48 bits) and every
+ * contraction summed with a compensated dot product; agrees with the FP64 operator to ~1e-14
+ * relative on well-conditioned inputs (FP64 L-vectors in and out, qdata 8 bytes per value). */
+typedef enum { CEED_F64 = 0, CEED_F32 = 1, CEED_BF16 = 2, CEED_F16 = 3, CEED_F32_GEO = 4, CEED_F64_DF = 5 } ceed_prec;
 
 /* Quadrature: GLL = collocated on the p+1 Gauss-Lobatto nodes (BP5 style, Q = p+1);
  * GAUSS = Q Gauss-Legendre points per direction (BP1/BP3 style, default Q = p+2). */

@@ -19,7 +19,7 @@ CEED_OK, CEED_ERR_INVALID, CEED_ERR_CUDA, CEED_ERR_OOM = 0, 1, 2, 3
 CEED_ERR_NOT_CONVERGED, CEED_ERR_UNSUPPORTED, CEED_ERR_BAD_GEOMETRY = 4, 5, 6
 CEED_ERR_TIMEOUT, CEED_ERR_NONFINITE = 7, 8
 # ceed_prec
-CEED_F64, CEED_F32, CEED_BF16, CEED_F16, CEED_F32_GEO = 0, 1, 2, 3, 4
+CEED_F64, CEED_F32, CEED_BF16, CEED_F16, CEED_F32_GEO, CEED_F64_DF = 0, 1, 2, 3, 4, 5
 # ceed_qrule / ceed_op / ceed_coeff
 CEED_QRULE_GLL, CEED_QRULE_GAUSS = 0, 1
 CEED_OP_MASS, CEED_OP_DIFFUSION = 0, 1
@@ -27,7 +27,7 @@ CEED_COEFF_ONE, CEED_COEFF_CONST, CEED_COEFF_SINE, CEED_COEFF_PER_QPT = 0, 1, 2,
 CEED_APPLY_DIRICHLET = 1
 CEED_CG_FP64, CEED_CG_MIXED = 0, 1
 
-PREC_BYTES = {CEED_F64: 8, CEED_F32: 4, CEED_BF16: 2, CEED_F16: 2, CEED_F32_GEO: 4}
+PREC_BYTES = {CEED_F64: 8, CEED_F32: 4, CEED_BF16: 2, CEED_F16: 2, CEED_F32_GEO: 4, CEED_F64_DF: 8}
 
 
 class CeedError(RuntimeError):

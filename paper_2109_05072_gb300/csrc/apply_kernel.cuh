@@ -28,11 +28,13 @@
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
+#include "df.cuh"
 #include "internal.h"
 
 namespace ceedgb {
 
 // ------------------------------------------------------------------ storage conversions
+__device__ __forceinline__ DF q_to(DF v, DF) { return v; }
 __device__ __forceinline__ double q_to(double v, double) { return v; }
 __device__ __forceinline__ float q_to(float v, float) { return v; }
 __device__ __forceinline__ float q_to(__nv_bfloat16 v, float) { return __bfloat162float(v); }
@@ -94,6 +96,15 @@ __device__ __forceinline__ float d2f_exact(double d) {
 
 template <typename T>
 struct LVec;
+template <>
+struct LVec<DF> {     // FP64-accurate double-float operator: split on the way in, one FP64 add on the way out
+  static __device__ __forceinline__ DF in(double v) {
+    const float h = d2f_fast(v);
+    return DF(h, d2f_fast(v - f2d_int(h)));
+  }
+  static __device__ __forceinline__ double out(DF v) { return f2d_int(v.hi) + f2d_int(v.lo); }
+  static __device__ __forceinline__ double add(double old, DF v) { return (old + f2d_int(v.hi)) + f2d_int(v.lo); }
+};
 template <>
 struct LVec<double> {  // FP64 operator: native
   static __device__ __forceinline__ double in(double v) { return v; }
@@ -175,6 +186,61 @@ __device__ __forceinline__ void eo_apply(const EOMat<T> &M, const T *v, T *out) 
 
 constexpr int APPLY_MAX_THREADS = 256;
 constexpr int APPLY_MAX_NE = 32;
+
+// g1 a + g2 b + g3 c and a + b + c: plain FMAs for float/double, compensated for double-float
+template <typename T>
+__device__ __forceinline__ T dot3(T g1, T a, T g2, T b, T g3, T c) {
+  return g1 * a + g2 * b + g3 * c;
+}
+template <>
+__device__ __forceinline__ DF dot3<DF>(DF g1, DF a, DF g2, DF b, DF g3, DF c) {
+  DFAcc A{0.f, 0.f};
+  acc_mac(A, g1, a);
+  acc_mac(A, g2, b);
+  acc_mac(A, g3, c);
+  return acc_get(A);
+}
+template <typename T>
+__device__ __forceinline__ T add3(T a, T b, T c) {
+  return a + b + c;
+}
+template <>
+__device__ __forceinline__ DF add3<DF>(DF a, DF b, DF c) {
+  return df_add(df_add(a, b), c);
+}
+
+// Even-odd 1D operator in double-float: folds/unfolds by exact-sum additions, the two half-size
+// products by compensated dot products (same algebra as the float/double version below).
+template <int NO, int NI, int S>
+__device__ __forceinline__ void eo_apply(const EOMat<DF> &M, const DF *v, DF *out) {
+  constexpr int HI = NI / 2, HO = NO / 2;
+  DF e[HI > 0 ? HI : 1], o[HI > 0 ? HI : 1];
+#pragma unroll
+  for (int j = 0; j < HI; ++j) {
+    e[j] = df_add(v[j], v[NI - 1 - j]);
+    o[j] = df_sub(v[j], v[NI - 1 - j]);
+  }
+#pragma unroll
+  for (int i = 0; i < HO; ++i) {
+    DFAcc A{0.f, 0.f}, B{0.f, 0.f};
+    if (NI & 1) acc_mac(A, M.cmid[i], v[HI]);
+#pragma unroll
+    for (int j = 0; j < HI; ++j) {
+      acc_mac(A, M.E[i * EO_H + j], e[j]);
+      acc_mac(B, M.O[i * EO_H + j], o[j]);
+    }
+    const DF a = acc_get(A), b = acc_get(B);
+    out[i] = df_add(a, b);
+    out[NO - 1 - i] = (S > 0) ? df_sub(a, b) : df_sub(b, a);
+  }
+  if constexpr (NO & 1) {
+    DFAcc C{0.f, 0.f};
+    if (NI & 1) acc_mac(C, M.cc, v[HI]);
+#pragma unroll
+    for (int j = 0; j < HI; ++j) acc_mac(C, M.rmid[j], (S > 0) ? e[j] : o[j]);
+    out[HO] = acc_get(C);
+  }
+}
 
 template <int Q>
 constexpr int max_elems_per_block() {
@@ -416,9 +482,9 @@ __device__ __forceinline__ void apply_block(const ApplyArgs &a, const OpTab<T> &
           gss = q_to(sq[3 * NQ + q], T()), gst = q_to(sq[4 * NQ + q], T()), gtt = q_to(sq[5 * NQ + q], T());
         }
         const T ur = sb[tix<Q>(k, j, i)], us = sc[tix<Q>(k, j, i)];
-        sb[tix<Q>(k, j, i)] = grr * ur + grs * us + grt * ut[k];
-        sc[tix<Q>(k, j, i)] = grs * ur + gss * us + gst * ut[k];
-        vt[k] = grt * ur + gst * us + gtt * ut[k];
+        sb[tix<Q>(k, j, i)] = dot3(grr, ur, grs, us, grt, ut[k]);
+        sc[tix<Q>(k, j, i)] = dot3(grs, ur, gss, us, gst, ut[k]);
+        vt[k] = dot3(grt, ur, gst, us, gtt, ut[k]);
       }
       __syncthreads();
       {  // r transposed: owners (s = i, t = j)
@@ -441,7 +507,7 @@ __device__ __forceinline__ void apply_block(const ApplyArgs &a, const OpTab<T> &
       eo_apply<Q, Q, -1>(tab.eDT, vt, yt);
       __syncthreads();
 #pragma unroll
-      for (int k = 0; k < Q; ++k) w[k] = yt[k] + sa[tix<Q>(k, j, i)] + sc[tix<Q>(k, j, i)];
+      for (int k = 0; k < Q; ++k) w[k] = add3(yt[k], sa[tix<Q>(k, j, i)], sc[tix<Q>(k, j, i)]);
     }
 
     // ---- transposed interpolation back to the nodes

@@ -1,0 +1,84 @@
+// Double-float ("f32x2") arithmetic for an FP64-accurate operator computed on the FP32 pipe.
+//
+// GB300 issues about 60 FP32 FMAs for every FP64 FMA, so a value x is carried as an unevaluated sum
+// hi + lo of two floats (about 48 significant bits) and every contraction sum_m M_m v_m is evaluated
+// with the compensated dot product "Dot2" of Ogita, Rump and Oishi (SIAM J. Sci. Comput. 26, 2005):
+// exact products by FMA (TwoProduct), exact partial sums by Knuth's TwoSum, and the rounding errors
+// accumulated in a second float, which returns the sum as if computed in twice the working precision.
+// The cross terms m_hi v_lo + m_lo v_hi enter the error accumulator by FMA.  Results are renormalised
+// by TwoSum before they are stored.  Accuracy ~ 2^-47 relative per contraction (plus the condition of
+// the sum), versus 2^-53 for native FP64: enough for 1e-12 agreement with an FP64 reference.
+#pragma once
+
+#include <cuda_runtime.h>
+
+namespace ceedgb {
+
+struct DF {
+  float hi, lo;
+  DF() = default;
+  __host__ __device__ constexpr DF(float h, float l) : hi(h), lo(l) {}
+  __host__ __device__ constexpr DF(int v) : hi((float)v), lo(0.f) {}
+};
+
+// Knuth's TwoSum: s + e == a + b exactly.
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
+  s = a + b;
+  const float z = s - a;
+  e = (a - (s - z)) + (b - z);
+}
+
+__device__ __forceinline__ DF df_norm(DF a) {
+  float s, e;
+  two_sum(a.hi, a.lo, s, e);
+  return DF(s, e);
+}
+
+__device__ __forceinline__ DF df_add(DF a, DF b) {
+  float s, e;
+  two_sum(a.hi, b.hi, s, e);
+  return df_norm(DF(s, e + (a.lo + b.lo)));
+}
+
+__device__ __forceinline__ DF df_sub(DF a, DF b) {
+  float s, e;
+  two_sum(a.hi, -b.hi, s, e);
+  return df_norm(DF(s, e + (a.lo - b.lo)));
+}
+
+// Dot2 accumulator: s holds the running float sum of the product high parts, c every rounding error.
+struct DFAcc {
+  float s, c;
+};
+
+__device__ __forceinline__ void acc_mac(DFAcc &A, DF m, DF v) {
+  const float p = m.hi * v.hi;
+  float e = fmaf(m.hi, v.hi, -p);  // TwoProduct error, exact
+  e = fmaf(m.hi, v.lo, e);
+  e = fmaf(m.lo, v.hi, e);
+  float t, q;
+  two_sum(A.s, p, t, q);
+  A.s = t;
+  A.c += q + e;
+}
+
+__device__ __forceinline__ DF acc_get(const DFAcc &A) { return df_norm(DF(A.s, A.c)); }
+
+// y = sum_j M_j v_j over an NI-term row stored with stride 1 (used by the even-odd kernels).
+template <int N>
+__device__ __forceinline__ DF df_dot(const DF *m, const DF *v) {
+  DFAcc A{0.f, 0.f};
+#pragma unroll
+  for (int j = 0; j < N; ++j) acc_mac(A, m[j], v[j]);
+  return acc_get(A);
+}
+
+// Host/device split of a double into the nearest float and the float nearest to the remainder.
+__host__ __device__ inline DF df_from_double(double v) {
+  const float h = (float)v;
+  return DF(h, (float)(v - (double)h));
+}
+
+__device__ __forceinline__ double df_to_double(DF a) { return (double)a.hi + (double)a.lo; }
+
+}  // namespace ceedgb

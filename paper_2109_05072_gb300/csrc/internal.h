@@ -8,6 +8,7 @@
 #include <vector>
 
 #include "../../include/ceed_gb300.h"
+#include "df.cuh"
 
 namespace ceedgb {
 
@@ -94,9 +95,10 @@ struct ceed_mesh_s {
   bool has_dirichlet = false;
   ceedgb::OpTab<double> tab64;
   ceedgb::OpTab<float> tab32;
+  ceedgb::OpTab<ceedgb::DF> tabdf;     // double-float tables of the FP64-accurate FP32-pipe operator
   ceedgb::QRule rule;                   // quadrature rule of the mesh
   double gll_x[ceedgb::MAX_P];          // GLL nodes of the basis
-  ceedgb::ApplyChoice tuned[3][5];      // [op][prec] autotuned apply variant
+  ceedgb::ApplyChoice tuned[3][6];      // [op][prec] autotuned apply variant
 };
 
 namespace ceedgb {
@@ -135,6 +137,7 @@ struct ApplyReq {
 int launch_apply_f64(ceed_mesh_t m, const ApplyReq &r, cudaStream_t s);
 int launch_apply_f32(ceed_mesh_t m, const ApplyReq &r, cudaStream_t s);
 int launch_apply_qf32geo(ceed_mesh_t m, const ApplyReq &r, cudaStream_t s);
+int launch_apply_df(ceed_mesh_t m, const ApplyReq &r, cudaStream_t s);
 int launch_apply(ceed_mesh_t m, const ApplyReq &r, cudaStream_t s);
 
 // p-multigrid transfers (pmg_kernels.cu)

@@ -206,6 +206,11 @@ static void build_tables(ceed_mesh_s *m) {
     m->tab64.qx[i] = m->rule.x[i];
     m->tab32.qx[i] = (float)m->rule.x[i];
   }
+  // double-float copy of every FP64 table (same layout, each double split into hi + lo floats)
+  const double *src = reinterpret_cast<const double *>(&m->tab64);
+  DF *dst = reinterpret_cast<DF *>(&m->tabdf);
+  static_assert(sizeof(OpTab<double>) == sizeof(OpTab<DF>), "table layouts differ");
+  for (size_t k = 0; k < sizeof(OpTab<double>) / sizeof(double); ++k) dst[k] = df_from_double(src[k]);
 }
 
 int launch_apply(ceed_mesh_t m, const ApplyReq &r, cudaStream_t s);
@@ -224,6 +229,7 @@ int launch_apply_f32(ceed_mesh_t m, const ApplyReq &r, cudaStream_t s) {
 
 int launch_apply(ceed_mesh_t m, const ApplyReq &r, cudaStream_t s) {
   if (r.prec == CEED_F64) return launch_apply_f64(m, r, s);
+  if (r.prec == CEED_F64_DF) return launch_apply_df(m, r, s);
   if (r.prec == CEED_F32_GEO) {
     if (r.op != CEED_OP_DIFFUSION) return fail(CEED_ERR_UNSUPPORTED, "F32_GEO quadrature data is for diffusion");
     return launch_apply_qf32geo(m, r, s);
@@ -425,7 +431,8 @@ extern "C" int ceed_mesh_info(ceed_mesh_t m, int32_t *n_colors, int32_t *Q, int3
 
 size_t ceedgb::prec_size(int prec) {
   switch (prec) {
-    case CEED_F64: return 8;
+    case CEED_F64:
+    case CEED_F64_DF: return 8;
     case CEED_F32:
     case CEED_F32_GEO: return 4;
     case CEED_BF16:
@@ -450,7 +457,7 @@ static int apply_common(ceed_mesh_t m, int op, const void *qdata, int prec, cons
   if (x == y) return fail(CEED_ERR_INVALID, "x and y must not alias");
   if (nrhs < 1) return fail(CEED_ERR_INVALID, "nrhs must be >= 1");
   if (prec_size(prec) == 0) return fail(CEED_ERR_INVALID, "unknown precision");
-  if (prec < CEED_F64 || prec > CEED_F32_GEO) return fail(CEED_ERR_INVALID, "unknown precision");
+  if (prec < CEED_F64 || prec > CEED_F64_DF) return fail(CEED_ERR_INVALID, "unknown precision");
   ApplyReq r;
   r.op = op;
   r.prec = prec;
@@ -480,7 +487,7 @@ extern "C" int ceed_autotune_apply(ceed_mesh_t m, int op, const void *qdata, int
                                    int nrhs, int32_t *best_ne, int32_t *best_stage, float *best_ms, void *stream) {
   if (int st = check_mesh(m)) return st;
   if (op != CEED_OP_MASS && op != CEED_OP_DIFFUSION) return fail(CEED_ERR_INVALID, "unknown operator");
-  if (prec < CEED_F64 || prec > CEED_F32_GEO) return fail(CEED_ERR_INVALID, "unknown precision");
+  if (prec < CEED_F64 || prec > CEED_F64_DF) return fail(CEED_ERR_INVALID, "unknown precision");
   if (!qdata || !x || !y || x == y || nrhs < 1) return fail(CEED_ERR_INVALID, "bad autotune arguments");
   cudaStream_t s = (cudaStream_t)stream;
   const int ne_max = std::max(1, 256 / (m->Q * m->Q));
@@ -531,7 +538,7 @@ extern "C" int ceed_autotune_apply(ceed_mesh_t m, int op, const void *qdata, int
 extern "C" int ceed_set_apply_variant(ceed_mesh_t m, int op, int prec, int ne, int stage) {
   if (int st = check_mesh(m)) return st;
   if (op != CEED_OP_MASS && op != CEED_OP_DIFFUSION) return fail(CEED_ERR_INVALID, "unknown operator");
-  if (prec < CEED_F64 || prec > CEED_F32_GEO) return fail(CEED_ERR_INVALID, "unknown precision");
+  if (prec < CEED_F64 || prec > CEED_F64_DF) return fail(CEED_ERR_INVALID, "unknown precision");
   if (ne < 0 || ne > std::max(1, 256 / (m->Q * m->Q)) || (stage != 0 && stage != 1))
     return fail(CEED_ERR_INVALID, "elements per block must be 0 (default) .. 256 / Q^2, stage 0 or 1");
   m->tuned[op][prec].ne = ne;

@@ -17,6 +17,8 @@ template <>
 __device__ __forceinline__ __nv_bfloat16 to_store<__nv_bfloat16>(double v) { return __float2bfloat16_rn((float)v); }
 template <>
 __device__ __forceinline__ __half to_store<__half>(double v) { return __float2half_rn((float)v); }
+template <>
+__device__ __forceinline__ DF to_store<DF>(double v) { return df_from_double(v); }
 
 // One thread per (colour-sorted element, quadrature point).  Paper Section 2: the symmetric
 // geometric tensor G^e stored as six diagonal matrices; here G = w k adj(J) adj(J)^T / det J
@@ -253,6 +255,7 @@ static int build_qdata_impl(ceed_mesh_t m, int op, int coeff_kind, const double 
     case CEED_F32: CEEDGB_Q(float); break;
     case CEED_BF16: CEEDGB_Q(__nv_bfloat16); break;
     case CEED_F16: CEEDGB_Q(__half); break;
+    case CEED_F64_DF: CEEDGB_Q(DF); break;
     default: return fail(CEED_ERR_INVALID, "unknown precision");
   }
 #undef CEEDGB_Q

@@ -184,7 +184,8 @@ def test_setup_diagonal_and_rhs(ceed):
 
 @pytest.mark.parametrize("p,qkind,op,prec", [(7, "gll", "diffusion", 0), (7, "gll", "diffusion", 1),
                                              (3, "gauss", "mass", 0), (5, "gauss", "diffusion", 2), (2, "gll", "diffusion", 1),
-                                             (7, "gll", "diffusion", 4), (4, "gauss", "diffusion", 4)])
+                                             (7, "gll", "diffusion", 4), (4, "gauss", "diffusion", 4),
+                                             (7, "gll", "diffusion", 5)])
 def test_apply_variants_identical_and_autotune(ceed, p, qkind, op, prec):
     # every (elements per block, staging) variant runs the same arithmetic: bitwise-identical output
     m = synthetic.HexMesh(5, 3, 3, p, seed=13)
@@ -212,8 +213,38 @@ def test_apply_variants_identical_and_autotune(ceed, p, qkind, op, prec):
     assert torch.equal(y, outs[0])
     with pytest.raises(ceed.CeedError):
         ceed.ceed_set_apply_variant(mesh, cop, prec, ne_max + 1, 1)
-    if prec == 0:
+    if prec in (0, 5):
         sp_, qref = oracle_qdata(m, qkind, op, "sine")
         ref = fem.apply(sp_, m.elem_dofs, qref, x.cpu().numpy(), fem.DIFFUSION if op == "diffusion" else fem.MASS)
         assert rel_err(y.cpu().numpy(), ref) <= 1e-12
+    mesh.close()
+
+
+@pytest.mark.parametrize("p", list(range(1, 9)))
+def test_apply_double_float_matches_oracle(ceed, p):
+    # FP64-accurate operator on the FP32 pipe (double-float values, compensated contractions):
+    # the same 1e-12 bar as the FP64 operator
+    dims = (5, 3, 2) if p <= 4 else (3, 2, 2)
+    m = synthetic.HexMesh(*dims, p, seed=50 + p)
+    mesh = gpu_mesh(ceed, m, "gll")
+    qd = _qdata(ceed, mesh, "diffusion", ceed.CEED_F64_DF)
+    sp_, qref = oracle_qdata(m, "gll", "diffusion", "sine")
+    x = synthetic.uniform(m.n_ldof, seed=60 + p)
+    y = _apply(ceed, mesh, "diffusion", qd, ceed.CEED_F64_DF, x)
+    ref = fem.apply(sp_, m.elem_dofs, qref, x, fem.DIFFUSION)
+    err = rel_err(y, ref)
+    print(f"double-float p={p}: rel err {err:.2e}")
+    assert err <= 1e-12
+    assert np.abs(y - ref).max() <= 1e-12 * np.abs(ref).max()
+    # masked operator and several columns
+    ym = _apply(ceed, mesh, "diffusion", qd, ceed.CEED_F64_DF, x, flags=ceed.CEED_APPLY_DIRICHLET)
+    Am = fem.masked(lambda v: fem.apply(sp_, m.elem_dofs, qref, v, fem.DIFFUSION), m.boundary)
+    assert rel_err(ym, Am(x)) <= 1e-12
+    X = synthetic.uniform(m.n_ldof * 3, seed=70 + p).reshape(m.n_ldof, 3)
+    Y = _apply(ceed, mesh, "diffusion", qd, ceed.CEED_F64_DF, X.reshape(-1), nrhs=3).reshape(m.n_ldof, 3)
+    assert rel_err(Y, fem.apply(sp_, m.elem_dofs, qref, X, fem.DIFFUSION)) <= 1e-12
+    # not offered for Gauss quadrature or the mass operator
+    if p == 3:
+        with pytest.raises(ceed.CeedError):
+            _apply(ceed, mesh, "mass", qd, ceed.CEED_F64_DF, x)
     mesh.close()
