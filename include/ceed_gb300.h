@@ -232,10 +232,10 @@ int ceed_cg_solve(ceed_mesh_t mesh, const void *qdata, int prec, const double *b
  * with prec_lo selects an FP32-arithmetic smoothing operator.  The handle allocates its level
  * vectors at creation (several n_ldof-sized FP64 vectors per level).  Synchronizes `stream`. */
 typedef struct {
-  int32_t smooth_degree;    /* 0 -> 3 */
+  int32_t smooth_degree;    /* 0 -> 4 */
   double smooth_ratio;      /* 0 -> 10 */
   int32_t eig_iters;        /* 0 -> 20 */
-  double coarse_tol;        /* 0 -> 1e-2 */
+  double coarse_tol;        /* 0 -> 3e-2 */
   int32_t coarse_max_iter;  /* 0 -> 500 */
   int32_t prec_lo;          /* precision of qdata_lo (F32, BF16, F16, F32_GEO) */
 } ceed_pmg_opts;

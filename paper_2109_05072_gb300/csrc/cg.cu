@@ -813,10 +813,10 @@ extern "C" int ceed_pmg_create(int nlevels, const ceed_mesh_t *meshes, const voi
   ceed_pmg_s *P = new (std::nothrow) ceed_pmg_s();
   if (!P) return fail(CEED_ERR_OOM, "host allocation");
   if (opts) P->o = *opts;
-  if (P->o.smooth_degree <= 0) P->o.smooth_degree = 3;
+  if (P->o.smooth_degree <= 0) P->o.smooth_degree = 4;
   if (P->o.smooth_ratio <= 1.0) P->o.smooth_ratio = 10.0;
   if (P->o.eig_iters <= 0) P->o.eig_iters = 20;
-  if (P->o.coarse_tol <= 0) P->o.coarse_tol = 1e-2;
+  if (P->o.coarse_tol <= 0) P->o.coarse_tol = 3e-2;
   if (P->o.coarse_max_iter <= 0) P->o.coarse_max_iter = 500;
   P->L = nlevels;
   auto dalloc = [&](size_t bytes, void **ptr) -> int {
