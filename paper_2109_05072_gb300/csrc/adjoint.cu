@@ -1,15 +1,19 @@
 // Diffusion with a per-quadrature-point coefficient k and its adjoint (collocated GLL quadrature).
 //
 // A(k) = sum_e P_e^T D^T G^e(k) D P_e (paper Section 2's factored form) with G_q = k_q Ghat_q,
-// Ghat_q = w_q adj(J) adj(J)^T / det J, either read from stored FP64 geometry or recomputed from
-// the element's 8 vertices at every point.  For L = 0.5 ||A(k) x - b||^2 and r = A(k) x - b:
+// Ghat_q = w_q adj(J) adj(J)^T / det J, read from stored FP64 geometry or recomputed at every point
+// from the trilinear map.  For L = 0.5 ||A(k) x - b||^2 and r = A(k) x - b:
 //   dL/dx = A(k) r,   dL/dk_{e,q} = (grad_xi r)_q^T Ghat_q (grad_xi x)_q,
-// both from one fused pass over the elements (gather x and r, three derivative passes on each,
-// the pointwise products, transposed passes on k Ghat grad r, atomic-free scatter).
+// both from one fused pass over the elements: gather x and r, the three derivative passes on each
+// (line owners, even-odd 1D operators, padded shared tiles -- the same scheme as the apply kernel),
+// the pointwise products, transposed passes on k Ghat grad r, and the atomic-free colour scatter.
+// Geometry recomputation: x = a0 + a1 r + a2 s + a3 t + a4 rs + a5 rt + a6 st + a7 rst per element, so
+// along a thread's column of points only t varies and J costs 6 FMAs per point (coefficients from the
+// 8 vertices once per element, in shared memory).
 #include <algorithm>
 
+#include "apply_kernel.cuh"
 #include "geometry.cuh"
-#include "internal.h"
 
 namespace ceedgb {
 
@@ -24,27 +28,54 @@ struct KArgs {
   double *y;            // A(k) x, or dL/dx = A(k) r
   double *dLdk;         // adjoint only, caller order
   int64_t e_begin, e_count;
+  int64_t gstride;      // stored geometry per element (doubles)
   int masked;
   QRule rule;
   OpTab<double> tab;
 };
 
+template <int P>
+constexpr int kop_ne() {
+  return (P * P >= 128) ? 1 : (128 / (P * P));
+}
+
 template <int P, bool ADJ>
-__global__ void __launch_bounds__(P * P * (P * P >= 128 ? 1 : 128 / (P * P))) kop_kernel(const KArgs a) {
-  constexpr int NE = (P * P >= 128) ? 1 : (128 / (P * P));
+constexpr size_t kop_elem_smem() {
+  return ((size_t)(ADJ ? 5 : 3) * tile_words<P>() * sizeof(double) + 24 * sizeof(double) + 127) & ~(size_t)127;
+}
+
+template <int P, bool ADJ>
+__global__ void __launch_bounds__(P * P * kop_ne<P>()) kop_kernel(const KArgs a) {
+  constexpr int NE = kop_ne<P>();
   constexpr int NPT = P * P, ND = P * P * P;
-  __shared__ double smem[NE][ADJ ? 3 : 2][ND];
-  __shared__ double sv[NE][24];
+  constexpr int TW = tile_words<P>();
+  extern __shared__ __align__(128) unsigned char smem_raw[];
   const int tid = threadIdx.x;
   const int el = tid / NPT;
   const int ij = tid - el * NPT;
   const int i = ij % P, j = ij / P;
   const int64_t e = a.e_begin + (int64_t)blockIdx.x * NE + el;
   const bool active = e < a.e_begin + a.e_count;
-  double *s0 = smem[el][0], *s1 = smem[el][1];
-  double *s2 = smem[el][ADJ ? 2 : 1];
-  if (!a.geo)
-    for (int t = ij; t < 24; t += NPT) sv[el][t] = active ? a.vert[e * 24 + t] : 0.0;
+  double *t0 = (double *)(smem_raw + el * kop_elem_smem<P, ADJ>());
+  double *t1 = t0 + TW, *t2 = t1 + TW;
+  double *t3 = t2 + TW, *t4 = t3 + TW;  // adjoint only
+  double *coef = t0 + (ADJ ? 5 : 3) * TW;  // a1..a7 (21 values)
+
+  if (!a.geo)  // trilinear-map coefficients of this element
+    for (int t = ij; t < 21; t += NPT) {
+    double v = 0.0;
+    if (active) {
+      const int n = t / 3, c = t % 3;  // coefficient a_{n+1}, coordinate c
+      const double *V = a.vert + e * 24;
+#pragma unroll
+      for (int w = 0; w < 8; ++w) {
+        const double sr = (w & 1) ? 1.0 : -1.0, ss = (w & 2) ? 1.0 : -1.0, st = (w & 4) ? 1.0 : -1.0;
+        const double sg[7] = {sr, ss, st, sr * ss, sr * st, ss * st, sr * ss * st};
+        v += 0.125 * sg[n] * V[w * 3 + c];
+      }
+    }
+    coef[t] = v;
+  }
 
   uint32_t idx[P];
   double u[P], rv[P];
@@ -53,88 +84,144 @@ __global__ void __launch_bounds__(P * P * (P * P >= 128 ? 1 : 128 / (P * P))) ko
     idx[c] = active ? __ldg(a.emap + e * ND + (c * P + j) * P + i) : 0u;
     const bool dir = a.masked && (idx[c] & FLAG_DIR);
     const int64_t dof = idx[c] & DOF_MASK;
-    u[c] = (active && !dir) ? a.x[dof] : 0.0;
-    rv[c] = (ADJ && active && !dir) ? a.r[dof] : 0.0;
+    u[c] = (active && !dir) ? __ldg(a.x + dof) : 0.0;
+    rv[c] = (ADJ && active && !dir) ? __ldg(a.r + dof) : 0.0;
   }
+  // grad_xi x: t in registers, r and s by line owners
+  double xt[P], xr[P], xs[P];
+  eo_apply<P, P, -1>(a.tab.eD, u, xt);
 #pragma unroll
-  for (int c = 0; c < P; ++c) {
-    s0[(c * P + j) * P + i] = u[c];
-    if (ADJ) s2[(c * P + j) * P + i] = rv[c];
+  for (int k = 0; k < P; ++k) t0[tix<P>(k, j, i)] = u[k];
+  __syncthreads();
+  {
+    double v[P], g[P];
+#pragma unroll
+    for (int m = 0; m < P; ++m) v[m] = t0[tix<P>(j, i, m)];
+    eo_apply<P, P, -1>(a.tab.eD, v, g);
+#pragma unroll
+    for (int n = 0; n < P; ++n) t1[tix<P>(j, i, n)] = g[n];
+#pragma unroll
+    for (int m = 0; m < P; ++m) v[m] = t0[tix<P>(j, m, i)];
+    eo_apply<P, P, -1>(a.tab.eD, v, g);
+#pragma unroll
+    for (int n = 0; n < P; ++n) t2[tix<P>(j, n, i)] = g[n];
   }
   __syncthreads();
-  const double *D = a.tab.D;
-  double xr[P], xs[P], xt[P];
-  double gr_[P], gs_[P], gt_[P];
+  double rt[P];
+  if constexpr (ADJ) {  // grad_xi r, the same way
+    eo_apply<P, P, -1>(a.tab.eD, rv, rt);
+#pragma unroll
+    for (int k = 0; k < P; ++k) t0[tix<P>(k, j, i)] = rv[k];
+    __syncthreads();
+    double v[P], g[P];
+#pragma unroll
+    for (int m = 0; m < P; ++m) v[m] = t0[tix<P>(j, i, m)];
+    eo_apply<P, P, -1>(a.tab.eD, v, g);
+#pragma unroll
+    for (int n = 0; n < P; ++n) t3[tix<P>(j, i, n)] = g[n];
+#pragma unroll
+    for (int m = 0; m < P; ++m) v[m] = t0[tix<P>(j, m, i)];
+    eo_apply<P, P, -1>(a.tab.eD, v, g);
+#pragma unroll
+    for (int n = 0; n < P; ++n) t4[tix<P>(j, n, i)] = g[n];
+    __syncthreads();
+  }
 #pragma unroll
   for (int k = 0; k < P; ++k) {
-    double p0 = 0, p1 = 0, p2 = 0, q0 = 0, q1 = 0, q2 = 0;
-#pragma unroll
-    for (int m = 0; m < P; ++m) {
-      p0 += D[i * P + m] * s0[(k * P + j) * P + m];
-      p1 += D[j * P + m] * s0[(k * P + m) * P + i];
-      p2 += D[k * P + m] * u[m];
-      if (ADJ) {
-        q0 += D[i * P + m] * s2[(k * P + j) * P + m];
-        q1 += D[j * P + m] * s2[(k * P + m) * P + i];
-        q2 += D[k * P + m] * rv[m];
-      }
-    }
-    xr[k] = p0; xs[k] = p1; xt[k] = p2;
-    gr_[k] = q0; gs_[k] = q1; gt_[k] = q2;
+    xr[k] = t1[tix<P>(k, j, i)];
+    xs[k] = t2[tix<P>(k, j, i)];
   }
-  // pointwise: the operand of the transposed passes is k Ghat grad(w), w = x (forward) or r (adjoint)
-  const int nq = ND;
+
+  // pointwise: dL/dk (adjoint) and v = k Ghat grad(w), w = x (forward) or r (adjoint)
   const int64_t eo = active ? a.perm[e] : 0;
+  double c1[3], c1t[3], c2[3], c2t[3], c3[3];
+  if (!a.geo) {
+    const double xr0 = a.rule.x[i], xs0 = a.rule.x[j];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const double a1 = coef[c], a2 = coef[3 + c], a3 = coef[6 + c], a4 = coef[9 + c];
+      const double a5 = coef[12 + c], a6 = coef[15 + c], a7 = coef[18 + c];
+      c1[c] = a1 + a4 * xs0;
+      c1t[c] = a5 + a7 * xs0;
+      c2[c] = a2 + a4 * xr0;
+      c2t[c] = a6 + a7 * xr0;
+      c3[c] = a3 + a5 * xr0 + a6 * xs0 + a7 * xr0 * xs0;
+    }
+  }
+  double vt[P];
 #pragma unroll
   for (int k = 0; k < P; ++k) {
     const int q = (k * P + j) * P + i;
-    double g[6] = {0, 0, 0, 0, 0, 0};
-    double kq = 0.0;
+    double g0 = 0, g1 = 0, g2 = 0, g3 = 0, g4 = 0, g5 = 0, kq = 0;
     if (active) {
       if (a.geo) {
-        const double *gp = a.geo + e * 6 * nq + q;
-#pragma unroll
-        for (int c = 0; c < 6; ++c) g[c] = gp[c * nq];
+        const double *gp = a.geo + e * a.gstride + q;
+        g0 = __ldg(gp);
+        g1 = __ldg(gp + ND);
+        g2 = __ldg(gp + 2 * ND);
+        g3 = __ldg(gp + 3 * ND);
+        g4 = __ldg(gp + 4 * ND);
+        g5 = __ldg(gp + 5 * ND);
       } else {
-        double X[3], J[3][3], A[3][3];
-        trilinear_map(sv[el], a.rule.x[i], a.rule.x[j], a.rule.x[k], X, J);
+        const double zt = a.rule.x[k];
+        double J[3][3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          J[c][0] = c1[c] + c1t[c] * zt;
+          J[c][1] = c2[c] + c2t[c] * zt;
+          J[c][2] = c3[c];
+        }
+        double A[3][3];
         const double det = adjugate(J, A);
         const double f = a.rule.w[i] * a.rule.w[j] * a.rule.w[k] / det;
-        g[0] = f * (A[0][0] * A[0][0] + A[0][1] * A[0][1] + A[0][2] * A[0][2]);
-        g[1] = f * (A[0][0] * A[1][0] + A[0][1] * A[1][1] + A[0][2] * A[1][2]);
-        g[2] = f * (A[0][0] * A[2][0] + A[0][1] * A[2][1] + A[0][2] * A[2][2]);
-        g[3] = f * (A[1][0] * A[1][0] + A[1][1] * A[1][1] + A[1][2] * A[1][2]);
-        g[4] = f * (A[1][0] * A[2][0] + A[1][1] * A[2][1] + A[1][2] * A[2][2]);
-        g[5] = f * (A[2][0] * A[2][0] + A[2][1] * A[2][1] + A[2][2] * A[2][2]);
+        g0 = f * (A[0][0] * A[0][0] + A[0][1] * A[0][1] + A[0][2] * A[0][2]);
+        g1 = f * (A[0][0] * A[1][0] + A[0][1] * A[1][1] + A[0][2] * A[1][2]);
+        g2 = f * (A[0][0] * A[2][0] + A[0][1] * A[2][1] + A[0][2] * A[2][2]);
+        g3 = f * (A[1][0] * A[1][0] + A[1][1] * A[1][1] + A[1][2] * A[1][2]);
+        g4 = f * (A[1][0] * A[2][0] + A[1][1] * A[2][1] + A[1][2] * A[2][2]);
+        g5 = f * (A[2][0] * A[2][0] + A[2][1] * A[2][1] + A[2][2] * A[2][2]);
       }
-      kq = a.k[eo * nq + q];
+      kq = __ldg(a.k + eo * ND + q);
     }
-    const double wr = ADJ ? gr_[k] : xr[k], ws = ADJ ? gs_[k] : xs[k], wt = ADJ ? gt_[k] : xt[k];
-    const double hr = g[0] * wr + g[1] * ws + g[2] * wt;
-    const double hs = g[1] * wr + g[3] * ws + g[4] * wt;
-    const double ht = g[2] * wr + g[4] * ws + g[5] * wt;
-    if (ADJ && active) a.dLdk[eo * nq + q] = hr * xr[k] + hs * xs[k] + ht * xt[k];
-    xr[k] = kq * hr;
-    xs[k] = kq * hs;
-    xt[k] = kq * ht;
+    double wr, ws, wt;
+    if constexpr (ADJ) {
+      wr = t3[tix<P>(k, j, i)];
+      ws = t4[tix<P>(k, j, i)];
+      wt = rt[k];
+    } else {
+      wr = xr[k];
+      ws = xs[k];
+      wt = xt[k];
+    }
+    const double hr = g0 * wr + g1 * ws + g2 * wt;
+    const double hs = g1 * wr + g3 * ws + g4 * wt;
+    const double ht = g2 * wr + g4 * ws + g5 * wt;
+    if (ADJ && active) a.dLdk[eo * ND + q] = hr * xr[k] + hs * xs[k] + ht * xt[k];
+    t1[tix<P>(k, j, i)] = kq * hr;
+    t2[tix<P>(k, j, i)] = kq * hs;
+    vt[k] = kq * ht;
   }
   __syncthreads();
+  {  // transposed passes
+    double v[P], g[P];
 #pragma unroll
-  for (int k = 0; k < P; ++k) {
-    s0[(k * P + j) * P + i] = xr[k];
-    s1[(k * P + j) * P + i] = xs[k];
+    for (int m = 0; m < P; ++m) v[m] = t1[tix<P>(j, i, m)];
+    eo_apply<P, P, -1>(a.tab.eDT, v, g);
+#pragma unroll
+    for (int n = 0; n < P; ++n) t0[tix<P>(j, i, n)] = g[n];
+#pragma unroll
+    for (int m = 0; m < P; ++m) v[m] = t2[tix<P>(j, m, i)];
+    eo_apply<P, P, -1>(a.tab.eDT, v, g);
+#pragma unroll
+    for (int n = 0; n < P; ++n) t2[tix<P>(j, n, i)] = g[n];
   }
+  double yt[P];
+  eo_apply<P, P, -1>(a.tab.eDT, vt, yt);
   __syncthreads();
   if (!active) return;
 #pragma unroll
   for (int c = 0; c < P; ++c) {
-    double acc = 0.0;
-#pragma unroll
-    for (int m = 0; m < P; ++m) {
-      acc += D[m * P + i] * s0[(c * P + j) * P + m];
-      acc += D[m * P + j] * s1[(c * P + m) * P + i];
-      acc += D[m * P + c] * xt[m];
-    }
+    const double acc = yt[c] + t0[tix<P>(c, j, i)] + t2[tix<P>(c, j, i)];
     const uint32_t v = idx[c];
     const int64_t dof = v & DOF_MASK;
     if (a.masked && (v & FLAG_DIR)) {
@@ -142,19 +229,25 @@ __global__ void __launch_bounds__(P * P * (P * P >= 128 ? 1 : 128 / (P * P))) ko
     } else if (v & FLAG_FIRST) {
       a.y[dof] = acc;
     } else {
-      a.y[dof] += acc;
+      a.y[dof] = __ldcg(a.y + dof) + acc;
     }
   }
 }
 
 template <int P, bool ADJ>
 static int run_kop(ceed_mesh_t m, KArgs a, cudaStream_t s) {
-  constexpr int NE = (P * P >= 128) ? 1 : (128 / (P * P));
+  constexpr int NE = kop_ne<P>();
+  const size_t smem = NE * kop_elem_smem<P, ADJ>();
+  static size_t configured = 0;
+  if (smem > configured) {
+    CEED_CUDA_CHECK(cudaFuncSetAttribute(kop_kernel<P, ADJ>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    configured = smem;
+  }
   for (int c = 0; c < m->n_colors; ++c) {
     a.e_begin = m->color_start[c];
     a.e_count = m->color_start[c + 1] - a.e_begin;
     if (a.e_count == 0) continue;
-    kop_kernel<P, ADJ><<<(unsigned)((a.e_count + NE - 1) / NE), P * P * NE, 0, s>>>(a);
+    kop_kernel<P, ADJ><<<(unsigned)((a.e_count + NE - 1) / NE), P * P * NE, smem, s>>>(a);
   }
   CEED_CUDA_CHECK(cudaGetLastError());
   return CEED_OK;
@@ -189,6 +282,7 @@ static int kop_prepare(ceed_mesh_t m, const double *k, const void *geo, KArgs *a
   a->perm = m->d_perm;
   a->vert = m->d_vertices;
   a->geo = (const double *)geo;
+  a->gstride = qdata_estride(CEED_OP_DIFFUSION, 8, m->Q);
   a->k = k;
   a->rule = m->rule;
   a->tab = m->tab64;
