@@ -124,7 +124,7 @@ int ceed_apply_diffusion(ceed_mesh_t mesh, const void *qdata, int prec, const do
 
 /* Autotuner (the batched-apply design calls for tile shape and elements per block chosen by
  * measurement): runs every variant of the fused apply kernel -- elements per thread block
- * (1, 2, 4, ... up to 256 threads) x quadrature-data staging (TMA bulk copy into shared memory,
+ * (1, 2, 4, ... up to 256 threads and 32 elements) x quadrature-data staging (TMA bulk copy into shared memory,
  * or direct loads) -- on the caller's qdata, x and y (y is overwritten), times each with CUDA
  * events on `stream`, and keeps the fastest in the handle for (op, prec); later applies use it.
  * Returns the choice and its time per application.  Synchronizes `stream`. */
@@ -133,7 +133,7 @@ int ceed_autotune_apply(ceed_mesh_t mesh, int op, const void *qdata, int prec, c
 
 /* Fix the apply variant for (op, prec) by hand: ne elements per thread block (0 restores the
  * default), stage = 1 for TMA staging of quadrature data, 0 for direct loads.  INVALID if ne
- * exceeds 256 / Q^2.  Results do not depend on the variant (same arithmetic order). */
+ * exceeds min(32, 256 / Q^2).  Results do not depend on the variant (same arithmetic order). */
 int ceed_set_apply_variant(ceed_mesh_t mesh, int op, int prec, int ne, int stage);
 
 /* Jacobi diagonal of the operator (the cheap preconditioner for CG, Section 1), FP64

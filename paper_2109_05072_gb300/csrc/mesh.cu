@@ -490,7 +490,7 @@ extern "C" int ceed_autotune_apply(ceed_mesh_t m, int op, const void *qdata, int
   if (prec < CEED_F64 || prec > CEED_F64_DF) return fail(CEED_ERR_INVALID, "unknown precision");
   if (!qdata || !x || !y || x == y || nrhs < 1) return fail(CEED_ERR_INVALID, "bad autotune arguments");
   cudaStream_t s = (cudaStream_t)stream;
-  const int ne_max = std::max(1, 256 / (m->Q * m->Q));
+  const int ne_max = std::min(32, std::max(1, 256 / (m->Q * m->Q)));
   ApplyReq r;
   r.op = op;
   r.prec = prec;
@@ -539,8 +539,8 @@ extern "C" int ceed_set_apply_variant(ceed_mesh_t m, int op, int prec, int ne, i
   if (int st = check_mesh(m)) return st;
   if (op != CEED_OP_MASS && op != CEED_OP_DIFFUSION) return fail(CEED_ERR_INVALID, "unknown operator");
   if (prec < CEED_F64 || prec > CEED_F64_DF) return fail(CEED_ERR_INVALID, "unknown precision");
-  if (ne < 0 || ne > std::max(1, 256 / (m->Q * m->Q)) || (stage != 0 && stage != 1))
-    return fail(CEED_ERR_INVALID, "elements per block must be 0 (default) .. 256 / Q^2, stage 0 or 1");
+  if (ne < 0 || ne > std::min(32, std::max(1, 256 / (m->Q * m->Q))) || (stage != 0 && stage != 1))
+    return fail(CEED_ERR_INVALID, "elements per block must be 0 (default) .. min(32, 256 / Q^2), stage 0 or 1");
   m->tuned[op][prec].ne = ne;
   m->tuned[op][prec].stage = stage;
   m->tuned[op][prec].ms = 0.f;
