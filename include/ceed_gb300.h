@@ -50,7 +50,7 @@ typedef enum {
  * F32_GEO (diffusion only) -> FP32 contractions with the geometric factors recomputed from the
  * trilinear element map at every application: the quadrature data holds only the map's 8
  * coefficient vectors per element and w k per point (FP32), about 1/6 of the F32 bytes.
- * F64_DF (GLL-collocated diffusion only) -> an FP64-accurate operator computed on the FP32 pipe:
+ * F64_DF (mass and diffusion, either rule) -> an FP64-accurate operator computed on the FP32 pipe:
  * values and quadrature data carried as double-float pairs (hi + lo, about 48 bits) and every
  * contraction summed with a compensated dot product; agrees with the FP64 operator to ~1e-14
  * relative on well-conditioned inputs (FP64 L-vectors in and out, qdata 8 bytes per value). */

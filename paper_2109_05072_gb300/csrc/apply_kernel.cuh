@@ -200,6 +200,17 @@ __device__ __forceinline__ DF dot3<DF>(DF g1, DF a, DF g2, DF b, DF g3, DF c) {
   acc_mac(A, g3, c);
   return acc_get(A);
 }
+// pointwise q u (mass operator): one FMA-able product, or the double-float product rounded once
+template <typename T>
+__device__ __forceinline__ T qmul(T q, T u) {
+  return q * u;
+}
+template <>
+__device__ __forceinline__ DF qmul<DF>(DF q, DF u) {
+  DFAcc A{0.f, 0.f};
+  acc_mac(A, q, u);
+  return acc_get(A);
+}
 template <typename T>
 __device__ __forceinline__ T add3(T a, T b, T c) {
   return a + b + c;
@@ -404,7 +415,7 @@ __device__ __forceinline__ void apply_block(const ApplyArgs &a, const OpTab<T> &
     }
     if constexpr (OP == CEED_OP_MASS) {
 #pragma unroll
-      for (int k = 0; k < Q; ++k) w[k] = active ? q_to(sq[(k * Q + j) * Q + i], T()) * uq[k] : (T)0;
+      for (int k = 0; k < Q; ++k) w[k] = active ? qmul(q_to(sq[(k * Q + j) * Q + i], T()), uq[k]) : (T)0;
     } else {
       T ut[Q];
       eo_apply<Q, Q, -1>(tab.eD, uq, ut);
@@ -664,19 +675,15 @@ int launch_colours(ceed_mesh_t m, const OpTab<T> &tab, const ApplyReq &r, cudaSt
   return launch_variant<P, Q, OP, T, TQ, false>(m, tab, r, ne, s);
 }
 
-// Dispatch on (P, collocated?, op) for one (T, TQ) pair.
-template <typename T, typename TQ>
-int dispatch_apply(ceed_mesh_t m, const OpTab<T> &tab, const ApplyReq &r, cudaStream_t s) {
+// Dispatch on (P, collocated?) for one (op, T, TQ).
+template <int OP, typename T, typename TQ>
+int dispatch_apply_op(ceed_mesh_t m, const OpTab<T> &tab, const ApplyReq &r, cudaStream_t s) {
   if (((uintptr_t)r.qdata & 15) != 0) return fail(CEED_ERR_INVALID, "qdata must be 16-byte aligned");
   const bool colloc = (m->Q == m->P);
-#define CEEDGB_CASE(PP)                                                                                   \
-  case PP:                                                                                               \
-    if (colloc)                                                                                          \
-      return r.op == CEED_OP_MASS ? launch_colours<PP, PP, CEED_OP_MASS, T, TQ>(m, tab, r, s)             \
-                                  : launch_colours<PP, PP, CEED_OP_DIFFUSION, T, TQ>(m, tab, r, s);      \
-    else                                                                                                 \
-      return r.op == CEED_OP_MASS ? launch_colours<PP, PP + 1, CEED_OP_MASS, T, TQ>(m, tab, r, s)         \
-                                  : launch_colours<PP, PP + 1, CEED_OP_DIFFUSION, T, TQ>(m, tab, r, s);
+#define CEEDGB_CASE(PP)                                                                      \
+  case PP:                                                                                  \
+    return colloc ? launch_colours<PP, PP, OP, T, TQ>(m, tab, r, s)                         \
+                  : launch_colours<PP, PP + 1, OP, T, TQ>(m, tab, r, s);
   switch (m->P) {
     CEEDGB_CASE(2)
     CEEDGB_CASE(3)
@@ -690,6 +697,13 @@ int dispatch_apply(ceed_mesh_t m, const OpTab<T> &tab, const ApplyReq &r, cudaSt
       return fail(CEED_ERR_UNSUPPORTED, "p outside 1..8");
   }
 #undef CEEDGB_CASE
+}
+
+// Dispatch on (P, collocated?, op) for one (T, TQ) pair.
+template <typename T, typename TQ>
+int dispatch_apply(ceed_mesh_t m, const OpTab<T> &tab, const ApplyReq &r, cudaStream_t s) {
+  return r.op == CEED_OP_MASS ? dispatch_apply_op<CEED_OP_MASS, T, TQ>(m, tab, r, s)
+                              : dispatch_apply_op<CEED_OP_DIFFUSION, T, TQ>(m, tab, r, s);
 }
 
 }  // namespace ceedgb

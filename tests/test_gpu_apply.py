@@ -221,31 +221,28 @@ def test_apply_variants_identical_and_autotune(ceed, p, qkind, op, prec):
     mesh.close()
 
 
-@pytest.mark.parametrize("p", list(range(1, 9)))
-def test_apply_double_float_matches_oracle(ceed, p):
+@pytest.mark.parametrize("p,qkind,op", CASES)
+def test_apply_double_float_matches_oracle(ceed, p, qkind, op):
     # FP64-accurate operator on the FP32 pipe (double-float values, compensated contractions):
-    # the same 1e-12 bar as the FP64 operator
+    # the same 1e-12 bar as the FP64 operator, for both operators and both quadrature rules
     dims = (5, 3, 2) if p <= 4 else (3, 2, 2)
     m = synthetic.HexMesh(*dims, p, seed=50 + p)
-    mesh = gpu_mesh(ceed, m, "gll")
-    qd = _qdata(ceed, mesh, "diffusion", ceed.CEED_F64_DF)
-    sp_, qref = oracle_qdata(m, "gll", "diffusion", "sine")
+    mesh = gpu_mesh(ceed, m, qkind)
+    kind = fem.DIFFUSION if op == "diffusion" else fem.MASS
+    qd = _qdata(ceed, mesh, op, ceed.CEED_F64_DF)
+    sp_, qref = oracle_qdata(m, qkind, op, "sine")
     x = synthetic.uniform(m.n_ldof, seed=60 + p)
-    y = _apply(ceed, mesh, "diffusion", qd, ceed.CEED_F64_DF, x)
-    ref = fem.apply(sp_, m.elem_dofs, qref, x, fem.DIFFUSION)
+    y = _apply(ceed, mesh, op, qd, ceed.CEED_F64_DF, x)
+    ref = fem.apply(sp_, m.elem_dofs, qref, x, kind)
     err = rel_err(y, ref)
-    print(f"double-float p={p}: rel err {err:.2e}")
+    print(f"double-float p={p} {qkind} {op}: rel err {err:.2e}")
     assert err <= 1e-12
     assert np.abs(y - ref).max() <= 1e-12 * np.abs(ref).max()
     # masked operator and several columns
-    ym = _apply(ceed, mesh, "diffusion", qd, ceed.CEED_F64_DF, x, flags=ceed.CEED_APPLY_DIRICHLET)
-    Am = fem.masked(lambda v: fem.apply(sp_, m.elem_dofs, qref, v, fem.DIFFUSION), m.boundary)
+    ym = _apply(ceed, mesh, op, qd, ceed.CEED_F64_DF, x, flags=ceed.CEED_APPLY_DIRICHLET)
+    Am = fem.masked(lambda v: fem.apply(sp_, m.elem_dofs, qref, v, kind), m.boundary)
     assert rel_err(ym, Am(x)) <= 1e-12
     X = synthetic.uniform(m.n_ldof * 3, seed=70 + p).reshape(m.n_ldof, 3)
-    Y = _apply(ceed, mesh, "diffusion", qd, ceed.CEED_F64_DF, X.reshape(-1), nrhs=3).reshape(m.n_ldof, 3)
-    assert rel_err(Y, fem.apply(sp_, m.elem_dofs, qref, X, fem.DIFFUSION)) <= 1e-12
-    # not offered for Gauss quadrature or the mass operator
-    if p == 3:
-        with pytest.raises(ceed.CeedError):
-            _apply(ceed, mesh, "mass", qd, ceed.CEED_F64_DF, x)
+    Y = _apply(ceed, mesh, op, qd, ceed.CEED_F64_DF, X.reshape(-1), nrhs=3).reshape(m.n_ldof, 3)
+    assert rel_err(Y, fem.apply(sp_, m.elem_dofs, qref, X, kind)) <= 1e-12
     mesh.close()
