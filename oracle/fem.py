@@ -5,6 +5,8 @@ the reading of it) that it follows.  Index conventions shared with the C-ABI:
   element nodes  n = a + P (b + P c)       (a along r, fastest)
   quad points    q = i + Q (j + Q k)       (i along r, fastest)
   per-element arrays [E, nq] are in the caller's element order.
+Geometry arguments (named `vertices`) are either the trilinear vertices [E, 8, 3]
+or an Isoparametric (curved, degree-p) element geometry.
 """
 from __future__ import annotations
 
@@ -80,6 +82,52 @@ def trilinear_map(vertices, XI):
     return X, J
 
 
+class Isoparametric:
+    """Curved element geometry of degree p (isoparametric): x(xi) = sum_n phi_n(xi) x_n.
+
+    The element map is interpolated with the element's own Q_p basis from the physical
+    positions of its nodes, coords [E, (p+1)^3, 3] in element-node order; Section 2 asks only
+    for deformed (non-affine) elements, and this is the usual curved generalisation of the
+    trilinear map (same basis for geometry and solution).
+    """
+
+    def __init__(self, coords):
+        self.coords = np.asarray(coords, dtype=np.float64)
+
+
+def node_points(p: int, vertices):
+    """Physical positions [E, (p+1)^3, 3] of the Q_p element nodes under the trilinear map."""
+    nodes, w = gll(p + 1)
+    _, _, _, XI = tabulate(nodes, nodes, w)
+    X, _ = trilinear_map(vertices, XI)
+    return X
+
+
+def global_node_points(p: int, vertices, elem_dofs, n: int):
+    """Positions [n, 3] of the global nodes under the (conforming) trilinear element maps."""
+    X = node_points(p, vertices)
+    out = np.zeros((n, 3))
+    out[np.asarray(elem_dofs).reshape(-1)] = X.reshape(-1, 3)
+    return out
+
+
+def isoparametric_map(space: Space, coords):
+    """X [E, nq, 3] and J [E, nq, 3, 3] (J[..., a, b] = dx_a / dxi_b) of the isoparametric map."""
+    coords = np.asarray(coords, dtype=np.float64)
+    if coords.shape[1] != space.nd:
+        raise ValueError("coords must hold the (p+1)^3 nodes of each element")
+    X = np.einsum("qn,enc->eqc", space.Phi, coords)
+    J = np.einsum("bqn,ena->eqab", space.dPhi, coords)
+    return X, J
+
+
+def element_map(space: Space, geom):
+    """(X, J) at the quadrature points: trilinear from vertices [E, 8, 3], or isoparametric."""
+    if isinstance(geom, Isoparametric):
+        return isoparametric_map(space, geom.coords)
+    return trilinear_map(geom, space.XI)
+
+
 def coeff_sine(X):
     """k(x) = 1 + 0.5 sin(2 pi x) sin(2 pi y) sin(2 pi z) at points X [..., 3]."""
     s = np.sin(2.0 * np.pi * X)
@@ -88,7 +136,7 @@ def coeff_sine(X):
 
 def qdata_mass(space: Space, vertices, rho=None):
     """Mass quadrature data w_q |det J_q| rho_q, [E, nq]."""
-    _, J = trilinear_map(vertices, space.XI)
+    _, J = element_map(space, vertices)
     qd = space.W[None, :] * np.abs(np.linalg.det(J))
     if rho is not None:
         qd = qd * rho
@@ -97,7 +145,7 @@ def qdata_mass(space: Space, vertices, rho=None):
 
 def geometric_factor(space: Space, vertices):
     """w_q |det J| J^{-1} J^{-T} per point, [E, nq, 3, 3] (the symmetric G^e of Section 2 without k)."""
-    _, J = trilinear_map(vertices, space.XI)
+    _, J = element_map(space, vertices)
     Jinv = np.linalg.inv(J)
     return (space.W[None, :] * np.abs(np.linalg.det(J)))[..., None, None] * (Jinv @ np.swapaxes(Jinv, -1, -2))
 
@@ -115,7 +163,7 @@ def qdata_diffusion(space: Space, vertices, k=None):
     if isinstance(k, str):
         if k != "sine":
             raise ValueError(k)
-        X, _ = trilinear_map(vertices, space.XI)
+        X, _ = element_map(space, vertices)
         k = coeff_sine(X)
     return np.asarray(k)[..., None, None] * G
 
@@ -248,7 +296,7 @@ def manufactured_source(X, coeff: str = "sine"):
 
 def manufactured_rhs(space: Space, vertices, elem_dofs, n: int, coeff: str = "sine", mask=None):
     """b_i = sum_e sum_q w_q |det J| f(x_q) phi_i(x_q), same quadrature as the operator; 0 on Dirichlet nodes."""
-    X, J = trilinear_map(vertices, space.XI)
+    X, J = element_map(space, vertices)
     fq = space.W[None, :] * np.abs(np.linalg.det(J)) * manufactured_source(X, coeff)
     be = np.einsum("qn,eq->en", space.Phi, fq)
     b = np.zeros(n)
@@ -261,7 +309,7 @@ def manufactured_rhs(space: Space, vertices, elem_dofs, n: int, coeff: str = "si
 def l2_error(p: int, vertices, elem_dofs, u, qextra: int = 3):
     """||u_h - u*||_{L2} with Gauss quadrature of p+qextra points per direction."""
     sp_ = Space(p, "gauss", p + qextra)
-    X, J = trilinear_map(vertices, sp_.XI)
+    X, J = element_map(sp_, vertices)
     uh = np.einsum("qn,en->eq", sp_.Phi, u[elem_dofs])
     err = (uh - exact_solution(X)) ** 2
     return float(np.sqrt(np.sum(sp_.W[None, :] * np.abs(np.linalg.det(J)) * err)))

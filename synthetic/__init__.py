@@ -171,5 +171,17 @@ class HexMesh:
         return (self.Mx - 2) * (self.My - 2) * (self.Mz - 2)
 
 
+def bubble_warp(X: np.ndarray, amplitude: float = 0.05) -> np.ndarray:
+    """A smooth deformation of the unit cube that keeps its boundary fixed (curved-mesh inputs).
+
+    x -> x + amplitude * b(x) * (1, -0.75, 0.5) with the bubble b = 64 x(1-x) y(1-y) z(1-z)
+    (zero on every face, 1 at the centre).  |grad b| <= 4 per component, so the map stays
+    invertible for amplitude < 1/9.  X [..., 3] physical points; returns the moved points.
+    """
+    X = np.asarray(X, dtype=np.float64)
+    b = 64.0 * np.prod(X * (1.0 - X), axis=-1)
+    return X + amplitude * b[..., None] * np.array([1.0, -0.75, 0.5])
+
+
 def cube_mesh(N: int, p: int, seed: int = 0, perturb: float = 0.1, build_map: bool = True) -> HexMesh:
     return HexMesh(N, N, N, p, seed=seed, perturb=perturb, build_map=build_map)
