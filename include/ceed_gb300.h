@@ -82,6 +82,11 @@ typedef struct {
   const int32_t *elem_dofs;  /* device [E][(p+1)^3], 0 <= dof < n_ldof, every dof referenced */
   const double *vertices;    /* device [E][8][3], trilinear element map, vertex v = vx + 2 vy + 4 vz */
   const uint8_t *dirichlet;  /* device [n_ldof] (nonzero = Dirichlet node) or NULL */
+  const double *coords;      /* device [n_ldof][3] physical node positions of a curved (isoparametric,
+                              * degree-p) geometry, or NULL for the trilinear map of `vertices`.  With
+                              * coords, quadrature data and right-hand sides use x(xi) = sum_n phi_n(xi)
+                              * x_n; F32_GEO data and the adjoint's recomputed geometry (both built on
+                              * the trilinear map) are refused with UNSUPPORTED. */
 } ceed_mesh_desc;
 
 /* Build a mesh handle (paper Section 2: the element restriction and 1D bases of the
@@ -92,6 +97,12 @@ typedef struct {
  * afterwards.  Synchronizes `stream`.  Errors: INVALID (sizes, p, out-of-range or
  * unreferenced dof), UNSUPPORTED (more than 64 colours), OOM, CUDA. */
 int ceed_setup_mesh(const ceed_mesh_desc *desc, ceed_mesh_t *out, void *stream);
+
+/* Physical positions of every node, device [n_ldof][3]: the handle's curved-geometry copy if it
+ * has one, else the trilinear map of each element at its GLL nodes (the isoparametric form of the
+ * trilinear geometry; a caller can move these points and set up a curved mesh from them).
+ * Asynchronous on `stream`.  Errors: INVALID. */
+int ceed_mesh_node_coords(ceed_mesh_t mesh, double *coords, void *stream);
 
 /* Release a handle and its device tables (NULL is a no-op).  Synchronizes the device. */
 int ceed_destroy_mesh(ceed_mesh_t mesh);

@@ -39,7 +39,8 @@ class CeedError(RuntimeError):
 class _MeshDesc(ctypes.Structure):
     _fields_ = [("n_elem", ctypes.c_int64), ("n_ldof", ctypes.c_int64), ("p", ctypes.c_int32),
                 ("q_rule", ctypes.c_int32), ("n_qpts_1d", ctypes.c_int32), ("ncomp", ctypes.c_int32),
-                ("elem_dofs", ctypes.c_void_p), ("vertices", ctypes.c_void_p), ("dirichlet", ctypes.c_void_p)]
+                ("elem_dofs", ctypes.c_void_p), ("vertices", ctypes.c_void_p), ("dirichlet", ctypes.c_void_p),
+                ("coords", ctypes.c_void_p)]
 
 
 class _CgOpts(ctypes.Structure):
@@ -67,6 +68,7 @@ def _load():
     sig = {
         "ceed_setup_mesh": (ctypes.c_int, [ctypes.POINTER(_MeshDesc), ctypes.POINTER(vp), vp]),
         "ceed_destroy_mesh": (ctypes.c_int, [vp]),
+        "ceed_mesh_node_coords": (ctypes.c_int, [vp, vp, vp]),
         "ceed_mesh_info": (ctypes.c_int, [vp, ctypes.POINTER(i32), ctypes.POINTER(i32), ctypes.POINTER(i32)]),
         "ceed_qdata_bytes": (sz, [vp, ctypes.c_int, ctypes.c_int]),
         "ceed_build_qdata": (ctypes.c_int, [vp, ctypes.c_int, ctypes.c_int, vp, ctypes.c_int, vp, vp]),
@@ -163,10 +165,12 @@ class Mesh:
 
 
 def ceed_setup_mesh(n_elem, n_ldof, p, elem_dofs, vertices, dirichlet=None, q_rule=CEED_QRULE_GLL, n_qpts_1d=0,
-                    ncomp=1, stream=None) -> Mesh:
+                    ncomp=1, stream=None, coords=None) -> Mesh:
     assert elem_dofs.dtype == torch.int32 and vertices.dtype == torch.float64
     assert dirichlet is None or dirichlet.dtype == torch.uint8
-    d = _MeshDesc(n_elem, n_ldof, p, q_rule, n_qpts_1d, ncomp, _ptr(elem_dofs), _ptr(vertices), _ptr(dirichlet))
+    assert coords is None or (coords.dtype == torch.float64 and coords.is_contiguous())
+    d = _MeshDesc(n_elem, n_ldof, p, q_rule, n_qpts_1d, ncomp, _ptr(elem_dofs), _ptr(vertices), _ptr(dirichlet),
+                  _ptr(coords))
     h = ctypes.c_void_p()
     _check(_lib.ceed_setup_mesh(ctypes.byref(d), ctypes.byref(h), _stream(stream)))
     return Mesh(h, n_elem, n_ldof, p, q_rule, ncomp)
@@ -177,6 +181,12 @@ def ceed_mesh_info(mesh: Mesh):
     nc, Q, P = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
     _check(_lib.ceed_mesh_info(mesh.handle, ctypes.byref(nc), ctypes.byref(Q), ctypes.byref(P)))
     return nc.value, Q.value, P.value
+
+
+def ceed_mesh_node_coords(mesh: Mesh, coords: torch.Tensor, stream=None):
+    """Physical node positions [n_ldof, 3] (curved copy, or the trilinear map at the GLL nodes)."""
+    assert coords.dtype == torch.float64 and coords.is_contiguous() and coords.numel() == 3 * mesh.n_ldof
+    _check(_lib.ceed_mesh_node_coords(mesh.handle, _ptr(coords), _stream(stream)))
 
 
 def ceed_destroy_mesh(mesh: Mesh):

@@ -277,6 +277,8 @@ static int kop_prepare(ceed_mesh_t m, const double *k, const void *geo, KArgs *a
   if (m->Q != m->P) return fail(CEED_ERR_UNSUPPORTED, "per-point coefficient operators need collocated GLL quadrature");
   if (m->ncomp != 1) return fail(CEED_ERR_UNSUPPORTED, "per-point coefficient operators need ncomp = 1");
   if (!k) return fail(CEED_ERR_INVALID, "null k");
+  if (!geo && m->d_coords)
+    return fail(CEED_ERR_UNSUPPORTED, "recomputed geometry is the trilinear map; pass stored geometry for a curved mesh");
   *a = KArgs{};
   a->emap = m->d_emap;
   a->perm = m->d_perm;

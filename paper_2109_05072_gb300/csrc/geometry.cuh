@@ -67,4 +67,79 @@ __device__ __forceinline__ double manufactured_source(const double X[3], int coe
   return 3.0 * pi * pi * k * u - gk_dot_gu;
 }
 
+// ------------------------------------------------------------------ curved (isoparametric) geometry
+// x(xi) = sum_n phi_n(xi) x_n with the element's own Q_p basis: X and J at the quadrature points by
+// sum factorization of the gathered node positions, one coordinate at a time (passes along r, s,
+// t with the 1D interpolation B[q][a] and the derivative of the nodal basis G[q][a] at the points).
+struct IsoTab {
+  double B[MAX_Q * MAX_P];  // l_a(x_q)
+  double G[MAX_Q * MAX_P];  // l_a'(x_q)
+};
+
+constexpr int ISO_THREADS = 256;
+constexpr int ISO_PPT = (MAX_Q * MAX_Q * MAX_Q + ISO_THREADS - 1) / ISO_THREADS;  // points per thread
+
+// shared memory (doubles): node values P^3, r pass 2 P^2 Q, s pass 3 P Q^2
+__host__ __device__ inline int iso_smem_doubles(int P, int Q) { return P * P * P + 2 * P * P * Q + 3 * P * Q * Q; }
+
+// X[t][c] and J[t][c][b] = dx_c / dxi_b at points q = threadIdx.x + t * blockDim.x (q < Q^3) of one
+// element whose node indices (restriction with flags) are emap_e; blockDim.x * ISO_PPT >= Q^3.
+__device__ inline void iso_geometry(const double *__restrict__ coords, const uint32_t *__restrict__ emap_e, int P,
+                                    int Q, const IsoTab &T, double *sm, double X[ISO_PPT][3],
+                                    double J[ISO_PPT][3][3]) {
+  const int nd = P * P * P, nq = Q * Q * Q;
+  double *s0 = sm, *s1b = s0 + nd, *s1d = s1b + P * P * Q;
+  double *s2bb = s1d + P * P * Q, *s2bd = s2bb + P * Q * Q, *s2db = s2bd + P * Q * Q;
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {  // unrolled: X and J stay in registers
+    for (int n = threadIdx.x; n < nd; n += blockDim.x) s0[n] = coords[(int64_t)(emap_e[n] & DOF_MASK) * 3 + c];
+    __syncthreads();
+    for (int o = threadIdx.x; o < P * P * Q; o += blockDim.x) {  // r: (cc, b, i)
+      const int i = o % Q, b = (o / Q) % P, cc = o / (Q * P);
+      double vb = 0.0, vd = 0.0;
+      for (int a = 0; a < P; ++a) {
+        const double x = s0[(cc * P + b) * P + a];
+        vb += T.B[i * P + a] * x;
+        vd += T.G[i * P + a] * x;
+      }
+      s1b[o] = vb;
+      s1d[o] = vd;
+    }
+    __syncthreads();
+    for (int o = threadIdx.x; o < P * Q * Q; o += blockDim.x) {  // s: (cc, j, i)
+      const int i = o % Q, j = (o / Q) % Q, cc = o / (Q * Q);
+      double bb = 0.0, bd = 0.0, db = 0.0;
+      for (int b = 0; b < P; ++b) {
+        const double u = s1b[(cc * P + b) * Q + i], ud = s1d[(cc * P + b) * Q + i];
+        bb += T.B[j * P + b] * u;
+        bd += T.G[j * P + b] * u;
+        db += T.B[j * P + b] * ud;
+      }
+      s2bb[o] = bb;
+      s2bd[o] = bd;
+      s2db[o] = db;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int t = 0; t < ISO_PPT; ++t) {  // t: my points
+      const int q = threadIdx.x + t * blockDim.x;
+      if (q >= nq) continue;
+      const int i = q % Q, j = (q / Q) % Q, k = q / (Q * Q);
+      double x = 0.0, jr = 0.0, js = 0.0, jt = 0.0;
+      for (int cc = 0; cc < P; ++cc) {
+        const int o = (cc * Q + j) * Q + i;
+        x += T.B[k * P + cc] * s2bb[o];
+        jt += T.G[k * P + cc] * s2bb[o];
+        js += T.B[k * P + cc] * s2bd[o];
+        jr += T.B[k * P + cc] * s2db[o];
+      }
+      X[t][c] = x;
+      J[t][c][0] = jr;
+      J[t][c][1] = js;
+      J[t][c][2] = jt;
+    }
+    __syncthreads();  // s0 is refilled by the next coordinate
+  }
+}
+
 }  // namespace ceedgb

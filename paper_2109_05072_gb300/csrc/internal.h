@@ -91,6 +91,7 @@ struct ceed_mesh_s {
   uint32_t *d_emap = nullptr;           // [E][P^3] colour-sorted restriction with flags
   int32_t *d_perm = nullptr;            // sorted position -> caller's element index
   double *d_vertices = nullptr;         // [E][8][3] colour-sorted
+  double *d_coords = nullptr;           // [n_ldof][3] curved (isoparametric) node positions, or null
   int *d_err = nullptr;                 // device status word
   bool has_dirichlet = false;
   ceedgb::OpTab<double> tab64;

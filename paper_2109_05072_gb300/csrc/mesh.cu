@@ -250,6 +250,7 @@ struct HostFree {
     cudaFree(m->d_emap);
     cudaFree(m->d_perm);
     cudaFree(m->d_vertices);
+    cudaFree(m->d_coords);
     cudaFree(m->d_err);
     delete m;
   }
@@ -409,6 +410,10 @@ extern "C" int ceed_setup_mesh(const ceed_mesh_desc *desc, ceed_mesh_t *out, voi
   CEED_CUDA_CHECK(cudaMemcpyAsync(m->d_perm, perm.data(), E * 4, cudaMemcpyHostToDevice, s));
   CEED_CUDA_CHECK(cudaMemcpyAsync(m->d_vertices, svert.data(), E * 24 * 8, cudaMemcpyHostToDevice, s));
   CEED_CUDA_CHECK(cudaMemsetAsync(m->d_err, 0, sizeof(int) * 4, s));
+  if (desc->coords) {  // curved geometry: the handle keeps its own copy of the node positions
+    CEED_CUDA_CHECK(cudaMalloc(&m->d_coords, nL * 3 * sizeof(double)));
+    CEED_CUDA_CHECK(cudaMemcpyAsync(m->d_coords, desc->coords, nL * 3 * sizeof(double), cudaMemcpyDefault, s));
+  }
   CEED_CUDA_CHECK(cudaStreamSynchronize(s));
   *out = m.release();
   return CEED_OK;

@@ -13,12 +13,18 @@ def rel_err(a, b):
     return float(np.linalg.norm(a - b) / np.linalg.norm(b))
 
 
-def gpu_mesh(ceed, m, qkind="gll", ncomp=1, dirichlet=True, device="cuda"):
+def gpu_mesh(ceed, m, qkind="gll", ncomp=1, dirichlet=True, device="cuda", coords=None):
     import torch
     return ceed.ceed_setup_mesh(m.n_elem, m.n_ldof, m.p, torch.from_numpy(m.elem_dofs).to(device),
                                 torch.from_numpy(m.vertices).to(device),
                                 torch.from_numpy(m.boundary).to(device) if dirichlet else None,
-                                q_rule=RULES[qkind], ncomp=ncomp)
+                                q_rule=RULES[qkind], ncomp=ncomp,
+                                coords=None if coords is None else torch.from_numpy(coords).to(device))
+
+
+def curved_coords(m, amplitude=0.05):
+    """Node positions [n_ldof, 3] of a curved mesh: the trilinear nodes moved by the bubble warp (oracle side)."""
+    return synthetic.bubble_warp(fem.global_node_points(m.p, m.vertices, m.elem_dofs, m.n_ldof), amplitude)
 
 
 def oracle_qdata(m, qkind, op, coeff):
