@@ -185,3 +185,74 @@ def bubble_warp(X: np.ndarray, amplitude: float = 0.05) -> np.ndarray:
 
 def cube_mesh(N: int, p: int, seed: int = 0, perturb: float = 0.1, build_map: bool = True) -> HexMesh:
     return HexMesh(N, N, N, p, seed=seed, perturb=perturb, build_map=build_map)
+
+
+# Kuhn (Freudenthal) split of a cube into 6 tetrahedra: one per ordering of the axes, the path
+# 0 -> e_s0 -> e_s0 + e_s1 -> (1, 1, 1).  Listed with the sign of the permutation.
+KUHN_PATHS = (((0, 1, 2), 1), ((0, 2, 1), -1), ((1, 0, 2), -1), ((1, 2, 0), 1), ((2, 0, 1), 1), ((2, 1, 0), -1))
+
+
+def simplex_multi_indices(p: int) -> np.ndarray:
+    """Local node order of a degree-p tetrahedron: multi-indices (i, j, k), i + j + k <= p, with
+    k slowest and i fastest; node (i, j, k) sits at xi = (i, j, k) / p of the reference element."""
+    out = [(i, j, k) for k in range(p + 1) for j in range(p + 1 - k) for i in range(p + 1 - j - k)]
+    return np.array(out, dtype=np.int64)
+
+
+class TetMesh:
+    """Tetrahedral mesh of the unit cube: every cube of the perturbed nx*ny*nz lattice (the same
+    vertex positions as HexMesh) split into the 6 Kuhn tetrahedra, with degree-p nodes.
+
+    Attributes (host numpy arrays):
+      vertices  [E, 4, 3] float64: the element's vertices v0..v3; the element map is
+                x(xi) = v0 + sum_d xi_d (v_{d+1} - v0) on the reference tetrahedron
+                {xi >= 0, xi_1 + xi_2 + xi_3 <= 1}
+      elem_dofs [E, (p+1)(p+2)(p+3)/6] int32 in the order of simplex_multi_indices(p)
+      boundary  [n_ldof] uint8
+    Element e = 6 c + t for cube c = ex + nx (ey + ny ez) and path t of KUHN_PATHS; paths of odd
+    permutations list their last two vertices swapped, so every element has a positive volume on
+    the unperturbed lattice.  The equispaced degree-p nodes of every element are points of the
+    lattice refined p times, so the global node of local node (i, j, k) is that lattice point:
+    nodes shared by neighbouring elements get one number, and n_ldof = (p nx + 1)(p ny + 1)(p nz + 1).
+    """
+
+    def __init__(self, nx: int, ny: int, nz: int, p: int, seed: int = 0, perturb: float = 0.1):
+        if p < 1 or min(nx, ny, nz) < 1:
+            raise ValueError("need p >= 1 and at least one cube per direction")
+        hexes = HexMesh(nx, ny, nz, p, seed=seed, perturb=perturb, build_map=False)
+        self.nx, self.ny, self.nz, self.p = nx, ny, nz, p
+        self.n_elem = 6 * nx * ny * nz
+        self.Mx, self.My, self.Mz = hexes.Mx, hexes.My, hexes.Mz
+        self.n_ldof = hexes.n_ldof
+        self.boundary = hexes.boundary
+        corners = np.zeros((6, 4, 3), dtype=np.int64)       # lattice offsets of v0..v3 per path
+        for t, (perm, sign) in enumerate(KUHN_PATHS):
+            c = [np.zeros(3, np.int64)]
+            for a in perm:
+                c.append(c[-1].copy())
+                c[-1][a] += 1
+            if sign < 0:
+                c[2], c[3] = c[3], c[2]
+            corners[t] = np.array(c)
+        self.corners = corners
+        X = hexes.vertex_lattice                              # [nz+1, ny+1, nx+1, 3]
+        ez, ey, ex = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+        ex, ey, ez = ex.reshape(-1), ey.reshape(-1), ez.reshape(-1)
+        V = np.empty((nx * ny * nz, 6, 4, 3))
+        for t in range(6):
+            for v in range(4):
+                cx, cy, cz = corners[t, v]
+                V[:, t, v, :] = X[ez + cz, ey + cy, ex + cx]
+        self.vertices = V.reshape(self.n_elem, 4, 3)
+        mi = simplex_multi_indices(p)                         # [nd, 3]
+        # lattice offset of node (i, j, k): i c1 + j c2 + k c3 (c0 is the cube's origin corner)
+        off = np.einsum("nk,tkc->tnc", mi, corners[:, 1:, :])  # [6, nd, 3]
+        base = np.stack([p * ex, p * ey, p * ez], -1)          # [cubes, 3]
+        L = base[:, None, None, :] + off[None, :, :, :]        # [cubes, 6, nd, 3]
+        dofs = L[..., 0] + self.Mx * (L[..., 1] + self.My * L[..., 2])
+        self.elem_dofs = dofs.reshape(self.n_elem, -1).astype(np.int32)
+        self.nd = mi.shape[0]
+
+
+def tet_cube_mesh(N: int, p: int, seed: int = 0, perturb: float = 0.1) -> TetMesh:
+    return TetMesh(N, N, N, p, seed=seed, perturb=perturb)
