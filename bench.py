@@ -283,6 +283,47 @@ def run_adjoint(ceed, dev, args):
     return out
 
 
+def run_nontensor(ceed, dev, args):
+    """Non-tensor elements (the paper's GEMM formulation of the MAGMA backend, and the fused kernel):
+    degree-4 tetrahedra, 6 per cube of the perturbed 48^3 lattice (663,552 elements, 7,189,057 nodes),
+    conical rule with q = 5 points per direction (Q = 125), diffusion with the sine coefficient."""
+    import torch
+    p, q, N = 4, 5, 48
+    m = synthetic.TetMesh(N, N, N, p, seed=0)
+    interp, grad, qw, qref = ceed.ceed_simplex_basis(p, q)
+    nt = ceed.ceed_nt_setup(m.n_elem, m.n_ldof, interp, grad, qw, qref, torch.from_numpy(m.elem_dofs).to(dev),
+                            torch.from_numpy(m.vertices).to(dev), None)
+    P, Q, E = nt.P, nt.Q, m.n_elem
+    x = torch.from_numpy(synthetic.uniform(m.n_ldof, seed=1)).to(dev)
+    y = torch.empty_like(x)
+    flops = E * (2 * 2 * 3 * Q * P + 15 * Q)
+    out = {"workload": f"diffusion, degree-{p} tetrahedra (Kuhn split of the perturbed {N}^3 lattice), "
+                       f"conical rule q={q}", "n_elem": E, "n_ldof": m.n_ldof, "P": P, "Q": Q,
+           "flops_per_apply": flops, "runs": []}
+    hbm_peak, _ = load_peaks()
+    for prec, name, tb in ((ceed.CEED_F64, "f64", 8), (ceed.CEED_F32, "f32", 4)):
+        qd = ceed.alloc_nt_qdata(nt, ceed.CEED_OP_DIFFUSION, prec, dev)
+        ceed.ceed_nt_build_qdata(nt, ceed.CEED_OP_DIFFUSION, ceed.CEED_COEFF_SINE, None, prec, qd)
+        # algorithmic bytes: x and y once per node, the quadrature data, the int32 restriction
+        by = 16 * m.n_ldof + 6 * Q * E * tb + 4 * P * E
+        modes = [("fused", ceed.CEED_NT_FUSED, 0, 0), ("gemm_native", ceed.CEED_NT_GEMM, 0, 0),
+                 ("gemm_emulated", ceed.CEED_NT_GEMM, 0, 1)]
+        if prec == ceed.CEED_F32:
+            modes.append(("gemm_tf32", ceed.CEED_NT_GEMM, 0, 2))
+        for label, algo, eta, gm in modes:
+            ceed.ceed_nt_set_algorithm(nt, ceed.CEED_OP_DIFFUSION, prec, algo, eta, gm)
+            ms = _time_cuda(lambda: ceed.ceed_nt_apply(nt, ceed.CEED_OP_DIFFUSION, qd, prec, x, y), 5, 3)
+            out["runs"].append({"prec": name, "algo": label, "gemm_mode": gm, "ms": ms,
+                                "gdofs": m.n_ldof / ms / 1e6, "tflops": flops / ms / 1e9,
+                                "alg_gbs": by / ms / 1e6, "hbm_frac": by / ms / 1e6 / hbm_peak})
+        algo, eta, gm, tms = ceed.ceed_nt_autotune(nt, ceed.CEED_OP_DIFFUSION, qd, prec, x, y)
+        out[f"autotuned_{name}"] = {"algo": ["fused", "gemm"][algo], "eta": eta, "gemm_mode": gm, "ms": tms}
+        del qd
+        torch.cuda.empty_cache()
+    nt.close()
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -301,6 +342,7 @@ def main():
     ap.add_argument("--batched", type=int, default=1, help="measure the batched mixed-order apply")
     ap.add_argument("--adjoint", type=int, default=1, help="measure the adjoint kernels")
     ap.add_argument("--df", type=int, default=1, help="measure the double-float FP64-accurate operator")
+    ap.add_argument("--nontensor", type=int, default=1, help="measure the non-tensor (tetrahedral) operator")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -506,6 +548,11 @@ def main():
     if args.adjoint:
         adjoint = run_adjoint(ceed, dev, args)
 
+    # ---------------- non-tensor elements: degree-4 tetrahedra, fused kernel vs the GEMM formulation
+    nontensor = None
+    if args.nontensor:
+        nontensor = run_nontensor(ceed, dev, args)
+
     # ---------------- CPU oracle on a bounded sample (rank 0, N = 1 only)
     cpu = None
     if rank == 0 and ws == 1 and args.cpu_sample > 0:
@@ -544,6 +591,7 @@ def main():
             "cg": cg,
             "batched": batched,
             "adjoint": adjoint,
+            "nontensor": nontensor,
             "cpu_baseline": cpu,
         }
         print(json.dumps(line), flush=True)

@@ -282,6 +282,78 @@ int ceed_apply_diffusion_k(ceed_mesh_t mesh, const double *k, const void *geo, c
 int ceed_apply_diffusion_adjoint(ceed_mesh_t mesh, const double *k, const void *geo, const double *x,
                                  const double *r, double *dLdx, double *dLdk, void *stream);
 
+/* ---------------------------------------------------------------- non-tensor (simplex) elements */
+
+/* Non-tensor elements (paper Section 3, libCEED's non-tensor bases and the MAGMA backend): the
+ * caller provides the interpolation and gradient matrices of the basis at the quadrature points and
+ * the quadrature weights, and the operator applies them densely, element by element:
+ *   mass       y^e = B^T D B u^e,   D = w |det J| rho
+ *   diffusion  y^e = G^T D G u^e,   D = w k adj(J) adj(J)^T / det J   (3x3 per point)
+ * The operator is basis- and rule-agnostic; the element geometry is the affine simplex map
+ * x(xi) = v0 + sum_d xi_d (v_d - v0) from 4 vertices (tetrahedra).  L-vectors are FP64 [n_ldof]
+ * (one component).  Two algorithms, selectable per (op, prec):
+ *   CEED_NT_FUSED  one fused kernel (gather, forward contraction, pointwise D, transposed
+ *                  contraction in shared memory and registers), 32 elements per thread block;
+ *   CEED_NT_GEMM   the paper's GEMM formulation: the element inputs form one [E x P] matrix, each
+ *                  basis action is one GEMM with the [P x D Q] basis matrix (cuBLAS), optionally
+ *                  split into a strided batch of eta-element blocks; gemm_mode 0 = native
+ *                  FP64/FP32, 1 = emulated on the tensor cores (FP64: fixed-point slices; FP32:
+ *                  three BF16 terms), 2 = TF32 inputs (F32 only; about 1e-3 relative accuracy).
+ * Both finish with a deterministic transposed restriction (every node sums its element entries in
+ * a fixed order).  The handle owns its tables, an element-vector buffer [P][E] and, once the GEMM
+ * algorithm has been selected or tuned, two GEMM work arrays ([P][E] and [3 Q][E] doubles). */
+typedef struct ceed_nt_s *ceed_nt_t;
+typedef enum { CEED_NT_FUSED = 0, CEED_NT_GEMM = 1 } ceed_nt_algo;
+
+typedef struct {
+  int64_t n_elem;            /* E >= 1 */
+  int64_t n_ldof;            /* nodes, < 2^29 */
+  int32_t P;                 /* basis functions per element, 1..128 */
+  int32_t Q;                 /* quadrature points per element, 1..1024 */
+  const double *interp;      /* host [Q][P]: B[q][n] = phi_n(xi_q) */
+  const double *grad;        /* host [3][Q][P]: G[d][q][n] = d phi_n / d xi_d (xi_q) */
+  const double *qweight;     /* host [Q] reference weights (sum = reference volume) */
+  const double *qref;        /* host [Q][3] reference coordinates of the points (for x(xi_q)) */
+  const int32_t *elem_dofs;  /* device [E][P], node n of element e (the column order of interp/grad) */
+  const double *vertices;    /* device [E][4][3] simplex vertices v0..v3 */
+  const uint8_t *dirichlet;  /* device [n_ldof] (nonzero = Dirichlet node) or NULL */
+} ceed_nt_desc;
+
+/* The degree-p tetrahedron as a basis for ceed_nt_setup (a helper; the operator takes any basis):
+ * equispaced Lagrange basis of P_p on the reference tetrahedron {xi >= 0, xi_1+xi_2+xi_3 <= 1}, in
+ * Silvester's product form, nodes (i, j, k)/p with i + j + k <= p ordered k slowest and i fastest;
+ * the conical product rule with q Gauss-Jacobi points per collapsed direction (exact for total
+ * degree 2q - 1; point a + q (b + q c) at xi = (u_a, (1-u_a) v_b, (1-u_a)(1-v_b) w_c)).
+ * Sizes: P = (p+1)(p+2)(p+3)/6, Q = q^3; p in 1..7, q in 1..10.  Host arrays, no GPU work. */
+int ceed_simplex_sizes(int p, int q, int32_t *P, int32_t *Q);
+int ceed_simplex_basis(int p, int q, double *interp, double *grad, double *qweight, double *qref);
+
+/* Build a non-tensor operator handle: copies the basis to the device, validates elem_dofs (in
+ * range, no node twice in an element, every node referenced), builds the transposed restriction.
+ * Synchronizes `stream`.  Errors: INVALID, OOM, CUDA. */
+int ceed_nt_setup(const ceed_nt_desc *desc, ceed_nt_t *out, void *stream);
+int ceed_nt_destroy(ceed_nt_t h);
+/* Quadrature-data bytes for (op, prec F64 or F32); layout [ncomp][Q][E] (element fastest). */
+size_t ceed_nt_qdata_bytes(ceed_nt_t h, int op, int prec);
+/* Quadrature data of the affine simplices (coefficients as for ceed_build_qdata; PER_QPT is
+ * [E][Q]).  Synchronizes; BAD_GEOMETRY if det J <= 0 in some element. */
+int ceed_nt_build_qdata(ceed_nt_t h, int op, int coeff_kind, const double *coeff, int prec, void *qdata,
+                        void *stream);
+/* y = A x with the algorithm selected for (op, prec) (default FUSED); asynchronous on `stream`;
+ * y overwritten; CEED_APPLY_DIRICHLET masks Dirichlet rows and columns (y = x there). */
+int ceed_nt_apply(ceed_nt_t h, int op, const void *qdata, int prec, const double *x, double *y,
+                  unsigned flags, void *stream);
+/* Select the algorithm for (op, prec); GEMM allocates the handle's GEMM work arrays. */
+int ceed_nt_set_algorithm(ceed_nt_t h, int op, int prec, int algo, int64_t eta, int gemm_mode);
+int ceed_nt_get_algorithm(ceed_nt_t h, int op, int prec, int32_t *algo, int64_t *eta, int32_t *gemm_mode,
+                          float *ms);
+/* Autotuner (the paper's selection of routine and batch size eta by measurement): times FUSED and
+ * GEMM with eta in {all, 1024, 4096, 16384, 65536} and gemm_mode 0 and 1 (and 2 if include_tf32,
+ * F32 only) on the caller's buffers (y overwritten) with CUDA events, and keeps the fastest for
+ * (op, prec).  Synchronizes `stream`. */
+int ceed_nt_autotune(ceed_nt_t h, int op, const void *qdata, int prec, const double *x, double *y,
+                     int include_tf32, void *stream);
+
 /* ---------------------------------------------------------------- vectors */
 
 /* Deterministic dot product of two device FP64 vectors; the result is written to *out

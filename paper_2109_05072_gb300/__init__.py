@@ -26,6 +26,7 @@ CEED_OP_MASS, CEED_OP_DIFFUSION = 0, 1
 CEED_COEFF_ONE, CEED_COEFF_CONST, CEED_COEFF_SINE, CEED_COEFF_PER_QPT = 0, 1, 2, 3
 CEED_APPLY_DIRICHLET = 1
 CEED_CG_FP64, CEED_CG_MIXED = 0, 1
+CEED_NT_FUSED, CEED_NT_GEMM = 0, 1
 
 PREC_BYTES = {CEED_F64: 8, CEED_F32: 4, CEED_BF16: 2, CEED_F16: 2, CEED_F32_GEO: 4, CEED_F64_DF: 8}
 
@@ -53,6 +54,13 @@ class _CgOpts(ctypes.Structure):
 class _PmgOpts(ctypes.Structure):
     _fields_ = [("smooth_degree", ctypes.c_int32), ("smooth_ratio", ctypes.c_double), ("eig_iters", ctypes.c_int32),
                 ("coarse_tol", ctypes.c_double), ("coarse_max_iter", ctypes.c_int32), ("prec_lo", ctypes.c_int32)]
+
+
+class _NtDesc(ctypes.Structure):
+    _fields_ = [("n_elem", ctypes.c_int64), ("n_ldof", ctypes.c_int64), ("P", ctypes.c_int32), ("Q", ctypes.c_int32),
+                ("interp", ctypes.c_void_p), ("grad", ctypes.c_void_p), ("qweight", ctypes.c_void_p),
+                ("qref", ctypes.c_void_p), ("elem_dofs", ctypes.c_void_p), ("vertices", ctypes.c_void_p),
+                ("dirichlet", ctypes.c_void_p)]
 
 
 class _CgReport(ctypes.Structure):
@@ -101,6 +109,18 @@ def _load():
         "ceed_batch_info": (ctypes.c_int, [vp, ctypes.POINTER(i32), ctypes.POINTER(i32), ctypes.POINTER(ctypes.c_uint32)]),
         "ceed_batch_status": (ctypes.c_int, [vp, vp]),
         "ceed_batch_destroy": (ctypes.c_int, [vp]),
+        "ceed_simplex_sizes": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.POINTER(i32), ctypes.POINTER(i32)]),
+        "ceed_simplex_basis": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, vp, vp, vp, vp]),
+        "ceed_nt_setup": (ctypes.c_int, [ctypes.POINTER(_NtDesc), ctypes.POINTER(vp), vp]),
+        "ceed_nt_destroy": (ctypes.c_int, [vp]),
+        "ceed_nt_qdata_bytes": (sz, [vp, ctypes.c_int, ctypes.c_int]),
+        "ceed_nt_build_qdata": (ctypes.c_int, [vp, ctypes.c_int, ctypes.c_int, vp, ctypes.c_int, vp, vp]),
+        "ceed_nt_apply": (ctypes.c_int, [vp, ctypes.c_int, vp, ctypes.c_int, vp, vp, u32, vp]),
+        "ceed_nt_set_algorithm": (ctypes.c_int, [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, i64, ctypes.c_int]),
+        "ceed_nt_get_algorithm": (ctypes.c_int, [vp, ctypes.c_int, ctypes.c_int, ctypes.POINTER(i32),
+                                                 ctypes.POINTER(i64), ctypes.POINTER(i32),
+                                                 ctypes.POINTER(ctypes.c_float)]),
+        "ceed_nt_autotune": (ctypes.c_int, [vp, ctypes.c_int, vp, ctypes.c_int, vp, vp, ctypes.c_int, vp]),
         "ceed_dot_workspace_bytes": (sz, [i64]),
         "ceed_dot": (ctypes.c_int, [vp, vp, i64, vp, vp, vp]),
         "ceed_dot_noalloc_max_n": (i64, []),
@@ -387,6 +407,102 @@ def ceed_apply_diffusion_k(mesh: Mesh, k, geo, x, y, flags=0, stream=None):
 def ceed_apply_diffusion_adjoint(mesh: Mesh, k, geo, x, r, dLdx, dLdk, stream=None):
     _check(_lib.ceed_apply_diffusion_adjoint(mesh.handle, _ptr(k), _ptr(geo), _ptr(x), _ptr(r), _ptr(dLdx),
                                              _ptr(dLdk), _stream(stream)))
+
+
+def ceed_simplex_sizes(p: int, q: int):
+    """(P, Q) of the degree-p tetrahedron with q conical-rule points per direction."""
+    P, Q = ctypes.c_int32(), ctypes.c_int32()
+    _check(_lib.ceed_simplex_sizes(p, q, ctypes.byref(P), ctypes.byref(Q)))
+    return P.value, Q.value
+
+
+def ceed_simplex_basis(p: int, q: int):
+    """Host tables of the degree-p tetrahedron: interp [Q, P], grad [3, Q, P], qweight [Q], qref [Q, 3]."""
+    import numpy as np
+    P, Q = ceed_simplex_sizes(p, q)
+    interp, grad = np.empty((Q, P)), np.empty((3, Q, P))
+    qw, qref = np.empty(Q), np.empty((Q, 3))
+    ptr = lambda a: a.ctypes.data_as(ctypes.c_void_p)
+    _check(_lib.ceed_simplex_basis(p, q, ptr(interp), ptr(grad), ptr(qw), ptr(qref)))
+    return interp, grad, qw, qref
+
+
+class NonTensor:
+    """Owns a ceed_nt_t (non-tensor element operator); released on close() or garbage collection."""
+
+    def __init__(self, handle, n_elem, n_ldof, P, Q):
+        self.handle, self.n_elem, self.n_ldof, self.P, self.Q = handle, n_elem, n_ldof, P, Q
+
+    def close(self):
+        if self.handle:
+            _lib.ceed_nt_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def ceed_nt_setup(n_elem, n_ldof, interp, grad, qweight, qref, elem_dofs, vertices, dirichlet=None,
+                  stream=None) -> NonTensor:
+    """interp/grad/qweight/qref: host numpy float64 arrays; elem_dofs/vertices/dirichlet: CUDA tensors."""
+    import numpy as np
+    assert elem_dofs.dtype == torch.int32 and vertices.dtype == torch.float64
+    assert dirichlet is None or dirichlet.dtype == torch.uint8
+    interp, grad, qweight, qref = (np.ascontiguousarray(a, dtype=np.float64) for a in (interp, grad, qweight, qref))
+    Q, P = interp.shape
+    assert grad.shape == (3, Q, P) and qweight.shape == (Q,) and qref.shape == (Q, 3)
+    hp = lambda a: a.ctypes.data_as(ctypes.c_void_p)
+    d = _NtDesc(n_elem, n_ldof, P, Q, hp(interp), hp(grad), hp(qweight), hp(qref), _ptr(elem_dofs), _ptr(vertices),
+                _ptr(dirichlet))
+    h = ctypes.c_void_p()
+    _check(_lib.ceed_nt_setup(ctypes.byref(d), ctypes.byref(h), _stream(stream)))
+    return NonTensor(h, n_elem, n_ldof, P, Q)
+
+
+def ceed_nt_destroy(nt: NonTensor):
+    nt.close()
+
+
+def ceed_nt_qdata_bytes(nt: NonTensor, op: int, prec: int) -> int:
+    return int(_lib.ceed_nt_qdata_bytes(nt.handle, op, prec))
+
+
+def alloc_nt_qdata(nt: NonTensor, op: int, prec: int, device=None) -> torch.Tensor:
+    return torch.empty(ceed_nt_qdata_bytes(nt, op, prec), dtype=torch.uint8, device=device or "cuda")
+
+
+def ceed_nt_build_qdata(nt: NonTensor, op, coeff_kind, coeff, prec, qdata, stream=None):
+    if coeff_kind == CEED_COEFF_CONST:
+        cval = (ctypes.c_double * 1)(float(coeff))
+        cptr = ctypes.cast(cval, ctypes.c_void_p)
+    else:
+        cptr = _ptr(coeff) if coeff is not None else None
+    _check(_lib.ceed_nt_build_qdata(nt.handle, op, coeff_kind, cptr, prec, _ptr(qdata), _stream(stream)))
+
+
+def ceed_nt_apply(nt: NonTensor, op, qdata, prec, x, y, flags=0, stream=None):
+    _check(_lib.ceed_nt_apply(nt.handle, op, _ptr(qdata), prec, _ptr(x), _ptr(y), flags, _stream(stream)))
+
+
+def ceed_nt_set_algorithm(nt: NonTensor, op, prec, algo, eta=0, gemm_mode=0):
+    _check(_lib.ceed_nt_set_algorithm(nt.handle, op, prec, algo, eta, gemm_mode))
+
+
+def ceed_nt_get_algorithm(nt: NonTensor, op, prec):
+    """(algo, eta, gemm_mode, ms) in use for (op, prec)."""
+    a, e, g, ms = ctypes.c_int32(), ctypes.c_int64(), ctypes.c_int32(), ctypes.c_float()
+    _check(_lib.ceed_nt_get_algorithm(nt.handle, op, prec, ctypes.byref(a), ctypes.byref(e), ctypes.byref(g),
+                                      ctypes.byref(ms)))
+    return a.value, e.value, g.value, ms.value
+
+
+def ceed_nt_autotune(nt: NonTensor, op, qdata, prec, x, y, include_tf32=False, stream=None):
+    _check(_lib.ceed_nt_autotune(nt.handle, op, _ptr(qdata), prec, _ptr(x), _ptr(y), int(include_tf32),
+                                 _stream(stream)))
+    return ceed_nt_get_algorithm(nt, op, prec)
 
 
 def ceed_dot_workspace_bytes(n: int) -> int:

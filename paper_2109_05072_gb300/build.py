@@ -67,7 +67,7 @@ def build(verbose: bool = False, jobs: int | None = None, force: bool = False, p
     if todo or not os.path.exists(LIB):
         tmp = LIB + ".tmp"
         cudalib = os.path.join(os.path.dirname(os.path.dirname(os.path.realpath(cc))), "lib64")
-        cmd = [cc, *ARCH, "-shared", "-cudart", "shared", "-Xlinker", "-rpath", "-Xlinker", cudalib, "-o", tmp, *objs]
+        cmd = [cc, *ARCH, "-shared", "-cudart", "shared", "-Xlinker", "-rpath", "-Xlinker", cudalib, "-o", tmp, *objs, "-lcublas"]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"link failed:\n{r.stderr}")
