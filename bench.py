@@ -283,16 +283,42 @@ def run_adjoint(ceed, dev, args):
     return out
 
 
+def nt_workload(ceed, dev, p=4, q=5, N=48):
+    """Degree-p tetrahedra, 6 per cube of the perturbed N^3 lattice, conical rule with q points per direction."""
+    import torch
+    m = synthetic.TetMesh(N, N, N, p, seed=0)
+    interp, grad, qw, qref = ceed.ceed_simplex_basis(p, q)
+    nt = ceed.ceed_nt_setup(m.n_elem, m.n_ldof, interp, grad, qw, qref, torch.from_numpy(m.elem_dofs).to(dev),
+                            torch.from_numpy(m.vertices).to(dev), None)
+    return m, nt
+
+
+def run_nt_profile(args):
+    """Three applies of the tetrahedral diffusion operator with one algorithm (for ncu captures)."""
+    import torch
+    import paper_2109_05072_gb300 as ceed
+    dev = torch.device("cuda", 0)
+    m, nt = nt_workload(ceed, dev)
+    algo, prec = {"fused64": (ceed.CEED_NT_FUSED, ceed.CEED_F64), "fused32": (ceed.CEED_NT_FUSED, ceed.CEED_F32),
+                  "gemm32": (ceed.CEED_NT_GEMM, ceed.CEED_F32), "tc": (ceed.CEED_NT_TC, ceed.CEED_F32)}[args.nt_profile]
+    qd = ceed.alloc_nt_qdata(nt, ceed.CEED_OP_DIFFUSION, prec, dev)
+    ceed.ceed_nt_build_qdata(nt, ceed.CEED_OP_DIFFUSION, ceed.CEED_COEFF_SINE, None, prec, qd)
+    ceed.ceed_nt_set_algorithm(nt, ceed.CEED_OP_DIFFUSION, prec, algo)
+    x = torch.from_numpy(synthetic.uniform(m.n_ldof, seed=1)).to(dev)
+    y = torch.empty_like(x)
+    for _ in range(3):
+        ceed.ceed_nt_apply(nt, ceed.CEED_OP_DIFFUSION, qd, prec, x, y)
+    ceed.ceed_nt_status(nt)
+    print(json.dumps({"nt_profile": args.nt_profile, "n_elem": m.n_elem, "n_ldof": m.n_ldof}))
+
+
 def run_nontensor(ceed, dev, args):
     """Non-tensor elements (the paper's GEMM formulation of the MAGMA backend, and the fused kernel):
     degree-4 tetrahedra, 6 per cube of the perturbed 48^3 lattice (663,552 elements, 7,189,057 nodes),
     conical rule with q = 5 points per direction (Q = 125), diffusion with the sine coefficient."""
     import torch
     p, q, N = 4, 5, 48
-    m = synthetic.TetMesh(N, N, N, p, seed=0)
-    interp, grad, qw, qref = ceed.ceed_simplex_basis(p, q)
-    nt = ceed.ceed_nt_setup(m.n_elem, m.n_ldof, interp, grad, qw, qref, torch.from_numpy(m.elem_dofs).to(dev),
-                            torch.from_numpy(m.vertices).to(dev), None)
+    m, nt = nt_workload(ceed, dev, p, q, N)
     P, Q, E = nt.P, nt.Q, m.n_elem
     x = torch.from_numpy(synthetic.uniform(m.n_ldof, seed=1)).to(dev)
     y = torch.empty_like(x)
@@ -310,6 +336,7 @@ def run_nontensor(ceed, dev, args):
                  ("gemm_emulated", ceed.CEED_NT_GEMM, 0, 1)]
         if prec == ceed.CEED_F32:
             modes.append(("gemm_tf32", ceed.CEED_NT_GEMM, 0, 2))
+            modes.append(("tensor_core_3xtf32", ceed.CEED_NT_TC, 0, 0))
         for label, algo, eta, gm in modes:
             ceed.ceed_nt_set_algorithm(nt, ceed.CEED_OP_DIFFUSION, prec, algo, eta, gm)
             ms = _time_cuda(lambda: ceed.ceed_nt_apply(nt, ceed.CEED_OP_DIFFUSION, qd, prec, x, y), 5, 3)
@@ -317,7 +344,7 @@ def run_nontensor(ceed, dev, args):
                                 "gdofs": m.n_ldof / ms / 1e6, "tflops": flops / ms / 1e9,
                                 "alg_gbs": by / ms / 1e6, "hbm_frac": by / ms / 1e6 / hbm_peak})
         algo, eta, gm, tms = ceed.ceed_nt_autotune(nt, ceed.CEED_OP_DIFFUSION, qd, prec, x, y)
-        out[f"autotuned_{name}"] = {"algo": ["fused", "gemm"][algo], "eta": eta, "gemm_mode": gm, "ms": tms}
+        out[f"autotuned_{name}"] = {"algo": ["fused", "gemm", "tensor_core"][algo], "eta": eta, "gemm_mode": gm, "ms": tms}
         del qd
         torch.cuda.empty_cache()
     nt.close()
@@ -343,11 +370,15 @@ def main():
     ap.add_argument("--adjoint", type=int, default=1, help="measure the adjoint kernels")
     ap.add_argument("--df", type=int, default=1, help="measure the double-float FP64-accurate operator")
     ap.add_argument("--nontensor", type=int, default=1, help="measure the non-tensor (tetrahedral) operator")
+    ap.add_argument("--nt-profile", default=None, choices=["fused64", "fused32", "gemm32", "tc"],
+                    help="profiling case: three tetrahedral diffusion applies with one algorithm, then exit")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
     if args.profile:
         return run_profile(args)
+    if args.nt_profile:
+        return run_nt_profile(args)
     if args.warmup < 3:
         raise SystemExit("--warmup must be >= 3")
 

@@ -299,11 +299,15 @@ int ceed_apply_diffusion_adjoint(ceed_mesh_t mesh, const double *k, const void *
  *                  split into a strided batch of eta-element blocks; gemm_mode 0 = native
  *                  FP64/FP32, 1 = emulated on the tensor cores (FP64: fixed-point slices; FP32:
  *                  three BF16 terms), 2 = TF32 inputs (F32 only; about 1e-3 relative accuracy).
- * Both finish with a deterministic transposed restriction (every node sums its element entries in
+ *   CEED_NT_TC     (F32, P in {4, 10, 20, 35, 56, 84}: the degree-1..6 tetrahedra) one fused kernel on
+ *                  the tensor cores (tcgen05): tiles of 128 elements, both basis actions as TF32 matrix
+ *                  products with FP32-level accuracy from the three-product split
+ *                  a b ~ a_hi b_hi + a_hi b_lo + a_lo b_hi, the pointwise D on the CUDA cores between them.
+ * All finish with a deterministic transposed restriction (every node sums its element entries in
  * a fixed order).  The handle owns its tables, an element-vector buffer [P][E] and, once the GEMM
  * algorithm has been selected or tuned, two GEMM work arrays ([P][E] and [3 Q][E] doubles). */
 typedef struct ceed_nt_s *ceed_nt_t;
-typedef enum { CEED_NT_FUSED = 0, CEED_NT_GEMM = 1 } ceed_nt_algo;
+typedef enum { CEED_NT_FUSED = 0, CEED_NT_GEMM = 1, CEED_NT_TC = 2 } ceed_nt_algo;
 
 typedef struct {
   int64_t n_elem;            /* E >= 1 */
@@ -347,12 +351,15 @@ int ceed_nt_apply(ceed_nt_t h, int op, const void *qdata, int prec, const double
 int ceed_nt_set_algorithm(ceed_nt_t h, int op, int prec, int algo, int64_t eta, int gemm_mode);
 int ceed_nt_get_algorithm(ceed_nt_t h, int op, int prec, int32_t *algo, int64_t *eta, int32_t *gemm_mode,
                           float *ms);
-/* Autotuner (the paper's selection of routine and batch size eta by measurement): times FUSED and
- * GEMM with eta in {all, 1024, 4096, 16384, 65536} and gemm_mode 0 and 1 (and 2 if include_tf32,
- * F32 only) on the caller's buffers (y overwritten) with CUDA events, and keeps the fastest for
- * (op, prec).  Synchronizes `stream`. */
+/* Autotuner (the paper's selection of routine and batch size eta by measurement): times FUSED,
+ * TC (F32, supported P) and GEMM with eta in {all, 1024, 4096, 16384, 65536} and gemm_mode 0 and 1
+ * (and 2 if include_tf32, F32 only) on the caller's buffers (y overwritten) with CUDA events, and
+ * keeps the fastest for (op, prec).  Synchronizes `stream`. */
 int ceed_nt_autotune(ceed_nt_t h, int op, const void *qdata, int prec, const double *x, double *y,
                      int include_tf32, void *stream);
+/* Synchronizes `stream`; TIMEOUT if a bounded device-side wait of an earlier tensor-core launch
+ * expired (the launch then left its element vectors incomplete). */
+int ceed_nt_status(ceed_nt_t h, void *stream);
 
 /* ---------------------------------------------------------------- vectors */
 

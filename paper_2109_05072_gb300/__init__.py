@@ -26,7 +26,7 @@ CEED_OP_MASS, CEED_OP_DIFFUSION = 0, 1
 CEED_COEFF_ONE, CEED_COEFF_CONST, CEED_COEFF_SINE, CEED_COEFF_PER_QPT = 0, 1, 2, 3
 CEED_APPLY_DIRICHLET = 1
 CEED_CG_FP64, CEED_CG_MIXED = 0, 1
-CEED_NT_FUSED, CEED_NT_GEMM = 0, 1
+CEED_NT_FUSED, CEED_NT_GEMM, CEED_NT_TC = 0, 1, 2
 
 PREC_BYTES = {CEED_F64: 8, CEED_F32: 4, CEED_BF16: 2, CEED_F16: 2, CEED_F32_GEO: 4, CEED_F64_DF: 8}
 
@@ -121,6 +121,7 @@ def _load():
                                                  ctypes.POINTER(i64), ctypes.POINTER(i32),
                                                  ctypes.POINTER(ctypes.c_float)]),
         "ceed_nt_autotune": (ctypes.c_int, [vp, ctypes.c_int, vp, ctypes.c_int, vp, vp, ctypes.c_int, vp]),
+        "ceed_nt_status": (ctypes.c_int, [vp, vp]),
         "ceed_dot_workspace_bytes": (sz, [i64]),
         "ceed_dot": (ctypes.c_int, [vp, vp, i64, vp, vp, vp]),
         "ceed_dot_noalloc_max_n": (i64, []),
@@ -503,6 +504,10 @@ def ceed_nt_autotune(nt: NonTensor, op, qdata, prec, x, y, include_tf32=False, s
     _check(_lib.ceed_nt_autotune(nt.handle, op, _ptr(qdata), prec, _ptr(x), _ptr(y), int(include_tf32),
                                  _stream(stream)))
     return ceed_nt_get_algorithm(nt, op, prec)
+
+
+def ceed_nt_status(nt: NonTensor, stream=None):
+    _check(_lib.ceed_nt_status(nt.handle, _stream(stream)))
 
 
 def ceed_dot_workspace_bytes(n: int) -> int:

@@ -26,47 +26,7 @@
 #include <vector>
 
 #include "geometry.cuh"
-#include "internal.h"
-
-namespace ceedgb {
-
-constexpr int NT_MAXP = 128;   // basis functions per element
-constexpr int NT_MAXQ = 1024;  // quadrature points per element
-constexpr int NT_NE = 32;      // elements per block of the fused kernel (one per lane)
-constexpr int NT_WARPS = 8;
-constexpr int NT_QC = 32;      // quadrature points per chunk of the fused kernel
-constexpr int NT_YR = NT_MAXP / NT_WARPS;
-
-struct NtChoice {
-  int algo = CEED_NT_FUSED;
-  int64_t eta = 0;     // GEMM: elements per batched block (0: one GEMM over all elements)
-  int gemm_mode = 0;   // GEMM: 0 native, 1 emulated on tensor cores, 2 TF32 (FP32 only)
-  float ms = 0.f;
-};
-
-}  // namespace ceedgb
-
-struct ceed_nt_s {
-  int device = 0;
-  int64_t E = 0, n_ldof = 0;
-  int P = 0, Q = 0;
-  double *d_tab64 = nullptr;   // [4][Q][P]: interp, then grad along xi_1, xi_2, xi_3
-  float *d_tab32 = nullptr;
-  double *d_qw = nullptr;      // [Q]
-  double *d_qref = nullptr;    // [Q][3]
-  uint32_t *d_rmap = nullptr;  // [P][E]
-  int64_t *d_off = nullptr;    // [n_ldof + 1] transposed restriction offsets
-  uint32_t *d_pos = nullptr;   // [P E] positions n E + e, ascending per node
-  uint8_t *d_dir = nullptr;    // [n_ldof] Dirichlet flags (all zero without a mask)
-  double *d_vert = nullptr;    // [E][4][3]
-  int *d_err = nullptr;
-  bool has_dirichlet = false;
-  void *d_evec = nullptr;      // [P][E] element outputs (FP64-sized)
-  void *d_u = nullptr;         // GEMM workspaces: [P][E] and [3 Q][E] (FP64-sized)
-  void *d_s = nullptr;
-  cublasHandle_t blas = nullptr;
-  ceedgb::NtChoice choice[2][2];  // [op][prec: 0 F64, 1 F32]
-};
+#include "nontensor.h"
 
 namespace ceedgb {
 
@@ -430,6 +390,12 @@ static int nt_gemm(ceed_nt_t h, bool transB, int m_n, int m_k, const T *A, const
   cublasComputeType_t ct;
   if (sizeof(T) == 8) ct = mode == 1 ? CUBLAS_COMPUTE_64F_EMULATED_FIXEDPOINT : CUBLAS_COMPUTE_64F;
   else ct = mode == 1 ? CUBLAS_COMPUTE_32F_EMULATED_16BFX9 : mode == 2 ? CUBLAS_COMPUTE_32F_FAST_TF32 : CUBLAS_COMPUTE_32F;
+  // the handle's math mode admits the emulated algorithms only when they are asked for
+  cublasMath_t mm = CUBLAS_DEFAULT_MATH;
+  if (mode == 1) mm = sizeof(T) == 8 ? CUBLAS_FP64_EMULATED_FIXEDPOINT_MATH : CUBLAS_FP32_EMULATED_BF16X9_MATH;
+  else if (mode == 2) mm = CUBLAS_TF32_TENSOR_OP_MATH;
+  cublasStatus_t ms = cublasSetMathMode(h->blas, mm);
+  if (ms != CUBLAS_STATUS_SUCCESS) return blas_fail(ms, "cublasSetMathMode");
   const T one = T(1), zero = T(0);
   const int64_t E = h->E;
   const cublasOperation_t ob = transB ? CUBLAS_OP_T : CUBLAS_OP_N;
@@ -472,6 +438,10 @@ static int nt_apply_t(ceed_nt_t h, const NtChoice &c, const T *tab, const T *qd,
   int st;
   if (c.algo == CEED_NT_FUSED) {
     st = launch_fused<T, D>(h, tab, qd, x, Ye, masked, s);
+  } else if (c.algo == CEED_NT_TC) {
+    if (sizeof(T) != 4) return fail(CEED_ERR_UNSUPPORTED, "tensor-core algorithm: F32 only");
+    st = nt_tc_apply(h, D == 1 ? CEED_OP_MASS : CEED_OP_DIFFUSION, reinterpret_cast<const float *>(qd), x,
+                     reinterpret_cast<float *>(Ye), masked, s);
   } else {
     if ((st = nt_ensure_gemm_workspace(h)) != CEED_OK) return st;
     T *U = reinterpret_cast<T *>(h->d_u), *S = reinterpret_cast<T *>(h->d_s);
@@ -536,6 +506,8 @@ struct NtFree {
     cudaFree(h->d_evec);
     cudaFree(h->d_u);
     cudaFree(h->d_s);
+    cudaFree(h->d_tc_tab[0]);
+    cudaFree(h->d_tc_tab[1]);
     delete h;
   }
 };
@@ -711,7 +683,12 @@ extern "C" int ceed_nt_apply(ceed_nt_t h, int op, const void *qdata, int prec, c
 }
 
 static int nt_check_choice(ceed_nt_t h, int prec, int algo, int64_t eta, int gemm_mode) {
-  if (algo != CEED_NT_FUSED && algo != CEED_NT_GEMM) return fail(CEED_ERR_INVALID, "algo must be FUSED or GEMM");
+  if (algo != CEED_NT_FUSED && algo != CEED_NT_GEMM && algo != CEED_NT_TC)
+    return fail(CEED_ERR_INVALID, "algo must be FUSED, GEMM or TC");
+  if (algo == CEED_NT_TC) {
+    if (prec != CEED_F32) return fail(CEED_ERR_INVALID, "the tensor-core algorithm computes in FP32 (prec F32)");
+    if (!nt_tc_supported(h->P)) return fail(CEED_ERR_UNSUPPORTED, "tensor-core algorithm: P must be 4, 10, 20, 35, 56 or 84");
+  }
   if (algo == CEED_NT_GEMM) {
     if (eta < 0) return fail(CEED_ERR_INVALID, "eta must be >= 0");
     if (gemm_mode < 0 || gemm_mode > 2 || (gemm_mode == 2 && prec != CEED_F32))
@@ -725,6 +702,7 @@ extern "C" int ceed_nt_set_algorithm(ceed_nt_t h, int op, int prec, int algo, in
   if (st != CEED_OK) return st;
   if ((st = nt_check_choice(h, prec, algo, eta, gemm_mode)) != CEED_OK) return st;
   if (algo == CEED_NT_GEMM && (st = nt_ensure_gemm_workspace(h)) != CEED_OK) return st;
+  if (algo == CEED_NT_TC && (st = nt_tc_prepare(h)) != CEED_OK) return st;
   NtChoice &c = h->choice[op][prec == CEED_F64 ? 0 : 1];
   c.algo = algo;
   c.eta = algo == CEED_NT_GEMM ? eta : 0;
@@ -754,6 +732,12 @@ extern "C" int ceed_nt_autotune(ceed_nt_t h, int op, const void *qdata, int prec
   cudaStream_t s = (cudaStream_t)stream;
   std::vector<NtChoice> cand;
   cand.push_back(NtChoice());
+  if (prec == CEED_F32 && nt_tc_supported(h->P)) {
+    if ((st = nt_tc_prepare(h)) != CEED_OK) return st;
+    NtChoice c;
+    c.algo = CEED_NT_TC;
+    cand.push_back(c);
+  }
   const int64_t etas[] = {0, 1024, 4096, 16384, 65536};
   const int nmodes = (prec == CEED_F32 && include_tf32) ? 3 : 2;
   for (int mode = 0; mode < nmodes; ++mode)
@@ -793,5 +777,14 @@ extern "C" int ceed_nt_autotune(ceed_nt_t h, int op, const void *qdata, int prec
   cudaEventDestroy(e1);
   if (st != CEED_OK) return st;
   h->choice[op][prec == CEED_F64 ? 0 : 1] = best;
+  return CEED_OK;
+}
+
+extern "C" int ceed_nt_status(ceed_nt_t h, void *stream) {
+  if (!h) return fail(CEED_ERR_INVALID, "null non-tensor operator handle");
+  int err = 0;
+  CEED_CUDA_CHECK(cudaMemcpyAsync(&err, h->d_err, sizeof(int), cudaMemcpyDeviceToHost, (cudaStream_t)stream));
+  CEED_CUDA_CHECK(cudaStreamSynchronize((cudaStream_t)stream));
+  if (err == CEED_ERR_TIMEOUT) return fail(CEED_ERR_TIMEOUT, "a bounded device wait of the tensor-core kernel expired");
   return CEED_OK;
 }

@@ -1,0 +1,629 @@
+// Tensor-core fused operator for non-tensor elements (the dense element operator of the paper's
+// Section 3, MAGMA backend: y^e = G^T D G u^e), written for the 5th-generation tensor cores of
+// sm_103a with tcgen05 instructions in inline PTX.
+//
+// One thread block processes a tile of 128 elements; element m of the tile is row m of every
+// matrix product, i.e. lane m of tensor memory (TMEM):
+//   GEMM1  S_d = U G_d^T          [128 x 16] per direction d and chunk of 16 quadrature points
+//                                  (A = U [128 x P] element inputs, B = the chunk's rows of G_d)
+//   pointwise (CUDA cores): thread of element m reads its row of S from TMEM, applies the 3x3
+//          (or 1x1) quadrature operator with the element's quadrature data, writes V
+//   GEMM2  Y += V_d G_d            [128 x P] accumulated in TMEM over directions and chunks
+// and the block finally stores Y as element vectors [P][E] (the transposed restriction that
+// follows is the same deterministic kernel as for the other algorithms).
+//
+// Precision: FP32 operands with FP32-level accuracy from TF32 tensor cores by the three-product
+// split a b ~ a_hi b_hi + a_hi b_lo + a_lo b_hi with a_hi = tf32(a), a_lo = a - a_hi (the
+// "3xTF32" scheme; the dropped a_lo b_lo term is ~2^-22 of a b), accumulated in FP32 in TMEM.
+//
+// Operands live in shared memory in the canonical no-swizzle K-major layout: 8-row x 16-byte core
+// matrices stored contiguously (128 bytes), core matrices adjacent along K at 128 bytes (LBO),
+// 8-row groups at K/4 * 128 bytes (SBO).  The basis matrices are constant: at setup they are
+// split, padded and written in that layout chunk by chunk, so one bulk TMA copy per chunk
+// (cp.async.bulk, completion on an mbarrier) brings a chunk's operands into shared memory,
+// double-buffered so the next chunk streams in while the current one is computed.
+// Every wait (bulk copy, MMA completion) is bounded; on expiry the kernel records
+// CEED_ERR_TIMEOUT, waits (bounded) for its own operations in flight, frees TMEM and returns.
+#include <algorithm>
+#include <cstring>
+#include <vector>
+
+#include "convert.cuh"
+#include "nontensor.h"
+
+namespace ceedgb {
+namespace {
+
+constexpr int TC_M = 128;      // elements per tile (MMA M, TMEM lanes)
+constexpr int TC_QC = 16;      // quadrature points per chunk (GEMM1 N, GEMM2 K)
+
+__host__ __device__ constexpr int kpad(int P) { return (P + 7) / 8 * 8; }     // K of GEMM1: multiple of 8
+__host__ __device__ constexpr int npad(int P) { return (P + 15) / 16 * 16; }  // N of GEMM2: multiple of 16
+
+// Offset (in 4-byte words) of element (r, k) in the canonical K-major no-swizzle layout of a
+// matrix with K columns (K a multiple of 4).
+__host__ __device__ constexpr int canon(int r, int k, int K) {
+  return ((r >> 3) * (K >> 2) + (k >> 2)) * 32 + (r & 7) * 4 + (k & 3);
+}
+
+// Words of one chunk of split tables for D directions: GT_hi, GT_lo [D][16 x KP], G_hi, G_lo [D][NP x 16].
+__host__ __device__ constexpr int chunk_words(int D, int KP, int NP) { return 2 * D * TC_QC * KP + 2 * D * NP * TC_QC; }
+
+__device__ __forceinline__ uint32_t su32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// Shared-memory matrix descriptor of tcgen05.mma: start address, leading (K-direction core matrix)
+// byte offset, stride (8-row group) byte offset, each >> 4; bits 46-48 = 0b001; no swizzle.
+__device__ __forceinline__ uint64_t sdesc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+  return (uint64_t)((saddr & 0x3FFFFu) >> 4) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
+         ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
+}
+
+// Instruction descriptor for kind::tf32: D F32 (bits 4-5 = 1), A and B TF32 (bits 7-9, 10-12 = 2),
+// both K-major, N >> 3 at bits 17-22, M >> 4 at bits 24-28.
+template <int M, int N>
+struct IDescTF32 {
+  static_assert(M == 128, "one CTA, M = 128");
+  static_assert(N % 16 == 0 && N >= 16 && N <= 256, "M = 128 needs N a multiple of 16 in [16, 256]");
+  static constexpr uint32_t value = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(N >> 3) << 17) |
+                                    ((uint32_t)(M >> 4) << 24);
+};
+
+__device__ __forceinline__ void mma_tf32(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t accum) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
+      "l"(a), "l"(b), "r"(idesc), "r"(accum)
+      : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t *bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(su32(bar))
+               : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+// 4 consecutive 32-bit TMEM columns of this thread's lane (warp w reads lanes 32 (w % 4) ...),
+// waiting for the load in the same statement so no use of the registers can precede it.
+__device__ __forceinline__ void tmem_ld4(uint32_t taddr, float (&v)[4]) {
+  uint32_t r0, r1, r2, r3;
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0, %1, %2, %3}, [%4];\n"
+      "tcgen05.wait::ld.sync.aligned;\n"
+      : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
+      : "r"(taddr)
+      : "memory");
+  v[0] = __uint_as_float(r0);
+  v[1] = __uint_as_float(r1);
+  v[2] = __uint_as_float(r2);
+  v[3] = __uint_as_float(r3);
+}
+
+__device__ __forceinline__ void bulk_load(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(su32(bar)), "r"(bytes) : "memory");
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   su32(dst)),
+               "l"(src), "r"(bytes), "r"(su32(bar))
+               : "memory");
+}
+
+// Bounded wait for phase `parity` of an mbarrier.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity) {
+  const uint32_t a = su32(bar);
+  for (int it = 0; it < (1 << 22); ++it) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(a), "r"(parity)
+        : "memory");
+    if (ok) return true;
+  }
+  return false;
+}
+
+// TF32 split: hi = x rounded to TF32 (10-bit mantissa), lo = x - hi (exact in FP32).
+__device__ __forceinline__ void split_tf32(float x, float &hi, float &lo) {
+  uint32_t h;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(h) : "f"(x));
+  hi = __uint_as_float(h);
+  lo = x - hi;
+}
+
+__device__ __forceinline__ void st_shared4(float *p, float a, float b, float c, float d) {
+  asm volatile("st.shared.v4.f32 [%0], {%1, %2, %3, %4};" ::"r"(su32(p)), "f"(a), "f"(b), "f"(c), "f"(d) : "memory");
+}
+
+// Shared-memory map of one block.  U: the tile's element inputs (hi, lo); TB[TBUF]: table chunks;
+// V[VBUF]: the pointwise results (hi, lo); then the mbarriers, the TMEM address and an abort flag.
+template <int D, int KP, int NP, int TBUF, int VBUF>
+struct TcLayout {
+  static constexpr int U_WORDS = TC_M * KP;                // per hi/lo
+  static constexpr int TB_WORDS = chunk_words(D, KP, NP);  // one table buffer
+  static constexpr int V_WORDS = D * TC_M * TC_QC;         // per hi/lo
+  static constexpr size_t U_HI = 0;
+  static constexpr size_t U_LO = U_HI + 4 * (size_t)U_WORDS;
+  static constexpr size_t TB = U_LO + 4 * (size_t)U_WORDS;
+  static constexpr size_t V = TB + 4 * (size_t)TB_WORDS * TBUF;   // buffer v: hi at V + 8 V_WORDS v, lo + 4 V_WORDS
+  static constexpr size_t BARS = V + 8 * (size_t)V_WORDS * VBUF;
+  static constexpr size_t BYTES = BARS + 16 * 8 + 16;
+  static_assert(BYTES <= 227 * 1024, "shared memory");
+};
+
+// mbarrier slots
+enum : int { B_TAB = 0, B_SFULL = 2, B_SFREE = 4, B_VFULL = 6, B_VFREE = 8, B_UFULL = 10, B_YFULL = 11, B_YFREE = 13,
+             B_DRAIN = 15 };
+constexpr int TC_CW = 16;                       // compute warps (0-15); warp 16 issues the MMAs
+constexpr int TC_COMPUTE = 32 * TC_CW;
+constexpr int TC_BLOCK = TC_COMPUTE + 32;
+constexpr int TC_GROUPS = TC_CW / 4;            // warps per TMEM lane quadrant
+constexpr int TC_PPT = TC_QC / TC_GROUPS;       // points of a chunk per compute thread
+static_assert(TC_PPT == 4, "one float4 of points per thread and direction");
+constexpr uint32_t TC_TMEM_ALLOC = 512;
+constexpr uint32_t TC_SCOL = 64;                // S buffer s at TMEM column 64 s
+constexpr uint32_t TC_YCOL0 = 256;              // Y buffer y at TMEM column 256 + 128 y
+
+__device__ __forceinline__ void mbar_init_n(uint64_t *bar, uint32_t n) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(bar)), "r"(n) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(su32(bar)) : "memory");
+}
+__device__ __forceinline__ bool mbar_try(uint64_t *bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(su32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Bounded wait that also gives up when another thread of the block has raised the abort flag.
+__device__ __forceinline__ bool mbar_wait_abortable(uint64_t *bar, uint32_t parity, volatile int *abort_flag) {
+  for (int it = 0; it < (1 << 22); ++it) {
+    if (mbar_try(bar, parity)) return true;
+    if ((it & 63) == 63 && *abort_flag) return false;
+  }
+  *abort_flag = 1;
+  return false;
+}
+
+// The tile's element inputs, split into TF32 hi/lo, written to the canonical layout (row m,
+// columns 4 k4 .. 4 k4 + 3 for this thread's share k4 = grp, grp + 4, ... of the column groups).  Loads go out in rounds
+// of up to two column groups (restriction entries first, then the L-vector values) so their
+// latencies overlap; the FP64 -> FP32 conversion uses integer instructions only.
+template <int KP>
+__device__ __forceinline__ void gather_tile(int64_t E, int P, int64_t e, bool valid, int grp, int m, int masked,
+                                            const uint32_t *__restrict__ rmap, const double *__restrict__ x,
+                                            float *u_hi, float *u_lo) {
+  constexpr int NG = KP / 4;   // column groups
+  constexpr int R = 2;         // groups per round
+#pragma unroll
+  for (int r0 = 0; r0 < (NG + TC_GROUPS - 1) / TC_GROUPS; r0 += R) {
+    uint32_t mm[R][4];
+#pragma unroll
+    for (int r = 0; r < R; ++r)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int k4 = grp + TC_GROUPS * (r0 + r), n = 4 * k4 + j;
+        mm[r][j] = (valid && k4 < NG && n < P) ? __ldg(rmap + (int64_t)n * E + e) : 0xFFFFFFFFu;
+      }
+    double v[R][4];
+#pragma unroll
+    for (int r = 0; r < R; ++r)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const uint32_t q = mm[r][j];
+        v[r][j] = (q == 0xFFFFFFFFu || (masked && (q & FLAG_DIR))) ? 0.0 : __ldg(x + (q & DOF_MASK));
+      }
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      const int k4 = grp + TC_GROUPS * (r0 + r);
+      if (k4 < NG) {
+        float h4[4], l4[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) split_tf32(d2f_fast(v[r][j]), h4[j], l4[j]);
+        const int o = canon(m, 4 * k4, KP);
+        st_shared4(u_hi + o, h4[0], h4[1], h4[2], h4[3]);
+        st_shared4(u_lo + o, l4[0], l4[1], l4[2], l4[3]);
+      }
+    }
+  }
+}
+
+// Quadrature data of one thread's TC_PPT points of chunk c of a tile (zero outside the mesh / rule).
+template <int D>
+__device__ __forceinline__ void load_qdata(const float *__restrict__ qd, int64_t E, int Q, int64_t e, bool valid,
+                                           int c, int grp, float (&qv)[TC_PPT][D == 3 ? 6 : 1]) {
+  const int64_t cs = (int64_t)Q * E;
+  const int q0 = c * TC_QC + TC_PPT * grp;
+  const float *base = qd + (int64_t)q0 * E + e;
+#pragma unroll
+  for (int j = 0; j < TC_PPT; ++j) {
+    const bool in = valid && q0 + j < Q;
+#pragma unroll
+    for (int k = 0; k < (D == 3 ? 6 : 1); ++k) qv[j][k] = in ? __ldg(base + k * cs + (int64_t)j * E) : 0.f;
+  }
+}
+
+// The fused kernel, persistent (block b takes tiles b, b + gridDim.x, ...) and warp-specialized:
+// warp 16 (one thread) streams the table chunks in with bulk copies and issues every matrix
+// product; warps 0-15 gather inputs, apply the pointwise operator and write the element vectors.
+// They hand buffers to each other through mbarriers (the tensor core signals completion through
+// tcgen05.commit), with S (TMEM), V (shared memory, when it fits) and Y (TMEM) double-buffered so
+// the tensor core works on chunk g+1 while the CUDA cores process chunk g.  Warp w < 16 serves TMEM
+// lane quadrant w % 4 (elements 32 (w % 4) ... of the tile) and group grp = w / 4: points
+// 4 grp .. 4 grp + 3 of each chunk, every fourth input column group and a quarter of the output nodes.
+template <int D, int KP, int NP, int TBUF, int VBUF>
+__global__ void __launch_bounds__(TC_BLOCK, 1)
+    nt_tc_kernel(int64_t E, int P, int Q, int nch, const uint32_t *__restrict__ rmap, const double *__restrict__ x,
+                 const float *__restrict__ tabs, const float *__restrict__ qd, float *__restrict__ Ye, int masked,
+                 int *err) {
+  using L = TcLayout<D, KP, NP, TBUF, VBUF>;
+  extern __shared__ __align__(1024) unsigned char tc_smem[];
+  float *u_hi = reinterpret_cast<float *>(tc_smem + L::U_HI);
+  float *u_lo = reinterpret_cast<float *>(tc_smem + L::U_LO);
+  float *tb = reinterpret_cast<float *>(tc_smem + L::TB);
+  float *vbase = reinterpret_cast<float *>(tc_smem + L::V);
+  uint64_t *bar = reinterpret_cast<uint64_t *>(tc_smem + L::BARS);
+  uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(tc_smem + L::BARS + 128);
+  volatile int *abort_flag = reinterpret_cast<volatile int *>(tc_smem + L::BARS + 132);
+
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int64_t ntiles = (E + TC_M - 1) / TC_M;
+  const int64_t my_tiles = blockIdx.x < ntiles ? (ntiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+  const int64_t G = my_tiles * nch;  // chunks this block processes
+  constexpr uint32_t TB_BYTES = 4u * (uint32_t)L::TB_WORDS;
+
+  if (warp == TC_CW) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(tmem_slot)),
+                 "r"(TC_TMEM_ALLOC)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  if (tid == 0) {
+    for (int i = 0; i < 16; ++i) {
+      const bool by_threads = i == B_SFREE || i == B_SFREE + 1 || i == B_VFULL || i == B_VFULL + 1 || i == B_UFULL ||
+                              i == B_YFREE || i == B_YFREE + 1;
+      mbar_init_n(&bar[i], by_threads ? TC_COMPUTE : 1);
+    }
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+  bool ok = true;
+
+  if (warp == TC_CW) {
+    // ------------------------------------------------------------------ MMA / copy issuer
+    if (lane == 0) {
+      constexpr uint32_t ID1 = IDescTF32<TC_M, 16 * D>::value;
+      constexpr uint32_t ID2 = IDescTF32<TC_M, NP>::value;
+      constexpr uint32_t SBO1 = (KP / 4) * 128;
+      const uint64_t du_hi = sdesc(su32(u_hi), 128, SBO1), du_lo = sdesc(su32(u_lo), 128, SBO1);
+      uint32_t filled[2] = {0u, 0u}, consumed[2] = {0u, 0u};   // table fills per buffer
+      bool issued_any = false;
+      for (int f = 0; f < TBUF && f < G; ++f) {
+        bulk_load(tb + f * L::TB_WORDS, tabs + (size_t)(f % nch) * L::TB_WORDS, TB_BYTES, &bar[B_TAB + f]);
+        filled[f]++;
+      }
+      int64_t g = 0;
+      for (int64_t t = 0; t < my_tiles && ok; ++t) {
+        const int yb = (int)(t & 1);
+        for (int c = 0; c < nch && ok; ++c, ++g) {
+          const int tbi = TBUF == 2 ? (int)(g & 1) : 0;
+          const int sb = (int)(g & 1), vb = VBUF == 2 ? (int)(g & 1) : 0;
+          const uint32_t sk = (uint32_t)(g >> 1), vk = (uint32_t)(VBUF == 2 ? (g >> 1) : g);
+          if (TBUF == 1 && g >= 1) {   // single table buffer: refill it once the previous chunk is done
+            const uint32_t pk = (uint32_t)(VBUF == 2 ? ((g - 1) >> 1) : (g - 1));
+            if (!mbar_wait_abortable(&bar[B_VFREE + (VBUF == 2 ? (int)((g - 1) & 1) : 0)], pk & 1u, abort_flag)) {
+              ok = false;
+              break;
+            }
+            bulk_load(tb, tabs + (size_t)(g % nch) * L::TB_WORDS, TB_BYTES, &bar[B_TAB]);
+            filled[0]++;
+          }
+          if (!mbar_wait_abortable(&bar[B_TAB + tbi], consumed[tbi] & 1u, abort_flag)) { ok = false; break; }
+          consumed[tbi]++;
+          if (c == 0 && !mbar_wait_abortable(&bar[B_UFULL], (uint32_t)(t & 1), abort_flag)) { ok = false; break; }
+          if (g >= 2 && !mbar_wait_abortable(&bar[B_SFREE + sb], (sk - 1) & 1u, abort_flag)) { ok = false; break; }
+          tc_fence_after();
+          // GEMM1: S [128 x 16 D] = U [128 x KP] * GT^T (all directions in one N = 16 D product)
+          const uint32_t tbs = su32(tb + tbi * L::TB_WORDS);
+          const uint64_t dg_hi = sdesc(tbs, 128, SBO1), dg_lo = sdesc(tbs + 4u * D * TC_QC * KP, 128, SBO1);
+          const uint32_t dcol = tmem + TC_SCOL * sb;
+#pragma unroll
+          for (int ks = 0; ks < KP / 8; ++ks) {
+            const uint64_t o = (uint64_t)(ks * 256) >> 4;
+            mma_tf32(dcol, du_hi + o, dg_hi + o, ID1, ks > 0);
+            mma_tf32(dcol, du_hi + o, dg_lo + o, ID1, 1);
+            mma_tf32(dcol, du_lo + o, dg_hi + o, ID1, 1);
+          }
+          mma_commit(&bar[B_SFULL + sb]);
+          issued_any = true;
+          // double table buffer: refill the other buffer (used by chunk g-1) with chunk g+1
+          if (TBUF == 2 && g >= 1 && g + 1 < G) {
+            const uint32_t pk = (uint32_t)(VBUF == 2 ? ((g - 1) >> 1) : (g - 1));
+            if (!mbar_wait_abortable(&bar[B_VFREE + (VBUF == 2 ? (int)((g - 1) & 1) : 0)], pk & 1u, abort_flag)) {
+              ok = false;
+              break;
+            }
+            const int ob = (int)((g + 1) & 1);
+            bulk_load(tb + ob * L::TB_WORDS, tabs + (size_t)((g + 1) % nch) * L::TB_WORDS, TB_BYTES, &bar[B_TAB + ob]);
+            filled[ob]++;
+          }
+          // GEMM2: Y [128 x NP] += V_d [128 x 16] * G_d [16 x NP]
+          if (!mbar_wait_abortable(&bar[B_VFULL + vb], vk & 1u, abort_flag)) { ok = false; break; }
+          if (c == 0 && t >= 2 &&
+              !mbar_wait_abortable(&bar[B_YFREE + yb], (uint32_t)(((t >> 1) - 1) & 1), abort_flag)) {
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          const uint32_t vs = su32(vbase + vb * 2 * L::V_WORDS);
+          const uint32_t gs = tbs + 4u * 2 * D * TC_QC * KP;
+          const uint64_t dv_hi = sdesc(vs, 128, 512), dv_lo = sdesc(vs + 4u * L::V_WORDS, 128, 512);
+          const uint64_t dG_hi = sdesc(gs, 128, 512), dG_lo = sdesc(gs + 4u * D * NP * TC_QC, 128, 512);
+          const uint32_t ycol = tmem + TC_YCOL0 + 128u * yb;
+#pragma unroll
+          for (int d = 0; d < D; ++d) {
+#pragma unroll
+            for (int ks = 0; ks < TC_QC / 8; ++ks) {
+              const uint64_t oa = (uint64_t)(d * TC_M * TC_QC * 4 + ks * 256) >> 4;
+              const uint64_t ob = (uint64_t)(d * NP * TC_QC * 4 + ks * 256) >> 4;
+              mma_tf32(ycol, dv_hi + oa, dG_hi + ob, ID2, (c > 0 || d > 0 || ks > 0) ? 1u : 0u);
+              mma_tf32(ycol, dv_hi + oa, dG_lo + ob, ID2, 1);
+              mma_tf32(ycol, dv_lo + oa, dG_hi + ob, ID2, 1);
+            }
+          }
+          mma_commit(&bar[B_VFREE + vb]);
+          if (c == nch - 1) mma_commit(&bar[B_YFULL + yb]);
+        }
+      }
+      if (!ok) {
+        *abort_flag = 1;
+        atomicExch(err, (int)CEED_ERR_TIMEOUT);
+        // let this block's own operations in flight finish before TMEM and shared memory are released
+        if (issued_any) {
+          mma_commit(&bar[B_DRAIN]);
+          mbar_wait_bounded(&bar[B_DRAIN], 0u);
+        }
+        for (int bb = 0; bb < 2; ++bb)
+          if (filled[bb] > consumed[bb]) mbar_wait_bounded(&bar[B_TAB + bb], consumed[bb] & 1u);
+      }
+    }
+    __syncwarp();
+  } else {
+    // ------------------------------------------------------------------ compute warps
+    const int quad = warp & 3, grp = warp >> 2;
+    const int m = quad * 32 + lane;
+    const uint32_t lane_base = (uint32_t)(quad * 32) << 16;
+    float qnext[TC_PPT][D == 3 ? 6 : 1];
+    if (my_tiles > 0) {
+      const int64_t e0 = (int64_t)blockIdx.x * TC_M + m;
+      load_qdata<D>(qd, E, Q, e0, e0 < E, 0, grp, qnext);
+      gather_tile<KP>(E, P, e0, e0 < E, grp, m, masked, rmap, x, u_hi, u_lo);
+      fence_proxy_async();
+      mbar_arrive(&bar[B_UFULL]);
+    }
+    int64_t g = 0;
+    for (int64_t t = 0; t < my_tiles && ok; ++t) {
+      const int64_t tile = (int64_t)blockIdx.x + t * gridDim.x;
+      const int64_t e = tile * TC_M + m;
+      const bool valid = e < E;
+      const int yb = (int)(t & 1);
+      for (int c = 0; c < nch; ++c, ++g) {
+        const int sb = (int)(g & 1), vb = VBUF == 2 ? (int)(g & 1) : 0;
+        const uint32_t sk = (uint32_t)(g >> 1), vk = (uint32_t)(VBUF == 2 ? (g >> 1) : g);
+        if (!mbar_wait_abortable(&bar[B_SFULL + sb], sk & 1u, abort_flag)) { ok = false; break; }
+        tc_fence_after();
+        float s[D][TC_PPT];
+#pragma unroll
+        for (int d = 0; d < D; ++d) tmem_ld4(tmem + lane_base + TC_SCOL * sb + 16u * d + TC_PPT * grp, s[d]);
+        tc_fence_before();
+        mbar_arrive(&bar[B_SFREE + sb]);
+        float qv[TC_PPT][D == 3 ? 6 : 1];
+#pragma unroll
+        for (int j = 0; j < TC_PPT; ++j)
+#pragma unroll
+          for (int k = 0; k < (D == 3 ? 6 : 1); ++k) qv[j][k] = qnext[j][k];
+        if (c + 1 < nch) {
+          load_qdata<D>(qd, E, Q, e, valid, c + 1, grp, qnext);
+        } else if (t + 1 < my_tiles) {
+          const int64_t e1 = (tile + gridDim.x) * TC_M + m;
+          load_qdata<D>(qd, E, Q, e1, e1 < E, 0, grp, qnext);
+        }
+#pragma unroll
+        for (int j = 0; j < TC_PPT; ++j) {
+          if (D == 3) {
+            const float g0 = s[0][j], g1 = s[1][j], g2 = s[2][j];
+            s[0][j] = qv[j][0] * g0 + qv[j][1] * g1 + qv[j][2] * g2;
+            s[1][j] = qv[j][1] * g0 + qv[j][3] * g1 + qv[j][4] * g2;
+            s[2][j] = qv[j][2] * g0 + qv[j][4] * g1 + qv[j][5] * g2;
+          } else {
+            s[0][j] *= qv[j][0];
+          }
+        }
+        // V buffer vb is free once the product of chunk g - VBUF that read it has completed
+        if (g >= VBUF && !mbar_wait_abortable(&bar[B_VFREE + vb], (vk - 1) & 1u, abort_flag)) {
+          ok = false;
+          break;
+        }
+        float *v_hi = vbase + vb * 2 * L::V_WORDS, *v_lo = v_hi + L::V_WORDS;
+#pragma unroll
+        for (int d = 0; d < D; ++d) {
+          float h4[4], l4[4];
+#pragma unroll
+          for (int j = 0; j < 4; ++j) split_tf32(s[d][j], h4[j], l4[j]);
+          const int o = d * TC_M * TC_QC + canon(m, TC_PPT * grp, TC_QC);
+          st_shared4(v_hi + o, h4[0], h4[1], h4[2], h4[3]);
+          st_shared4(v_lo + o, l4[0], l4[1], l4[2], l4[3]);
+        }
+        fence_proxy_async();
+        mbar_arrive(&bar[B_VFULL + vb]);
+        if (c == nch - 1 && t + 1 < my_tiles) {
+          // the next tile's inputs: U is free (this chunk's S landed, so every product reading U is done)
+          const int64_t e1 = (tile + gridDim.x) * TC_M + m;
+          gather_tile<KP>(E, P, e1, e1 < E, grp, m, masked, rmap, x, u_hi, u_lo);
+          fence_proxy_async();
+          mbar_arrive(&bar[B_UFULL]);
+        }
+      }
+      if (!ok) break;
+      // epilogue of tile t: this thread's quarter of the element's output nodes, TMEM -> element vectors
+      if (!mbar_wait_abortable(&bar[B_YFULL + yb], (uint32_t)((t >> 1) & 1), abort_flag)) { ok = false; break; }
+      tc_fence_after();
+#pragma unroll
+      for (int j0 = 0; j0 < NP / TC_GROUPS; j0 += 4) {
+        const int n0 = grp * (NP / TC_GROUPS) + j0;
+        float y4[4];
+        tmem_ld4(tmem + lane_base + TC_YCOL0 + 128u * yb + (uint32_t)n0, y4);
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+          if (valid && n0 + j < P) Ye[(int64_t)(n0 + j) * E + e] = y4[j];
+      }
+      tc_fence_before();
+      mbar_arrive(&bar[B_YFREE + yb]);
+    }
+    if (!ok) {
+      *abort_flag = 1;
+      atomicExch(err, (int)CEED_ERR_TIMEOUT);
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == TC_CW) {
+    __syncwarp();
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TC_TMEM_ALLOC) : "memory");
+  }
+}
+
+// Host: chunked, split, padded tables of one operator (D = 1 interp, 3 grad) in the shared-memory
+// image order of the kernel.
+static void build_tables(const std::vector<double> &tab, int D, int P, int Q, int KP, int NP, int nch,
+                         std::vector<float> &out) {
+  const int W = chunk_words(D, KP, NP);
+  out.assign((size_t)W * nch, 0.f);
+  auto split = [](double v, float &hi, float &lo) {
+    const float f = (float)v;
+    uint32_t u;
+    std::memcpy(&u, &f, 4);
+    // round to nearest, ties away from zero, keeping 10 mantissa bits (the cvt.rna.tf32 rounding)
+    u = (u + 0x1000u) & 0xFFFFE000u;
+    std::memcpy(&hi, &u, 4);
+    lo = (float)(v - (double)hi);
+  };
+  for (int c = 0; c < nch; ++c) {
+    float *o = out.data() + (size_t)c * W;
+    float *gt_hi = o, *gt_lo = o + D * TC_QC * KP;
+    float *g_hi = o + 2 * D * TC_QC * KP, *g_lo = g_hi + D * NP * TC_QC;
+    for (int d = 0; d < D; ++d)
+      for (int r = 0; r < TC_QC; ++r) {
+        const int q = c * TC_QC + r;
+        if (q >= Q) continue;
+        for (int n = 0; n < P; ++n) {
+          float hi, lo;
+          split(tab[((size_t)d * Q + q) * P + n], hi, lo);
+          gt_hi[d * TC_QC * KP + canon(r, n, KP)] = hi;   // GEMM1 B: row = point, K = node
+          gt_lo[d * TC_QC * KP + canon(r, n, KP)] = lo;
+          g_hi[d * NP * TC_QC + canon(n, r, TC_QC)] = hi;  // GEMM2 B: row = node, K = point
+          g_lo[d * NP * TC_QC + canon(n, r, TC_QC)] = lo;
+        }
+      }
+  }
+}
+
+template <int D, int KP, int NP, int TBUF, int VBUF>
+static int launch_tc(ceed_nt_t h, const float *tabs, const float *qd, const double *x, float *Ye, int masked,
+                     cudaStream_t s) {
+  using L = TcLayout<D, KP, NP, TBUF, VBUF>;
+  // one block per SM: the block holds 512 TMEM columns (S and Y double-buffered)
+  constexpr size_t SMEM = L::BYTES > 116 * 1024 ? L::BYTES : 116 * 1024;
+  static uint64_t attr_set = 0;
+  const uint64_t bit = 1ull << (h->device & 63);
+  if (!(attr_set & bit)) {
+    CEED_CUDA_CHECK(cudaFuncSetAttribute(nt_tc_kernel<D, KP, NP, TBUF, VBUF>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM));
+    attr_set |= bit;
+  }
+  static int nsm[64] = {0};
+  int &sms = nsm[h->device & 63];
+  if (sms == 0) CEED_CUDA_CHECK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device));
+  const int64_t ntiles = (h->E + TC_M - 1) / TC_M;
+  const unsigned grid = (unsigned)std::min<int64_t>(ntiles, (int64_t)sms);
+  nt_tc_kernel<D, KP, NP, TBUF, VBUF><<<grid, TC_BLOCK, SMEM, s>>>(h->E, h->P, h->Q, h->tc_nchunk, h->d_rmap, x, tabs,
+                                                                  qd, Ye, masked, h->d_err);
+  CEED_CUDA_CHECK(cudaGetLastError());
+  return CEED_OK;
+}
+
+// Buffering that fits in shared memory: V double if possible, then the tables double if possible.
+template <int D, int KP, int NP>
+struct TcBufs {
+  static constexpr size_t lim = 227 * 1024;
+  static constexpr size_t base = 8ull * TC_M * KP + 16 * 8 + 16;
+  static constexpr size_t tbw = 4ull * chunk_words(D, KP, NP), vw = 8ull * D * TC_M * TC_QC;
+  static constexpr int VBUF = base + tbw + 2 * vw <= lim ? 2 : 1;
+  static constexpr int TBUF = base + 2 * tbw + VBUF * vw <= lim ? 2 : 1;
+};
+
+template <int PP>
+static int dispatch_p(ceed_nt_t h, int op, const float *qd, const double *x, float *Ye, int masked, cudaStream_t s) {
+  constexpr int KP = kpad(PP), NP = npad(PP);
+  const float *tabs = h->d_tc_tab[op == CEED_OP_MASS ? 0 : 1];
+  using B1 = TcBufs<1, KP, NP>;
+  using B3 = TcBufs<3, KP, NP>;
+  return op == CEED_OP_MASS ? launch_tc<1, KP, NP, B1::TBUF, B1::VBUF>(h, tabs, qd, x, Ye, masked, s)
+                            : launch_tc<3, KP, NP, B3::TBUF, B3::VBUF>(h, tabs, qd, x, Ye, masked, s);
+}
+
+}  // namespace
+
+// The kernel is instantiated for the node counts of the degree-1..6 tetrahedra (P = 4, 10, 20, 35,
+// 56, 84); other bases run on the CUDA-core algorithms.
+bool nt_tc_supported(int P) { return P == 4 || P == 10 || P == 20 || P == 35 || P == 56 || P == 84; }
+
+int nt_tc_prepare(ceed_nt_t h) {
+  if (h->d_tc_tab[0]) return CEED_OK;
+  if (!nt_tc_supported(h->P)) return fail(CEED_ERR_UNSUPPORTED, "tensor-core operator: P must be 4, 10, 20, 35, 56 or 84");
+  const int P = h->P, Q = h->Q, KP = kpad(P), NP = npad(P);
+  const int nch = (Q + TC_QC - 1) / TC_QC;
+  std::vector<double> tab;
+  try {
+    tab.resize((size_t)4 * Q * P);
+  } catch (...) {
+    return fail(CEED_ERR_OOM, "host allocation");
+  }
+  CEED_CUDA_CHECK(cudaMemcpy(tab.data(), h->d_tab64, tab.size() * 8, cudaMemcpyDeviceToHost));
+  for (int op = 0; op < 2; ++op) {
+    const int D = op == 0 ? 1 : 3;
+    std::vector<double> t(tab.begin() + (op == 0 ? 0 : (size_t)Q * P), tab.begin() + (op == 0 ? (size_t)Q * P : tab.size()));
+    std::vector<float> img;
+    build_tables(t, D, P, Q, KP, NP, nch, img);
+    float *d = nullptr;
+    CEED_CUDA_CHECK(cudaMalloc(&d, img.size() * 4));
+    h->d_tc_tab[op] = d;
+    CEED_CUDA_CHECK(cudaMemcpy(d, img.data(), img.size() * 4, cudaMemcpyHostToDevice));
+  }
+  h->tc_nchunk = nch;
+  return CEED_OK;
+}
+
+int nt_tc_apply(ceed_nt_t h, int op, const float *qd, const double *x, float *Ye, int masked, cudaStream_t s) {
+  switch (h->P) {
+    case 4: return dispatch_p<4>(h, op, qd, x, Ye, masked, s);
+    case 10: return dispatch_p<10>(h, op, qd, x, Ye, masked, s);
+    case 20: return dispatch_p<20>(h, op, qd, x, Ye, masked, s);
+    case 35: return dispatch_p<35>(h, op, qd, x, Ye, masked, s);
+    case 56: return dispatch_p<56>(h, op, qd, x, Ye, masked, s);
+    case 84: return dispatch_p<84>(h, op, qd, x, Ye, masked, s);
+    default: return fail(CEED_ERR_UNSUPPORTED, "tensor-core operator: unsupported P");
+  }
+}
+
+}  // namespace ceedgb

@@ -118,6 +118,31 @@ def test_fused_fp32_matches_oracle(ceed, op):
     nt.close()
 
 
+@pytest.mark.parametrize("p,op", CASES)
+def test_tensor_core_matches_oracle(ceed, p, op):
+    # tcgen05 kernel, 3xTF32: 360 elements = two full tiles of 128 and a ragged tile of 104 (p <= 4)
+    m = synthetic.TetMesh(5, 4, 3, p, seed=30 + p) if p <= 4 else synthetic.TetMesh(4, 3, 2, p, seed=30 + p)
+    q = p + 1
+    nt = _setup(ceed, m, q)
+    cop = ceed.CEED_OP_DIFFUSION if op == "diffusion" else ceed.CEED_OP_MASS
+    qd = _qdata(ceed, nt, op, ceed.CEED_F32)
+    ceed.ceed_nt_set_algorithm(nt, cop, ceed.CEED_F32, ceed.CEED_NT_TC)
+    x = synthetic.uniform(m.n_ldof, seed=40 + p)
+    ref = _oracle(m, q, op, x)
+    for flags in (0, ceed.CEED_APPLY_DIRICHLET):
+        y = _apply(ceed, nt, op, qd, ceed.CEED_F32, x, flags=flags)
+        ceed.ceed_nt_status(nt)
+        r = ref if flags == 0 else _oracle(m, q, op, x, mask=m.boundary)
+        assert rel_err(y, r) <= 2e-5, (flags, rel_err(y, r))
+    # the same arithmetic on the CUDA cores agrees to FP32 rounding
+    ceed.ceed_nt_set_algorithm(nt, cop, ceed.CEED_F32, ceed.CEED_NT_FUSED)
+    y2 = _apply(ceed, nt, op, qd, ceed.CEED_F32, x)
+    ceed.ceed_nt_set_algorithm(nt, cop, ceed.CEED_F32, ceed.CEED_NT_TC)
+    y1 = _apply(ceed, nt, op, qd, ceed.CEED_F32, x)
+    assert rel_err(y1, y2) <= 2e-5
+    nt.close()
+
+
 @pytest.mark.parametrize("algo", ["fused", "gemm"])
 def test_dirichlet_masked_and_per_point_coefficient(ceed, algo):
     p, q = 2, 3
@@ -189,6 +214,8 @@ def test_invalid_arguments(ceed):
     assert ei.value.status == ceed.CEED_ERR_BAD_GEOMETRY
     with pytest.raises(ceed.CeedError):
         ceed.ceed_nt_set_algorithm(nt, ceed.CEED_OP_MASS, ceed.CEED_F64, ceed.CEED_NT_GEMM, 0, 2)  # TF32 needs F32
+    with pytest.raises(ceed.CeedError):
+        ceed.ceed_nt_set_algorithm(nt, ceed.CEED_OP_MASS, ceed.CEED_F64, ceed.CEED_NT_TC)  # tensor cores: F32
     nt.close()
 
 
@@ -205,7 +232,7 @@ def _sampled_oracle(m, q, x, nodes):
 
 
 @pytest.mark.parametrize("algo,prec,mode,tol", [("fused", "f64", 0, 1e-12), ("gemm", "f64", 1, 1e-12),
-                                                ("fused", "f32", 0, 2e-5)])
+                                                ("fused", "f32", 0, 2e-5), ("tc", "f32", 0, 2e-5)])
 def test_full_size_sampled(ceed, algo, prec, mode, tol):
     # the benchmark's tetrahedral workload (48^3 cubes x 6 = 663,552 degree-4 elements, 7.1M nodes),
     # compared with the oracle on 400 sampled nodes
@@ -216,8 +243,11 @@ def test_full_size_sampled(ceed, algo, prec, mode, tol):
     qd = _qdata(ceed, nt, "diffusion", cprec)
     if algo == "gemm":
         ceed.ceed_nt_set_algorithm(nt, ceed.CEED_OP_DIFFUSION, cprec, ceed.CEED_NT_GEMM, 0, mode)
+    elif algo == "tc":
+        ceed.ceed_nt_set_algorithm(nt, ceed.CEED_OP_DIFFUSION, cprec, ceed.CEED_NT_TC)
     x = synthetic.uniform(m.n_ldof, seed=1)
     y = _apply(ceed, nt, "diffusion", qd, cprec, x)
+    ceed.ceed_nt_status(nt)
     nodes = np.random.default_rng(0).choice(m.n_ldof, 400, replace=False)
     ref = _sampled_oracle(m, q, x, nodes)
     assert rel_err(y[nodes], ref) <= tol
