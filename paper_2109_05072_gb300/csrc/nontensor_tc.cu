@@ -136,34 +136,39 @@ __device__ __forceinline__ void st_shared4(float *p, float a, float b, float c, 
   asm volatile("st.shared.v4.f32 [%0], {%1, %2, %3, %4};" ::"r"(su32(p)), "f"(a), "f"(b), "f"(c), "f"(d) : "memory");
 }
 
-// Shared-memory map of one block.  U: the tile's element inputs (hi, lo); TB[TBUF]: table chunks;
-// V[VBUF]: the pointwise results (hi, lo); then the mbarriers, the TMEM address and an abort flag.
-template <int D, int KP, int NP, int TBUF, int VBUF>
-struct TcLayout {
-  static constexpr int U_WORDS = TC_M * KP;                // per hi/lo
-  static constexpr int TB_WORDS = chunk_words(D, KP, NP);  // one table buffer
-  static constexpr int V_WORDS = D * TC_M * TC_QC;         // per hi/lo
-  static constexpr size_t U_HI = 0;
-  static constexpr size_t U_LO = U_HI + 4 * (size_t)U_WORDS;
-  static constexpr size_t TB = U_LO + 4 * (size_t)U_WORDS;
-  static constexpr size_t V = TB + 4 * (size_t)TB_WORDS * TBUF;   // buffer v: hi at V + 8 V_WORDS v, lo + 4 V_WORDS
-  static constexpr size_t BARS = V + 8 * (size_t)V_WORDS * VBUF;
-  static constexpr size_t BYTES = BARS + 16 * 8 + 16;
-  static_assert(BYTES <= 227 * 1024, "shared memory");
-};
-
 // mbarrier slots
 enum : int { B_TAB = 0, B_SFULL = 2, B_SFREE = 4, B_VFULL = 6, B_VFREE = 8, B_UFULL = 10, B_YFULL = 11, B_YFREE = 13,
-             B_DRAIN = 15 };
-constexpr int TC_CW = 16;                       // compute warps (0-15); warp 16 issues the MMAs
+             B_TBFREE = 15, B_DRAIN1 = 17, B_DRAIN2 = 18 };
+constexpr int TC_NBAR = 20;
+constexpr int TC_CW = 16;                       // compute warps (0-15); warps 16, 17 issue the MMAs
 constexpr int TC_COMPUTE = 32 * TC_CW;
-constexpr int TC_BLOCK = TC_COMPUTE + 32;
+constexpr int TC_BLOCK = TC_COMPUTE + 64;
 constexpr int TC_GROUPS = TC_CW / 4;            // warps per TMEM lane quadrant
 constexpr int TC_PPT = TC_QC / TC_GROUPS;       // points of a chunk per compute thread
 static_assert(TC_PPT == 4, "one float4 of points per thread and direction");
 constexpr uint32_t TC_TMEM_ALLOC = 512;
 constexpr uint32_t TC_SCOL = 64;                // S buffer s at TMEM column 64 s
 constexpr uint32_t TC_YCOL0 = 256;              // Y buffer y at TMEM column 256 + 128 y
+
+// Shared-memory map of one block.  U: the tile's element inputs (hi, lo); TB[TBUF]: table chunks;
+// V[VBUF]: the pointwise results (hi, lo); QS: each compute thread's prefetch slots for its
+// quadrature data of the next chunk ([value][thread], when QPRE); then the mbarriers, the TMEM
+// address and an abort flag.
+template <int D, int KP, int NP, int TBUF, int VBUF, int QPRE>
+struct TcLayout {
+  static constexpr int U_WORDS = TC_M * KP;                // per hi/lo
+  static constexpr int TB_WORDS = chunk_words(D, KP, NP);  // one table buffer
+  static constexpr int V_WORDS = D * TC_M * TC_QC;         // per hi/lo
+  static constexpr int QS_WORDS = QPRE * TC_PPT * (D == 3 ? 6 : 1) * TC_COMPUTE;
+  static constexpr size_t U_HI = 0;
+  static constexpr size_t U_LO = U_HI + 4 * (size_t)U_WORDS;
+  static constexpr size_t TB = U_LO + 4 * (size_t)U_WORDS;
+  static constexpr size_t V = TB + 4 * (size_t)TB_WORDS * TBUF;   // buffer v: hi at V + 8 V_WORDS v, lo + 4 V_WORDS
+  static constexpr size_t QS = V + 8 * (size_t)V_WORDS * VBUF;
+  static constexpr size_t BARS = QS + 4 * (size_t)QS_WORDS;
+  static constexpr size_t BYTES = BARS + TC_NBAR * 8 + 16;
+  static_assert(BYTES <= 227 * 1024, "shared memory");
+};
 
 __device__ __forceinline__ void mbar_init_n(uint64_t *bar, uint32_t n) {
   asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(bar)), "r"(n) : "memory");
@@ -190,10 +195,16 @@ __device__ __forceinline__ bool mbar_wait_abortable(uint64_t *bar, uint32_t pari
   return false;
 }
 
+__device__ __forceinline__ void cp_async4(float *dst, const float *src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(su32(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+
 // The tile's element inputs, split into TF32 hi/lo, written to the canonical layout (row m,
-// columns 4 k4 .. 4 k4 + 3 for this thread's share k4 = grp, grp + 4, ... of the column groups).  Loads go out in rounds
-// of up to two column groups (restriction entries first, then the L-vector values) so their
-// latencies overlap; the FP64 -> FP32 conversion uses integer instructions only.
+// columns 4 k4 .. 4 k4 + 3 for this thread's share k4 = grp, grp + 4, ... of the column groups).
+// Loads go out in rounds of up to two column groups (restriction entries first, then the L-vector
+// values) so their latencies overlap; the FP64 -> FP32 conversion uses integer instructions only.
 template <int KP>
 __device__ __forceinline__ void gather_tile(int64_t E, int P, int64_t e, bool valid, int grp, int m, int masked,
                                             const uint32_t *__restrict__ rmap, const double *__restrict__ x,
@@ -233,7 +244,9 @@ __device__ __forceinline__ void gather_tile(int64_t E, int P, int64_t e, bool va
   }
 }
 
-// Quadrature data of one thread's TC_PPT points of chunk c of a tile (zero outside the mesh / rule).
+// Quadrature data of one thread's TC_PPT points of chunk c of a tile: into registers (qv) or, as
+// asynchronous copies, into the thread's prefetch slots (qs + k * TC_COMPUTE, value k); entries
+// outside the mesh or the rule are zero.
 template <int D>
 __device__ __forceinline__ void load_qdata(const float *__restrict__ qd, int64_t E, int Q, int64_t e, bool valid,
                                            int c, int grp, float (&qv)[TC_PPT][D == 3 ? 6 : 1]) {
@@ -247,29 +260,52 @@ __device__ __forceinline__ void load_qdata(const float *__restrict__ qd, int64_t
     for (int k = 0; k < (D == 3 ? 6 : 1); ++k) qv[j][k] = in ? __ldg(base + k * cs + (int64_t)j * E) : 0.f;
   }
 }
+template <int D>
+__device__ __forceinline__ void prefetch_qdata(const float *__restrict__ qd, int64_t E, int Q, int64_t e, bool valid,
+                                               int c, int grp, float *qs) {
+  const int64_t cs = (int64_t)Q * E;
+  const int q0 = c * TC_QC + TC_PPT * grp;
+  const float *base = qd + (int64_t)q0 * E + e;
+#pragma unroll
+  for (int j = 0; j < TC_PPT; ++j) {
+    const bool in = valid && q0 + j < Q;
+#pragma unroll
+    for (int k = 0; k < (D == 3 ? 6 : 1); ++k) {
+      float *dst = qs + (j * (D == 3 ? 6 : 1) + k) * TC_COMPUTE;
+      if (in) cp_async4(dst, base + k * cs + (int64_t)j * E);
+      else *dst = 0.f;
+    }
+  }
+  cp_async_commit();
+}
 
-// The fused kernel, persistent (block b takes tiles b, b + gridDim.x, ...) and warp-specialized:
-// warp 16 (one thread) streams the table chunks in with bulk copies and issues every matrix
-// product; warps 0-15 gather inputs, apply the pointwise operator and write the element vectors.
+// The fused kernel, persistent (block b takes tiles b, b + gridDim.x, ...) and warp-specialized.
+//   warp 16 (one thread): streams the table chunks in with bulk copies, issues GEMM1 of every chunk
+//   warp 17 (one thread): issues GEMM2 of every chunk
+//   warps 0-15: gather inputs, apply the pointwise operator, write the element vectors
 // They hand buffers to each other through mbarriers (the tensor core signals completion through
-// tcgen05.commit), with S (TMEM), V (shared memory, when it fits) and Y (TMEM) double-buffered so
-// the tensor core works on chunk g+1 while the CUDA cores process chunk g.  Warp w < 16 serves TMEM
-// lane quadrant w % 4 (elements 32 (w % 4) ... of the tile) and group grp = w / 4: points
-// 4 grp .. 4 grp + 3 of each chunk, every fourth input column group and a quarter of the output nodes.
-template <int D, int KP, int NP, int TBUF, int VBUF>
+// tcgen05.commit).  S (TMEM) and Y (TMEM) are double-buffered, V and the tables when shared memory
+// allows, so the tensor core works on one chunk while the CUDA cores process another.  Warp w < 16
+// serves TMEM lane quadrant w % 4 (elements 32 (w % 4) ... of the tile) and group grp = w / 4:
+// points 4 grp .. 4 grp + 3 of each chunk, every fourth input column group and a quarter of the
+// output nodes.  With QPRE, every compute thread copies its quadrature data for the next chunk into
+// its own shared-memory slots with cp.async while it works on the current one.
+template <int D, int KP, int NP, int TBUF, int VBUF, int QPRE>
 __global__ void __launch_bounds__(TC_BLOCK, 1)
     nt_tc_kernel(int64_t E, int P, int Q, int nch, const uint32_t *__restrict__ rmap, const double *__restrict__ x,
                  const float *__restrict__ tabs, const float *__restrict__ qd, float *__restrict__ Ye, int masked,
                  int *err) {
-  using L = TcLayout<D, KP, NP, TBUF, VBUF>;
+  using L = TcLayout<D, KP, NP, TBUF, VBUF, QPRE>;
+  constexpr int NQ = D == 3 ? 6 : 1;
   extern __shared__ __align__(1024) unsigned char tc_smem[];
   float *u_hi = reinterpret_cast<float *>(tc_smem + L::U_HI);
   float *u_lo = reinterpret_cast<float *>(tc_smem + L::U_LO);
   float *tb = reinterpret_cast<float *>(tc_smem + L::TB);
   float *vbase = reinterpret_cast<float *>(tc_smem + L::V);
+  float *qslots = reinterpret_cast<float *>(tc_smem + L::QS);
   uint64_t *bar = reinterpret_cast<uint64_t *>(tc_smem + L::BARS);
-  uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(tc_smem + L::BARS + 128);
-  volatile int *abort_flag = reinterpret_cast<volatile int *>(tc_smem + L::BARS + 132);
+  uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(tc_smem + L::BARS + TC_NBAR * 8);
+  volatile int *abort_flag = reinterpret_cast<volatile int *>(tc_smem + L::BARS + TC_NBAR * 8 + 4);
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int64_t ntiles = (E + TC_M - 1) / TC_M;
@@ -284,7 +320,7 @@ __global__ void __launch_bounds__(TC_BLOCK, 1)
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
   if (tid == 0) {
-    for (int i = 0; i < 16; ++i) {
+    for (int i = 0; i < TC_NBAR; ++i) {
       const bool by_threads = i == B_SFREE || i == B_SFREE + 1 || i == B_VFULL || i == B_VFULL + 1 || i == B_UFULL ||
                               i == B_YFREE || i == B_YFREE + 1;
       mbar_init_n(&bar[i], by_threads ? TC_COMPUTE : 1);
@@ -299,13 +335,12 @@ __global__ void __launch_bounds__(TC_BLOCK, 1)
   bool ok = true;
 
   if (warp == TC_CW) {
-    // ------------------------------------------------------------------ MMA / copy issuer
+    // ------------------------------------------------------------------ tables + GEMM1 issuer
     if (lane == 0) {
       constexpr uint32_t ID1 = IDescTF32<TC_M, 16 * D>::value;
-      constexpr uint32_t ID2 = IDescTF32<TC_M, NP>::value;
       constexpr uint32_t SBO1 = (KP / 4) * 128;
       const uint64_t du_hi = sdesc(su32(u_hi), 128, SBO1), du_lo = sdesc(su32(u_lo), 128, SBO1);
-      uint32_t filled[2] = {0u, 0u}, consumed[2] = {0u, 0u};   // table fills per buffer
+      uint32_t filled[3] = {0u, 0u, 0u}, consumed[3] = {0u, 0u, 0u};   // table fills per buffer
       bool issued_any = false;
       for (int f = 0; f < TBUF && f < G; ++f) {
         bulk_load(tb + f * L::TB_WORDS, tabs + (size_t)(f % nch) * L::TB_WORDS, TB_BYTES, &bar[B_TAB + f]);
@@ -313,19 +348,17 @@ __global__ void __launch_bounds__(TC_BLOCK, 1)
       }
       int64_t g = 0;
       for (int64_t t = 0; t < my_tiles && ok; ++t) {
-        const int yb = (int)(t & 1);
         for (int c = 0; c < nch && ok; ++c, ++g) {
-          const int tbi = TBUF == 2 ? (int)(g & 1) : 0;
-          const int sb = (int)(g & 1), vb = VBUF == 2 ? (int)(g & 1) : 0;
-          const uint32_t sk = (uint32_t)(g >> 1), vk = (uint32_t)(VBUF == 2 ? (g >> 1) : g);
-          if (TBUF == 1 && g >= 1) {   // single table buffer: refill it once the previous chunk is done
-            const uint32_t pk = (uint32_t)(VBUF == 2 ? ((g - 1) >> 1) : (g - 1));
-            if (!mbar_wait_abortable(&bar[B_VFREE + (VBUF == 2 ? (int)((g - 1) & 1) : 0)], pk & 1u, abort_flag)) {
+          const int tbi = (int)(g % TBUF), sb = (int)(g & 1);
+          const uint32_t sk = (uint32_t)(g >> 1);
+          if (g >= TBUF) {
+            // refill buffer tbi with chunk g once the GEMM2 that last read it (chunk g - TBUF) is done
+            if (!mbar_wait_abortable(&bar[B_TBFREE + tbi], (consumed[tbi] - 1) & 1u, abort_flag)) {
               ok = false;
               break;
             }
-            bulk_load(tb, tabs + (size_t)(g % nch) * L::TB_WORDS, TB_BYTES, &bar[B_TAB]);
-            filled[0]++;
+            bulk_load(tb + tbi * L::TB_WORDS, tabs + (size_t)(g % nch) * L::TB_WORDS, TB_BYTES, &bar[B_TAB + tbi]);
+            filled[tbi]++;
           }
           if (!mbar_wait_abortable(&bar[B_TAB + tbi], consumed[tbi] & 1u, abort_flag)) { ok = false; break; }
           consumed[tbi]++;
@@ -345,18 +378,33 @@ __global__ void __launch_bounds__(TC_BLOCK, 1)
           }
           mma_commit(&bar[B_SFULL + sb]);
           issued_any = true;
-          // double table buffer: refill the other buffer (used by chunk g-1) with chunk g+1
-          if (TBUF == 2 && g >= 1 && g + 1 < G) {
-            const uint32_t pk = (uint32_t)(VBUF == 2 ? ((g - 1) >> 1) : (g - 1));
-            if (!mbar_wait_abortable(&bar[B_VFREE + (VBUF == 2 ? (int)((g - 1) & 1) : 0)], pk & 1u, abort_flag)) {
-              ok = false;
-              break;
-            }
-            const int ob = (int)((g + 1) & 1);
-            bulk_load(tb + ob * L::TB_WORDS, tabs + (size_t)((g + 1) % nch) * L::TB_WORDS, TB_BYTES, &bar[B_TAB + ob]);
-            filled[ob]++;
-          }
-          // GEMM2: Y [128 x NP] += V_d [128 x 16] * G_d [16 x NP]
+        }
+      }
+      if (!ok) {
+        *abort_flag = 1;
+        atomicExch(err, (int)CEED_ERR_TIMEOUT);
+        // let this thread's operations in flight finish before TMEM and shared memory are released
+        if (issued_any) {
+          mma_commit(&bar[B_DRAIN1]);
+          mbar_wait_bounded(&bar[B_DRAIN1], 0u);
+        }
+        for (int bb = 0; bb < TBUF; ++bb)
+          if (filled[bb] > consumed[bb]) mbar_wait_bounded(&bar[B_TAB + bb], consumed[bb] & 1u);
+      }
+    }
+    __syncwarp();
+  } else if (warp == TC_CW + 1) {
+    // ------------------------------------------------------------------ GEMM2 issuer
+    if (lane == 0) {
+      constexpr uint32_t ID2 = IDescTF32<TC_M, NP>::value;
+      bool issued_any = false;
+      int64_t g = 0;
+      for (int64_t t = 0; t < my_tiles && ok; ++t) {
+        const int yb = (int)(t & 1);
+        for (int c = 0; c < nch && ok; ++c, ++g) {
+          const int tbi = (int)(g % TBUF), vb = (int)(g % VBUF);
+          const uint32_t vk = (uint32_t)(g / VBUF);
+          // V of chunk g written (the chunk's S landed before, so its tables are in buffer tbi)
           if (!mbar_wait_abortable(&bar[B_VFULL + vb], vk & 1u, abort_flag)) { ok = false; break; }
           if (c == 0 && t >= 2 &&
               !mbar_wait_abortable(&bar[B_YFREE + yb], (uint32_t)(((t >> 1) - 1) & 1), abort_flag)) {
@@ -364,8 +412,9 @@ __global__ void __launch_bounds__(TC_BLOCK, 1)
             break;
           }
           tc_fence_after();
+          // GEMM2: Y [128 x NP] += V_d [128 x 16] * G_d [16 x NP]
           const uint32_t vs = su32(vbase + vb * 2 * L::V_WORDS);
-          const uint32_t gs = tbs + 4u * 2 * D * TC_QC * KP;
+          const uint32_t gs = su32(tb + tbi * L::TB_WORDS) + 4u * 2 * D * TC_QC * KP;
           const uint64_t dv_hi = sdesc(vs, 128, 512), dv_lo = sdesc(vs + 4u * L::V_WORDS, 128, 512);
           const uint64_t dG_hi = sdesc(gs, 128, 512), dG_lo = sdesc(gs + 4u * D * NP * TC_QC, 128, 512);
           const uint32_t ycol = tmem + TC_YCOL0 + 128u * yb;
@@ -381,19 +430,18 @@ __global__ void __launch_bounds__(TC_BLOCK, 1)
             }
           }
           mma_commit(&bar[B_VFREE + vb]);
+          mma_commit(&bar[B_TBFREE + tbi]);
           if (c == nch - 1) mma_commit(&bar[B_YFULL + yb]);
+          issued_any = true;
         }
       }
       if (!ok) {
         *abort_flag = 1;
         atomicExch(err, (int)CEED_ERR_TIMEOUT);
-        // let this block's own operations in flight finish before TMEM and shared memory are released
         if (issued_any) {
-          mma_commit(&bar[B_DRAIN]);
-          mbar_wait_bounded(&bar[B_DRAIN], 0u);
+          mma_commit(&bar[B_DRAIN2]);
+          mbar_wait_bounded(&bar[B_DRAIN2], 0u);
         }
-        for (int bb = 0; bb < 2; ++bb)
-          if (filled[bb] > consumed[bb]) mbar_wait_bounded(&bar[B_TAB + bb], consumed[bb] & 1u);
       }
     }
     __syncwarp();
@@ -402,10 +450,10 @@ __global__ void __launch_bounds__(TC_BLOCK, 1)
     const int quad = warp & 3, grp = warp >> 2;
     const int m = quad * 32 + lane;
     const uint32_t lane_base = (uint32_t)(quad * 32) << 16;
-    float qnext[TC_PPT][D == 3 ? 6 : 1];
+    float *qs = qslots + tid;
     if (my_tiles > 0) {
       const int64_t e0 = (int64_t)blockIdx.x * TC_M + m;
-      load_qdata<D>(qd, E, Q, e0, e0 < E, 0, grp, qnext);
+      if (QPRE) prefetch_qdata<D>(qd, E, Q, e0, e0 < E, 0, grp, qs);
       gather_tile<KP>(E, P, e0, e0 < E, grp, m, masked, rmap, x, u_hi, u_lo);
       fence_proxy_async();
       mbar_arrive(&bar[B_UFULL]);
@@ -417,8 +465,8 @@ __global__ void __launch_bounds__(TC_BLOCK, 1)
       const bool valid = e < E;
       const int yb = (int)(t & 1);
       for (int c = 0; c < nch; ++c, ++g) {
-        const int sb = (int)(g & 1), vb = VBUF == 2 ? (int)(g & 1) : 0;
-        const uint32_t sk = (uint32_t)(g >> 1), vk = (uint32_t)(VBUF == 2 ? (g >> 1) : g);
+        const int sb = (int)(g & 1), vb = (int)(g % VBUF);
+        const uint32_t sk = (uint32_t)(g >> 1), vk = (uint32_t)(g / VBUF);
         if (!mbar_wait_abortable(&bar[B_SFULL + sb], sk & 1u, abort_flag)) { ok = false; break; }
         tc_fence_after();
         float s[D][TC_PPT];
@@ -426,16 +474,15 @@ __global__ void __launch_bounds__(TC_BLOCK, 1)
         for (int d = 0; d < D; ++d) tmem_ld4(tmem + lane_base + TC_SCOL * sb + 16u * d + TC_PPT * grp, s[d]);
         tc_fence_before();
         mbar_arrive(&bar[B_SFREE + sb]);
-        float qv[TC_PPT][D == 3 ? 6 : 1];
+        float qv[TC_PPT][NQ];
+        if (QPRE) {
+          cp_async_wait_all();   // this thread's own copies of chunk g
 #pragma unroll
-        for (int j = 0; j < TC_PPT; ++j)
+          for (int j = 0; j < TC_PPT; ++j)
 #pragma unroll
-          for (int k = 0; k < (D == 3 ? 6 : 1); ++k) qv[j][k] = qnext[j][k];
-        if (c + 1 < nch) {
-          load_qdata<D>(qd, E, Q, e, valid, c + 1, grp, qnext);
-        } else if (t + 1 < my_tiles) {
-          const int64_t e1 = (tile + gridDim.x) * TC_M + m;
-          load_qdata<D>(qd, E, Q, e1, e1 < E, 0, grp, qnext);
+            for (int k = 0; k < NQ; ++k) qv[j][k] = qs[(j * NQ + k) * TC_COMPUTE];
+        } else {
+          load_qdata<D>(qd, E, Q, e, valid, c, grp, qv);
         }
 #pragma unroll
         for (int j = 0; j < TC_PPT; ++j) {
@@ -446,6 +493,15 @@ __global__ void __launch_bounds__(TC_BLOCK, 1)
             s[2][j] = qv[j][2] * g0 + qv[j][4] * g1 + qv[j][5] * g2;
           } else {
             s[0][j] *= qv[j][0];
+          }
+        }
+        if (QPRE) {
+          // the slots are consumed (qv is in registers and used above): start the next chunk's copies
+          if (c + 1 < nch) {
+            prefetch_qdata<D>(qd, E, Q, e, valid, c + 1, grp, qs);
+          } else if (t + 1 < my_tiles) {
+            const int64_t e1 = (tile + gridDim.x) * TC_M + m;
+            prefetch_qdata<D>(qd, E, Q, e1, e1 < E, 0, grp, qs);
           }
         }
         // V buffer vb is free once the product of chunk g - VBUF that read it has completed
@@ -489,6 +545,7 @@ __global__ void __launch_bounds__(TC_BLOCK, 1)
       tc_fence_before();
       mbar_arrive(&bar[B_YFREE + yb]);
     }
+    if (QPRE) cp_async_wait_all();   // no copy into shared memory may outlive the block
     if (!ok) {
       *abort_flag = 1;
       atomicExch(err, (int)CEED_ERR_TIMEOUT);
@@ -538,16 +595,16 @@ static void build_tables(const std::vector<double> &tab, int D, int P, int Q, in
   }
 }
 
-template <int D, int KP, int NP, int TBUF, int VBUF>
+template <int D, int KP, int NP, int TBUF, int VBUF, int QPRE>
 static int launch_tc(ceed_nt_t h, const float *tabs, const float *qd, const double *x, float *Ye, int masked,
                      cudaStream_t s) {
-  using L = TcLayout<D, KP, NP, TBUF, VBUF>;
+  using L = TcLayout<D, KP, NP, TBUF, VBUF, QPRE>;
   // one block per SM: the block holds 512 TMEM columns (S and Y double-buffered)
   constexpr size_t SMEM = L::BYTES > 116 * 1024 ? L::BYTES : 116 * 1024;
   static uint64_t attr_set = 0;
   const uint64_t bit = 1ull << (h->device & 63);
   if (!(attr_set & bit)) {
-    CEED_CUDA_CHECK(cudaFuncSetAttribute(nt_tc_kernel<D, KP, NP, TBUF, VBUF>,
+    CEED_CUDA_CHECK(cudaFuncSetAttribute(nt_tc_kernel<D, KP, NP, TBUF, VBUF, QPRE>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM));
     attr_set |= bit;
   }
@@ -556,20 +613,23 @@ static int launch_tc(ceed_nt_t h, const float *tabs, const float *qd, const doub
   if (sms == 0) CEED_CUDA_CHECK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device));
   const int64_t ntiles = (h->E + TC_M - 1) / TC_M;
   const unsigned grid = (unsigned)std::min<int64_t>(ntiles, (int64_t)sms);
-  nt_tc_kernel<D, KP, NP, TBUF, VBUF><<<grid, TC_BLOCK, SMEM, s>>>(h->E, h->P, h->Q, h->tc_nchunk, h->d_rmap, x, tabs,
-                                                                  qd, Ye, masked, h->d_err);
+  nt_tc_kernel<D, KP, NP, TBUF, VBUF, QPRE><<<grid, TC_BLOCK, SMEM, s>>>(h->E, h->P, h->Q, h->tc_nchunk, h->d_rmap, x,
+                                                                        tabs, qd, Ye, masked, h->d_err);
   CEED_CUDA_CHECK(cudaGetLastError());
   return CEED_OK;
 }
 
-// Buffering that fits in shared memory: V double if possible, then the tables double if possible.
+// Buffering that fits in shared memory, in order of benefit: quadrature-data prefetch slots, a
+// second table buffer (the tables of the next chunk stream in during the current one), a second V.
 template <int D, int KP, int NP>
 struct TcBufs {
   static constexpr size_t lim = 227 * 1024;
-  static constexpr size_t base = 8ull * TC_M * KP + 16 * 8 + 16;
+  static constexpr size_t base = 8ull * TC_M * KP + TC_NBAR * 8 + 16;
   static constexpr size_t tbw = 4ull * chunk_words(D, KP, NP), vw = 8ull * D * TC_M * TC_QC;
-  static constexpr int VBUF = base + tbw + 2 * vw <= lim ? 2 : 1;
-  static constexpr int TBUF = base + 2 * tbw + VBUF * vw <= lim ? 2 : 1;
+  static constexpr size_t qw = 4ull * TC_PPT * (D == 3 ? 6 : 1) * TC_COMPUTE;
+  static constexpr int QPRE = base + tbw + vw + qw <= lim ? 1 : 0;
+  static constexpr int TBUF = base + 2 * tbw + vw + QPRE * qw <= lim ? 2 : 1;
+  static constexpr int VBUF = base + TBUF * tbw + 2 * vw + QPRE * qw <= lim ? 2 : 1;
 };
 
 template <int PP>
@@ -578,8 +638,8 @@ static int dispatch_p(ceed_nt_t h, int op, const float *qd, const double *x, flo
   const float *tabs = h->d_tc_tab[op == CEED_OP_MASS ? 0 : 1];
   using B1 = TcBufs<1, KP, NP>;
   using B3 = TcBufs<3, KP, NP>;
-  return op == CEED_OP_MASS ? launch_tc<1, KP, NP, B1::TBUF, B1::VBUF>(h, tabs, qd, x, Ye, masked, s)
-                            : launch_tc<3, KP, NP, B3::TBUF, B3::VBUF>(h, tabs, qd, x, Ye, masked, s);
+  return op == CEED_OP_MASS ? launch_tc<1, KP, NP, B1::TBUF, B1::VBUF, B1::QPRE>(h, tabs, qd, x, Ye, masked, s)
+                            : launch_tc<3, KP, NP, B3::TBUF, B3::VBUF, B3::QPRE>(h, tabs, qd, x, Ye, masked, s);
 }
 
 }  // namespace
