@@ -170,13 +170,19 @@ __device__ __forceinline__ float nt_cvt<float>(double v) { return (float)v; }
 // Quadrature data of the affine simplex map x = v0 + J xi (J columns v1-v0, v2-v0, v3-v0): mass
 // w |det J| rho, diffusion w k adj(J) adj(J)^T / det J.  One thread per (point, element).
 template <typename T>
-__global__ void nt_qdata_kernel(int64_t E, int Q, int op, const double *__restrict__ vert,
+__global__ void nt_qdata_kernel(int64_t E, int64_t Es, int Q, int op, const double *__restrict__ vert,
                                 const double *__restrict__ qw, const double *__restrict__ qref, int coeff_kind,
                                 double cconst, const double *__restrict__ coeff, T *__restrict__ out, int *err) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= E * Q) return;
-  const int64_t e = i % E;
-  const int q = (int)(i / E);
+  if (i >= Es * Q) return;
+  const int64_t e = i % Es;
+  const int q = (int)(i / Es);
+  const int64_t cs = (int64_t)Q * Es;
+  T *o = out + (int64_t)q * Es + e;
+  if (e >= E) {   // padding of the last tile: zeros
+    for (int k = 0; k < (op == CEED_OP_MASS ? 1 : 6); ++k) o[k * cs] = T(0);
+    return;
+  }
   const double *V = vert + e * 12;
   double J[3][3];
 #pragma unroll
@@ -199,8 +205,6 @@ __global__ void nt_qdata_kernel(int64_t E, int Q, int op, const double *__restri
     k = coeff[e * Q + q];
   }
   const double w = qw[q];
-  const int64_t cs = (int64_t)Q * E;
-  T *o = out + (int64_t)q * E + e;
   if (op == CEED_OP_MASS) {
     o[0] = nt_cvt<T>(w * fabs(det) * k);
   } else {
@@ -237,7 +241,7 @@ __device__ __forceinline__ void nt_pointwise(const T *__restrict__ qd, int64_t c
 // in registers (node rows spread over the warps).  Output: the element vectors, [P][E].
 template <typename T, int D>
 __global__ void __launch_bounds__(NT_NE * NT_WARPS)
-    nt_fused_kernel(int64_t E, int P, int Q, const uint32_t *__restrict__ rmap, const double *__restrict__ x,
+    nt_fused_kernel(int64_t E, int64_t Es, int P, int Q, const uint32_t *__restrict__ rmap, const double *__restrict__ x,
                     const T *__restrict__ tab, const T *__restrict__ qd, T *__restrict__ Ye, int masked) {
   extern __shared__ __align__(16) unsigned char nt_smem[];
   T *Us = reinterpret_cast<T *>(nt_smem);   // [P][NT_NE]
@@ -258,7 +262,7 @@ __global__ void __launch_bounds__(NT_NE * NT_WARPS)
   T yr[NT_YR];
 #pragma unroll
   for (int j = 0; j < NT_YR; ++j) yr[j] = T(0);
-  const int64_t cs = (int64_t)Q * E;
+  const int64_t cs = (int64_t)Q * Es;
   for (int q0 = 0; q0 < Q; q0 += NT_QC) {
     const int qc = min(NT_QC, Q - q0);
     __syncthreads();
@@ -285,7 +289,7 @@ __global__ void __launch_bounds__(NT_NE * NT_WARPS)
 #pragma unroll
       for (int d = 0; d < D; ++d) g[d] = Sv[(d * NT_QC + q) * LD + lane];
       if (valid) {
-        nt_pointwise<T, D>(qd + (int64_t)(q0 + q) * E + e, cs, g);
+        nt_pointwise<T, D>(qd + (int64_t)(q0 + q) * Es + e, cs, g);
       } else {
 #pragma unroll
         for (int d = 0; d < D; ++d) g[d] = T(0);
@@ -327,16 +331,17 @@ __global__ void nt_gather_kernel(int64_t total, const uint32_t *__restrict__ rma
   U[i] = (masked && (m & FLAG_DIR)) ? T(0) : nt_cvt<T>(x[m & DOF_MASK]);
 }
 
-// GEMM path, step 3: pointwise D in place on S [D][Q][E], one thread per (point, element).
+// GEMM path, step 3: pointwise D in place on S [D][Q][E]; grid x over elements, y over points.
 template <typename T, int D>
-__global__ void nt_pointwise_kernel(int64_t E, int Q, const T *__restrict__ qd, T *__restrict__ S) {
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const int64_t cs = (int64_t)Q * E;
-  if (i >= cs) return;
+__global__ void nt_pointwise_kernel(int64_t E, int64_t Es, int Q, const T *__restrict__ qd, T *__restrict__ S) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int q = blockIdx.y;
+  if (e >= E) return;
+  const int64_t cs = (int64_t)Q * E, i = (int64_t)q * E + e;
   T g[D];
 #pragma unroll
   for (int d = 0; d < D; ++d) g[d] = S[d * cs + i];
-  nt_pointwise<T, D>(qd + i, cs, g);
+  nt_pointwise<T, D>(qd + (int64_t)q * Es + e, (int64_t)Q * Es, g);
 #pragma unroll
   for (int d = 0; d < D; ++d) S[d * cs + i] = g[d];
 }
@@ -372,7 +377,7 @@ static int launch_fused(ceed_nt_t h, const T *tab, const T *qd, const double *x,
     attr_set |= bit;
   }
   const unsigned grid = (unsigned)((h->E + NT_NE - 1) / NT_NE);
-  nt_fused_kernel<T, D><<<grid, NT_NE * NT_WARPS, sm, s>>>(h->E, h->P, h->Q, h->d_rmap, x, tab, qd, Ye, masked);
+  nt_fused_kernel<T, D><<<grid, NT_NE * NT_WARPS, sm, s>>>(h->E, h->Es, h->P, h->Q, h->d_rmap, x, tab, qd, Ye, masked);
   CEED_CUDA_CHECK(cudaGetLastError());
   return CEED_OK;
 }
@@ -451,8 +456,8 @@ static int nt_apply_t(ceed_nt_t h, const NtChoice &c, const T *tab, const T *qd,
     cublasStatus_t bs = cublasSetStream(h->blas, s);
     if (bs != CUBLAS_STATUS_SUCCESS) return blas_fail(bs, "cublasSetStream");
     if ((st = nt_gemm<T>(h, false, D * h->Q, h->P, U, tab, S, c.eta, c.gemm_mode)) != CEED_OK) return st;
-    const int64_t pts = (int64_t)h->Q * h->E;
-    nt_pointwise_kernel<T, D><<<(unsigned)((pts + 255) / 256), 256, 0, s>>>(h->E, h->Q, qd, S);
+    nt_pointwise_kernel<T, D><<<dim3((unsigned)((h->E + 255) / 256), (unsigned)h->Q), 256, 0, s>>>(h->E, h->Es, h->Q,
+                                                                                               qd, S);
     CEED_CUDA_CHECK(cudaGetLastError());
     st = nt_gemm<T>(h, true, h->P, D * h->Q, S, tab, Ye, c.eta, c.gemm_mode);
   }
@@ -522,7 +527,7 @@ extern "C" int ceed_nt_setup(const ceed_nt_desc *desc, ceed_nt_t *out, void *str
   if (nL > (int64_t)DOF_MASK) return fail(CEED_ERR_INVALID, "n_ldof must be < 2^29");
   if (P < 1 || P > NT_MAXP) return fail(CEED_ERR_INVALID, "P must be in 1..128");
   if (Q < 1 || Q > NT_MAXQ) return fail(CEED_ERR_INVALID, "Q must be in 1..1024");
-  if ((int64_t)P * E >= ((int64_t)1 << 32) || (int64_t)3 * Q * E >= ((int64_t)1 << 31))
+  if ((int64_t)P * E >= ((int64_t)1 << 32) || (int64_t)3 * Q * (E + 127) >= ((int64_t)1 << 31))
     return fail(CEED_ERR_INVALID, "mesh too large for 32-bit element-vector positions");
   if (!desc->interp || !desc->grad || !desc->qweight || !desc->qref)
     return fail(CEED_ERR_INVALID, "interp, grad, qweight and qref (host arrays) are required");
@@ -532,6 +537,7 @@ extern "C" int ceed_nt_setup(const ceed_nt_desc *desc, ceed_nt_t *out, void *str
   if (!h) return fail(CEED_ERR_OOM, "host allocation");
   CEED_CUDA_CHECK(cudaGetDevice(&h->device));
   h->E = E;
+  h->Es = (E + 127) / 128 * 128;
   h->n_ldof = nL;
   h->P = P;
   h->Q = Q;
@@ -638,7 +644,7 @@ extern "C" int ceed_nt_destroy(ceed_nt_t h) {
 
 extern "C" size_t ceed_nt_qdata_bytes(ceed_nt_t h, int op, int prec) {
   if (nt_check(h, op, prec) != CEED_OK) return 0;
-  return (size_t)(op == CEED_OP_MASS ? 1 : 6) * h->Q * h->E * (prec == CEED_F64 ? 8 : 4);
+  return (size_t)(op == CEED_OP_MASS ? 1 : 6) * h->Q * h->Es * (prec == CEED_F64 ? 8 : 4);
 }
 
 extern "C" int ceed_nt_build_qdata(ceed_nt_t h, int op, int coeff_kind, const double *coeff, int prec, void *qdata,
@@ -657,13 +663,13 @@ extern "C" int ceed_nt_build_qdata(ceed_nt_t h, int op, int coeff_kind, const do
   }
   cudaStream_t s = (cudaStream_t)stream;
   CEED_CUDA_CHECK(cudaMemsetAsync(h->d_err, 0, sizeof(int), s));
-  const int64_t tot = (int64_t)h->Q * h->E;
+  const int64_t tot = (int64_t)h->Q * h->Es;
   const unsigned grid = (unsigned)((tot + 255) / 256);
   if (prec == CEED_F64)
-    nt_qdata_kernel<double><<<grid, 256, 0, s>>>(h->E, h->Q, op, h->d_vert, h->d_qw, h->d_qref, coeff_kind, cconst,
+    nt_qdata_kernel<double><<<grid, 256, 0, s>>>(h->E, h->Es, h->Q, op, h->d_vert, h->d_qw, h->d_qref, coeff_kind, cconst,
                                                  coeff, static_cast<double *>(qdata), h->d_err);
   else
-    nt_qdata_kernel<float><<<grid, 256, 0, s>>>(h->E, h->Q, op, h->d_vert, h->d_qw, h->d_qref, coeff_kind, cconst,
+    nt_qdata_kernel<float><<<grid, 256, 0, s>>>(h->E, h->Es, h->Q, op, h->d_vert, h->d_qw, h->d_qref, coeff_kind, cconst,
                                                 coeff, static_cast<float *>(qdata), h->d_err);
   CEED_CUDA_CHECK(cudaGetLastError());
   int err = 0;

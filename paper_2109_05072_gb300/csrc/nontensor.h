@@ -27,6 +27,7 @@ struct NtChoice {
 struct ceed_nt_s {
   int device = 0;
   int64_t E = 0, n_ldof = 0;
+  int64_t Es = 0;              // element stride of the quadrature data: E rounded up to whole 128-element tiles
   int P = 0, Q = 0;
   double *d_tab64 = nullptr;   // [4][Q][P]: interp, then grad along xi_1, xi_2, xi_3
   float *d_tab32 = nullptr;

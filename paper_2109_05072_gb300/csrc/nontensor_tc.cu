@@ -47,7 +47,9 @@ __host__ __device__ constexpr int canon(int r, int k, int K) {
 }
 
 // Words of one chunk of split tables for D directions: GT_hi, GT_lo [D][16 x KP], G_hi, G_lo [D][NP x 16].
-__host__ __device__ constexpr int chunk_words(int D, int KP, int NP) { return 2 * D * TC_QC * KP + 2 * D * NP * TC_QC; }
+__host__ __device__ constexpr int gt_words(int D, int KP) { return 2 * D * TC_QC * KP; }   // GEMM1 operand, hi + lo
+__host__ __device__ constexpr int g_words(int D, int NP) { return 2 * D * NP * TC_QC; }    // GEMM2 operand, hi + lo
+__host__ __device__ constexpr int chunk_words(int D, int KP, int NP) { return gt_words(D, KP) + g_words(D, NP); }
 
 __device__ __forceinline__ uint32_t su32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -137,9 +139,9 @@ __device__ __forceinline__ void st_shared4(float *p, float a, float b, float c, 
 }
 
 // mbarrier slots
-enum : int { B_TAB = 0, B_SFULL = 2, B_SFREE = 4, B_VFULL = 6, B_VFREE = 8, B_UFULL = 10, B_YFULL = 11, B_YFREE = 13,
-             B_TBFREE = 15, B_DRAIN1 = 17, B_DRAIN2 = 18 };
-constexpr int TC_NBAR = 20;
+enum : int { B_T1 = 0, B_T2 = 2, B_SFULL = 4, B_SFREE = 6, B_VFULL = 8, B_VFREE = 10, B_UFULL = 12, B_YFULL = 13,
+             B_YFREE = 15, B_T2FREE = 17, B_DRAIN1 = 19, B_DRAIN2 = 20, B_QFULL = 21 };
+constexpr int TC_NBAR = 24;
 constexpr int TC_CW = 16;                       // compute warps (0-15); warps 16, 17 issue the MMAs
 constexpr int TC_COMPUTE = 32 * TC_CW;
 constexpr int TC_BLOCK = TC_COMPUTE + 64;
@@ -150,20 +152,23 @@ constexpr uint32_t TC_TMEM_ALLOC = 512;
 constexpr uint32_t TC_SCOL = 64;                // S buffer s at TMEM column 64 s
 constexpr uint32_t TC_YCOL0 = 256;              // Y buffer y at TMEM column 256 + 128 y
 
-// Shared-memory map of one block.  U: the tile's element inputs (hi, lo); TB[TBUF]: table chunks;
-// V[VBUF]: the pointwise results (hi, lo); QS: each compute thread's prefetch slots for its
-// quadrature data of the next chunk ([value][thread], when QPRE); then the mbarriers, the TMEM
-// address and an abort flag.
+// Shared-memory map of one block.  U: the tile's element inputs (hi, lo); T1[TBUF], T2[TBUF]: the
+// GEMM1 and GEMM2 operands of a table chunk;
+// V[VBUF]: the pointwise results (hi, lo); QS: the tile's quadrature data of the next chunk
+// ([value][point][element], when QPRE); then the mbarriers, the TMEM address and an abort flag.
 template <int D, int KP, int NP, int TBUF, int VBUF, int QPRE>
 struct TcLayout {
   static constexpr int U_WORDS = TC_M * KP;                // per hi/lo
-  static constexpr int TB_WORDS = chunk_words(D, KP, NP);  // one table buffer
+  static constexpr int T1_WORDS = gt_words(D, KP);         // one GEMM1 table buffer
+  static constexpr int T2_WORDS = g_words(D, NP);          // one GEMM2 table buffer
+  static constexpr int TB_WORDS = T1_WORDS + T2_WORDS;     // one chunk of the global table image
   static constexpr int V_WORDS = D * TC_M * TC_QC;         // per hi/lo
-  static constexpr int QS_WORDS = QPRE * TC_PPT * (D == 3 ? 6 : 1) * TC_COMPUTE;
+  static constexpr int QS_WORDS = QPRE * (D == 3 ? 6 : 1) * TC_QC * TC_M;   // [value][point][element]
   static constexpr size_t U_HI = 0;
   static constexpr size_t U_LO = U_HI + 4 * (size_t)U_WORDS;
-  static constexpr size_t TB = U_LO + 4 * (size_t)U_WORDS;
-  static constexpr size_t V = TB + 4 * (size_t)TB_WORDS * TBUF;   // buffer v: hi at V + 8 V_WORDS v, lo + 4 V_WORDS
+  static constexpr size_t T1 = U_LO + 4 * (size_t)U_WORDS;
+  static constexpr size_t T2 = T1 + 4 * (size_t)T1_WORDS * TBUF;
+  static constexpr size_t V = T2 + 4 * (size_t)T2_WORDS * TBUF;   // buffer v: hi at V + 8 V_WORDS v, lo + 4 V_WORDS
   static constexpr size_t QS = V + 8 * (size_t)V_WORDS * VBUF;
   static constexpr size_t BARS = QS + 4 * (size_t)QS_WORDS;
   static constexpr size_t BYTES = BARS + TC_NBAR * 8 + 16;
@@ -195,11 +200,27 @@ __device__ __forceinline__ bool mbar_wait_abortable(uint64_t *bar, uint32_t pari
   return false;
 }
 
-__device__ __forceinline__ void cp_async4(float *dst, const float *src) {
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(su32(dst)), "l"(src) : "memory");
+// 16-byte asynchronous copy global -> shared; src_bytes = 0 writes zeros without reading.
+__device__ __forceinline__ void cp_async16(float *dst, const float *src, uint32_t src_bytes) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(su32(dst)), "l"(src), "r"(src_bytes) : "memory");
 }
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+// The mbarrier receives this thread's arrival once all its earlier cp.async copies have landed.
+__device__ __forceinline__ void cp_async_arrive(uint64_t *bar) {
+  asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(su32(bar)) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
+// Barrier among the compute warps only (id 1) that also ANDs a flag over them: every compute
+// thread executes the same sequence of these, so the block leaves its loops together.
+__device__ __forceinline__ bool compute_all(bool v) {
+  uint32_t r;
+  asm volatile(
+      "{\n .reg .pred p, q;\n setp.ne.u32 p, %1, 0;\n bar.red.and.pred q, 1, %2, p;\n selp.u32 %0, 1, 0, q;\n}\n"
+      : "=r"(r)
+      : "r"((uint32_t)v), "n"(TC_COMPUTE)
+      : "memory");
+  return r != 0;
+}
 
 // The tile's element inputs, split into TF32 hi/lo, written to the canonical layout (row m,
 // columns 4 k4 .. 4 k4 + 3 for this thread's share k4 = grp, grp + 4, ... of the column groups).
@@ -244,44 +265,42 @@ __device__ __forceinline__ void gather_tile(int64_t E, int P, int64_t e, bool va
   }
 }
 
-// Quadrature data of one thread's TC_PPT points of chunk c of a tile: into registers (qv) or, as
-// asynchronous copies, into the thread's prefetch slots (qs + k * TC_COMPUTE, value k); entries
-// outside the mesh or the rule are zero.
+// Quadrature data of one thread's TC_PPT points of chunk c of a tile, into registers (zero outside
+// the rule; rows are padded to whole tiles, so every element of a tile can be read).
 template <int D>
-__device__ __forceinline__ void load_qdata(const float *__restrict__ qd, int64_t E, int Q, int64_t e, bool valid,
-                                           int c, int grp, float (&qv)[TC_PPT][D == 3 ? 6 : 1]) {
-  const int64_t cs = (int64_t)Q * E;
+__device__ __forceinline__ void load_qdata(const float *__restrict__ qd, int64_t Es, int Q, int64_t e, int c, int grp,
+                                           float (&qv)[TC_PPT][D == 3 ? 6 : 1]) {
+  const int64_t cs = (int64_t)Q * Es;
   const int q0 = c * TC_QC + TC_PPT * grp;
-  const float *base = qd + (int64_t)q0 * E + e;
+  const float *base = qd + (int64_t)q0 * Es + e;
 #pragma unroll
   for (int j = 0; j < TC_PPT; ++j) {
-    const bool in = valid && q0 + j < Q;
+    const bool in = q0 + j < Q;
 #pragma unroll
-    for (int k = 0; k < (D == 3 ? 6 : 1); ++k) qv[j][k] = in ? __ldg(base + k * cs + (int64_t)j * E) : 0.f;
+    for (int k = 0; k < (D == 3 ? 6 : 1); ++k) qv[j][k] = in ? __ldg(base + k * cs + (int64_t)j * Es) : 0.f;
   }
 }
+// The tile's quadrature data of chunk c into the block's buffer qbuf [value k][point qq][element]
+// with 16-byte copies: compute warp w copies rows (k, qq) = w, w + 16, ... (128 consecutive
+// elements each, lane l elements 4 l .. 4 l + 3); points beyond the rule are zero-filled.  The
+// thread's arrival on q_full follows the completion of its copies.
 template <int D>
-__device__ __forceinline__ void prefetch_qdata(const float *__restrict__ qd, int64_t E, int Q, int64_t e, bool valid,
-                                               int c, int grp, float *qs) {
-  const int64_t cs = (int64_t)Q * E;
-  const int q0 = c * TC_QC + TC_PPT * grp;
-  const float *base = qd + (int64_t)q0 * E + e;
+__device__ __forceinline__ void tile_qdata_async(const float *__restrict__ qd, int64_t Es, int Q, int64_t tile, int c,
+                                                 int warp, int lane, float *qbuf, uint64_t *q_full) {
+  constexpr int NQ = D == 3 ? 6 : 1;
 #pragma unroll
-  for (int j = 0; j < TC_PPT; ++j) {
-    const bool in = valid && q0 + j < Q;
-#pragma unroll
-    for (int k = 0; k < (D == 3 ? 6 : 1); ++k) {
-      float *dst = qs + (j * (D == 3 ? 6 : 1) + k) * TC_COMPUTE;
-      if (in) cp_async4(dst, base + k * cs + (int64_t)j * E);
-      else *dst = 0.f;
-    }
+  for (int r = warp; r < NQ * TC_QC; r += TC_CW) {
+    const int k = r / TC_QC, qq = r - k * TC_QC, q = c * TC_QC + qq;
+    const bool in = q < Q;
+    const float *src = qd + ((int64_t)k * Q + (in ? q : 0)) * Es + tile * TC_M + 4 * lane;
+    cp_async16(qbuf + r * TC_M + 4 * lane, src, in ? 16u : 0u);
   }
-  cp_async_commit();
+  cp_async_arrive(q_full);
 }
 
 // The fused kernel, persistent (block b takes tiles b, b + gridDim.x, ...) and warp-specialized.
-//   warp 16 (one thread): streams the table chunks in with bulk copies, issues GEMM1 of every chunk
-//   warp 17 (one thread): issues GEMM2 of every chunk
+//   warp 16 (one thread): streams the GEMM1 operand of each table chunk in (bulk copies), issues GEMM1
+//   warp 17 (one thread): the same for GEMM2
 //   warps 0-15: gather inputs, apply the pointwise operator, write the element vectors
 // They hand buffers to each other through mbarriers (the tensor core signals completion through
 // tcgen05.commit).  S (TMEM) and Y (TMEM) are double-buffered, V and the tables when shared memory
@@ -292,15 +311,16 @@ __device__ __forceinline__ void prefetch_qdata(const float *__restrict__ qd, int
 // its own shared-memory slots with cp.async while it works on the current one.
 template <int D, int KP, int NP, int TBUF, int VBUF, int QPRE>
 __global__ void __launch_bounds__(TC_BLOCK, 1)
-    nt_tc_kernel(int64_t E, int P, int Q, int nch, const uint32_t *__restrict__ rmap, const double *__restrict__ x,
-                 const float *__restrict__ tabs, const float *__restrict__ qd, float *__restrict__ Ye, int masked,
-                 int *err) {
+    nt_tc_kernel(int64_t E, int64_t Es, int P, int Q, int nch, const uint32_t *__restrict__ rmap,
+                 const double *__restrict__ x, const float *__restrict__ tabs, const float *__restrict__ qd,
+                 float *__restrict__ Ye, int masked, int *err) {
   using L = TcLayout<D, KP, NP, TBUF, VBUF, QPRE>;
   constexpr int NQ = D == 3 ? 6 : 1;
   extern __shared__ __align__(1024) unsigned char tc_smem[];
   float *u_hi = reinterpret_cast<float *>(tc_smem + L::U_HI);
   float *u_lo = reinterpret_cast<float *>(tc_smem + L::U_LO);
-  float *tb = reinterpret_cast<float *>(tc_smem + L::TB);
+  float *t1 = reinterpret_cast<float *>(tc_smem + L::T1);
+  float *t2 = reinterpret_cast<float *>(tc_smem + L::T2);
   float *vbase = reinterpret_cast<float *>(tc_smem + L::V);
   float *qslots = reinterpret_cast<float *>(tc_smem + L::QS);
   uint64_t *bar = reinterpret_cast<uint64_t *>(tc_smem + L::BARS);
@@ -311,7 +331,7 @@ __global__ void __launch_bounds__(TC_BLOCK, 1)
   const int64_t ntiles = (E + TC_M - 1) / TC_M;
   const int64_t my_tiles = blockIdx.x < ntiles ? (ntiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
   const int64_t G = my_tiles * nch;  // chunks this block processes
-  constexpr uint32_t TB_BYTES = 4u * (uint32_t)L::TB_WORDS;
+  constexpr uint32_t T1_BYTES = 4u * (uint32_t)L::T1_WORDS, T2_BYTES = 4u * (uint32_t)L::T2_WORDS;
 
   if (warp == TC_CW) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(tmem_slot)),
@@ -322,7 +342,7 @@ __global__ void __launch_bounds__(TC_BLOCK, 1)
   if (tid == 0) {
     for (int i = 0; i < TC_NBAR; ++i) {
       const bool by_threads = i == B_SFREE || i == B_SFREE + 1 || i == B_VFULL || i == B_VFULL + 1 || i == B_UFULL ||
-                              i == B_YFREE || i == B_YFREE + 1;
+                              i == B_YFREE || i == B_YFREE + 1 || i == B_QFULL;
       mbar_init_n(&bar[i], by_threads ? TC_COMPUTE : 1);
     }
     *abort_flag = 0;
@@ -335,15 +355,15 @@ __global__ void __launch_bounds__(TC_BLOCK, 1)
   bool ok = true;
 
   if (warp == TC_CW) {
-    // ------------------------------------------------------------------ tables + GEMM1 issuer
+    // ------------------------------------------------------------------ GEMM1 tables + GEMM1 issuer
     if (lane == 0) {
       constexpr uint32_t ID1 = IDescTF32<TC_M, 16 * D>::value;
       constexpr uint32_t SBO1 = (KP / 4) * 128;
       const uint64_t du_hi = sdesc(su32(u_hi), 128, SBO1), du_lo = sdesc(su32(u_lo), 128, SBO1);
-      uint32_t filled[3] = {0u, 0u, 0u}, consumed[3] = {0u, 0u, 0u};   // table fills per buffer
+      uint32_t filled[2] = {0u, 0u}, consumed[2] = {0u, 0u};   // T1 fills per buffer
       bool issued_any = false;
       for (int f = 0; f < TBUF && f < G; ++f) {
-        bulk_load(tb + f * L::TB_WORDS, tabs + (size_t)(f % nch) * L::TB_WORDS, TB_BYTES, &bar[B_TAB + f]);
+        bulk_load(t1 + f * L::T1_WORDS, tabs + (size_t)(f % nch) * L::TB_WORDS, T1_BYTES, &bar[B_T1 + f]);
         filled[f]++;
       }
       int64_t g = 0;
@@ -351,22 +371,22 @@ __global__ void __launch_bounds__(TC_BLOCK, 1)
         for (int c = 0; c < nch && ok; ++c, ++g) {
           const int tbi = (int)(g % TBUF), sb = (int)(g & 1);
           const uint32_t sk = (uint32_t)(g >> 1);
-          if (g >= TBUF) {
-            // refill buffer tbi with chunk g once the GEMM2 that last read it (chunk g - TBUF) is done
-            if (!mbar_wait_abortable(&bar[B_TBFREE + tbi], (consumed[tbi] - 1) & 1u, abort_flag)) {
+          if (TBUF == 1 && g >= 1) {
+            // single buffer: refill it with chunk g once GEMM1 of chunk g - 1 has completed
+            if (!mbar_wait_abortable(&bar[B_SFULL + (int)((g - 1) & 1)], (uint32_t)(((g - 1) >> 1) & 1), abort_flag)) {
               ok = false;
               break;
             }
-            bulk_load(tb + tbi * L::TB_WORDS, tabs + (size_t)(g % nch) * L::TB_WORDS, TB_BYTES, &bar[B_TAB + tbi]);
-            filled[tbi]++;
+            bulk_load(t1, tabs + (size_t)(g % nch) * L::TB_WORDS, T1_BYTES, &bar[B_T1]);
+            filled[0]++;
           }
-          if (!mbar_wait_abortable(&bar[B_TAB + tbi], consumed[tbi] & 1u, abort_flag)) { ok = false; break; }
+          if (!mbar_wait_abortable(&bar[B_T1 + tbi], consumed[tbi] & 1u, abort_flag)) { ok = false; break; }
           consumed[tbi]++;
           if (c == 0 && !mbar_wait_abortable(&bar[B_UFULL], (uint32_t)(t & 1), abort_flag)) { ok = false; break; }
           if (g >= 2 && !mbar_wait_abortable(&bar[B_SFREE + sb], (sk - 1) & 1u, abort_flag)) { ok = false; break; }
           tc_fence_after();
           // GEMM1: S [128 x 16 D] = U [128 x KP] * GT^T (all directions in one N = 16 D product)
-          const uint32_t tbs = su32(tb + tbi * L::TB_WORDS);
+          const uint32_t tbs = su32(t1 + tbi * L::T1_WORDS);
           const uint64_t dg_hi = sdesc(tbs, 128, SBO1), dg_lo = sdesc(tbs + 4u * D * TC_QC * KP, 128, SBO1);
           const uint32_t dcol = tmem + TC_SCOL * sb;
 #pragma unroll
@@ -378,6 +398,16 @@ __global__ void __launch_bounds__(TC_BLOCK, 1)
           }
           mma_commit(&bar[B_SFULL + sb]);
           issued_any = true;
+          if (TBUF == 2 && g >= 1 && g + 1 < G) {
+            // the buffer of chunk g - 1 is free once its GEMM1 has completed: load chunk g + 1 into it
+            if (!mbar_wait_abortable(&bar[B_SFULL + (int)((g - 1) & 1)], (uint32_t)(((g - 1) >> 1) & 1), abort_flag)) {
+              ok = false;
+              break;
+            }
+            const int ob = (int)((g + 1) & 1);
+            bulk_load(t1 + ob * L::T1_WORDS, tabs + (size_t)((g + 1) % nch) * L::TB_WORDS, T1_BYTES, &bar[B_T1 + ob]);
+            filled[ob]++;
+          }
         }
       }
       if (!ok) {
@@ -389,32 +419,44 @@ __global__ void __launch_bounds__(TC_BLOCK, 1)
           mbar_wait_bounded(&bar[B_DRAIN1], 0u);
         }
         for (int bb = 0; bb < TBUF; ++bb)
-          if (filled[bb] > consumed[bb]) mbar_wait_bounded(&bar[B_TAB + bb], consumed[bb] & 1u);
+          if (filled[bb] > consumed[bb]) mbar_wait_bounded(&bar[B_T1 + bb], consumed[bb] & 1u);
       }
     }
     __syncwarp();
   } else if (warp == TC_CW + 1) {
-    // ------------------------------------------------------------------ GEMM2 issuer
+    // ------------------------------------------------------------------ GEMM2 tables + GEMM2 issuer
     if (lane == 0) {
       constexpr uint32_t ID2 = IDescTF32<TC_M, NP>::value;
+      uint32_t filled[2] = {0u, 0u}, consumed[2] = {0u, 0u};   // T2 fills per buffer
       bool issued_any = false;
+      for (int f = 0; f < TBUF && f < G; ++f) {
+        bulk_load(t2 + f * L::T2_WORDS, tabs + (size_t)(f % nch) * L::TB_WORDS + L::T1_WORDS, T2_BYTES, &bar[B_T2 + f]);
+        filled[f]++;
+      }
       int64_t g = 0;
       for (int64_t t = 0; t < my_tiles && ok; ++t) {
         const int yb = (int)(t & 1);
         for (int c = 0; c < nch && ok; ++c, ++g) {
           const int tbi = (int)(g % TBUF), vb = (int)(g % VBUF);
           const uint32_t vk = (uint32_t)(g / VBUF);
-          // V of chunk g written (the chunk's S landed before, so its tables are in buffer tbi)
+          if (TBUF == 1 && g >= 1) {
+            // single buffer: refill it with chunk g once GEMM2 of chunk g - 1 has completed
+            if (!mbar_wait_abortable(&bar[B_T2FREE], (uint32_t)((g - 1) & 1), abort_flag)) { ok = false; break; }
+            bulk_load(t2, tabs + (size_t)(g % nch) * L::TB_WORDS + L::T1_WORDS, T2_BYTES, &bar[B_T2]);
+            filled[0]++;
+          }
           if (!mbar_wait_abortable(&bar[B_VFULL + vb], vk & 1u, abort_flag)) { ok = false; break; }
           if (c == 0 && t >= 2 &&
               !mbar_wait_abortable(&bar[B_YFREE + yb], (uint32_t)(((t >> 1) - 1) & 1), abort_flag)) {
             ok = false;
             break;
           }
+          if (!mbar_wait_abortable(&bar[B_T2 + tbi], consumed[tbi] & 1u, abort_flag)) { ok = false; break; }
+          consumed[tbi]++;
           tc_fence_after();
           // GEMM2: Y [128 x NP] += V_d [128 x 16] * G_d [16 x NP]
           const uint32_t vs = su32(vbase + vb * 2 * L::V_WORDS);
-          const uint32_t gs = su32(tb + tbi * L::TB_WORDS) + 4u * 2 * D * TC_QC * KP;
+          const uint32_t gs = su32(t2 + tbi * L::T2_WORDS);
           const uint64_t dv_hi = sdesc(vs, 128, 512), dv_lo = sdesc(vs + 4u * L::V_WORDS, 128, 512);
           const uint64_t dG_hi = sdesc(gs, 128, 512), dG_lo = sdesc(gs + 4u * D * NP * TC_QC, 128, 512);
           const uint32_t ycol = tmem + TC_YCOL0 + 128u * yb;
@@ -430,9 +472,17 @@ __global__ void __launch_bounds__(TC_BLOCK, 1)
             }
           }
           mma_commit(&bar[B_VFREE + vb]);
-          mma_commit(&bar[B_TBFREE + tbi]);
+          mma_commit(&bar[B_T2FREE + tbi]);
           if (c == nch - 1) mma_commit(&bar[B_YFULL + yb]);
           issued_any = true;
+          if (TBUF == 2 && g >= 1 && g + 1 < G) {
+            // the buffer of chunk g - 1 is free once its GEMM2 has completed: load chunk g + 1 into it
+            const int ob = (int)((g + 1) & 1);
+            if (!mbar_wait_abortable(&bar[B_T2FREE + ob], (consumed[ob] - 1) & 1u, abort_flag)) { ok = false; break; }
+            bulk_load(t2 + ob * L::T2_WORDS, tabs + (size_t)((g + 1) % nch) * L::TB_WORDS + L::T1_WORDS, T2_BYTES,
+                      &bar[B_T2 + ob]);
+            filled[ob]++;
+          }
         }
       }
       if (!ok) {
@@ -442,24 +492,28 @@ __global__ void __launch_bounds__(TC_BLOCK, 1)
           mma_commit(&bar[B_DRAIN2]);
           mbar_wait_bounded(&bar[B_DRAIN2], 0u);
         }
+        for (int bb = 0; bb < TBUF; ++bb)
+          if (filled[bb] > consumed[bb]) mbar_wait_bounded(&bar[B_T2 + bb], consumed[bb] & 1u);
       }
     }
     __syncwarp();
   } else {
     // ------------------------------------------------------------------ compute warps
+    // Waits record failure in `ok` (made warp-uniform before the warp-collective TMEM loads) and
+    // dependent work is skipped; loops are left only right after compute_all, so every compute
+    // thread passes the same barriers.
     const int quad = warp & 3, grp = warp >> 2;
     const int m = quad * 32 + lane;
     const uint32_t lane_base = (uint32_t)(quad * 32) << 16;
-    float *qs = qslots + tid;
     if (my_tiles > 0) {
       const int64_t e0 = (int64_t)blockIdx.x * TC_M + m;
-      if (QPRE) prefetch_qdata<D>(qd, E, Q, e0, e0 < E, 0, grp, qs);
+      if (QPRE) tile_qdata_async<D>(qd, Es, Q, blockIdx.x, 0, warp, lane, qslots, &bar[B_QFULL]);
       gather_tile<KP>(E, P, e0, e0 < E, grp, m, masked, rmap, x, u_hi, u_lo);
       fence_proxy_async();
       mbar_arrive(&bar[B_UFULL]);
     }
     int64_t g = 0;
-    for (int64_t t = 0; t < my_tiles && ok; ++t) {
+    for (int64_t t = 0; t < my_tiles; ++t) {
       const int64_t tile = (int64_t)blockIdx.x + t * gridDim.x;
       const int64_t e = tile * TC_M + m;
       const bool valid = e < E;
@@ -467,22 +521,37 @@ __global__ void __launch_bounds__(TC_BLOCK, 1)
       for (int c = 0; c < nch; ++c, ++g) {
         const int sb = (int)(g & 1), vb = (int)(g % VBUF);
         const uint32_t sk = (uint32_t)(g >> 1), vk = (uint32_t)(g / VBUF);
-        if (!mbar_wait_abortable(&bar[B_SFULL + sb], sk & 1u, abort_flag)) { ok = false; break; }
-        tc_fence_after();
+        if (ok) ok = mbar_wait_abortable(&bar[B_SFULL + sb], sk & 1u, abort_flag);
+        ok = __all_sync(0xffffffffu, ok);
         float s[D][TC_PPT];
+        if (ok) {
+          tc_fence_after();
 #pragma unroll
-        for (int d = 0; d < D; ++d) tmem_ld4(tmem + lane_base + TC_SCOL * sb + 16u * d + TC_PPT * grp, s[d]);
-        tc_fence_before();
-        mbar_arrive(&bar[B_SFREE + sb]);
+          for (int d = 0; d < D; ++d) tmem_ld4(tmem + lane_base + TC_SCOL * sb + 16u * d + TC_PPT * grp, s[d]);
+          tc_fence_before();
+          mbar_arrive(&bar[B_SFREE + sb]);
+        }
         float qv[TC_PPT][NQ];
         if (QPRE) {
-          cp_async_wait_all();   // this thread's own copies of chunk g
+          if (ok) ok = mbar_wait_abortable(&bar[B_QFULL], (uint32_t)(g & 1), abort_flag);   // all copies of chunk g
+          if (ok) {
 #pragma unroll
-          for (int j = 0; j < TC_PPT; ++j)
+            for (int j = 0; j < TC_PPT; ++j)
 #pragma unroll
-            for (int k = 0; k < NQ; ++k) qv[j][k] = qs[(j * NQ + k) * TC_COMPUTE];
+              for (int k = 0; k < NQ; ++k) qv[j][k] = qslots[(k * TC_QC + TC_PPT * grp + j) * TC_M + m];
+          }
         } else {
-          load_qdata<D>(qd, E, Q, e, valid, c, grp, qv);
+          load_qdata<D>(qd, Es, Q, e, c, grp, qv);
+        }
+        // every compute thread has read the buffer (and agrees whether to go on)
+        if (!compute_all(ok)) {
+          ok = false;
+          break;
+        }
+        if (QPRE) {
+          if (c + 1 < nch) tile_qdata_async<D>(qd, Es, Q, tile, c + 1, warp, lane, qslots, &bar[B_QFULL]);
+          else if (t + 1 < my_tiles)
+            tile_qdata_async<D>(qd, Es, Q, tile + gridDim.x, 0, warp, lane, qslots, &bar[B_QFULL]);
         }
 #pragma unroll
         for (int j = 0; j < TC_PPT; ++j) {
@@ -495,55 +564,51 @@ __global__ void __launch_bounds__(TC_BLOCK, 1)
             s[0][j] *= qv[j][0];
           }
         }
-        if (QPRE) {
-          // the slots are consumed (qv is in registers and used above): start the next chunk's copies
-          if (c + 1 < nch) {
-            prefetch_qdata<D>(qd, E, Q, e, valid, c + 1, grp, qs);
-          } else if (t + 1 < my_tiles) {
+        // V buffer vb is free once the product of chunk g - VBUF that read it has completed
+        if (g >= VBUF) ok = mbar_wait_abortable(&bar[B_VFREE + vb], (vk - 1) & 1u, abort_flag);
+        if (ok) {
+          float *v_hi = vbase + vb * 2 * L::V_WORDS, *v_lo = v_hi + L::V_WORDS;
+#pragma unroll
+          for (int d = 0; d < D; ++d) {
+            float h4[4], l4[4];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) split_tf32(s[d][j], h4[j], l4[j]);
+            const int o = d * TC_M * TC_QC + canon(m, TC_PPT * grp, TC_QC);
+            st_shared4(v_hi + o, h4[0], h4[1], h4[2], h4[3]);
+            st_shared4(v_lo + o, l4[0], l4[1], l4[2], l4[3]);
+          }
+          fence_proxy_async();
+          mbar_arrive(&bar[B_VFULL + vb]);
+          if (c == nch - 1 && t + 1 < my_tiles) {
+            // the next tile's inputs: U is free (this chunk's S landed, so every product reading U is done)
             const int64_t e1 = (tile + gridDim.x) * TC_M + m;
-            prefetch_qdata<D>(qd, E, Q, e1, e1 < E, 0, grp, qs);
+            gather_tile<KP>(E, P, e1, e1 < E, grp, m, masked, rmap, x, u_hi, u_lo);
+            fence_proxy_async();
+            mbar_arrive(&bar[B_UFULL]);
           }
         }
-        // V buffer vb is free once the product of chunk g - VBUF that read it has completed
-        if (g >= VBUF && !mbar_wait_abortable(&bar[B_VFREE + vb], (vk - 1) & 1u, abort_flag)) {
-          ok = false;
-          break;
-        }
-        float *v_hi = vbase + vb * 2 * L::V_WORDS, *v_lo = v_hi + L::V_WORDS;
-#pragma unroll
-        for (int d = 0; d < D; ++d) {
-          float h4[4], l4[4];
-#pragma unroll
-          for (int j = 0; j < 4; ++j) split_tf32(s[d][j], h4[j], l4[j]);
-          const int o = d * TC_M * TC_QC + canon(m, TC_PPT * grp, TC_QC);
-          st_shared4(v_hi + o, h4[0], h4[1], h4[2], h4[3]);
-          st_shared4(v_lo + o, l4[0], l4[1], l4[2], l4[3]);
-        }
-        fence_proxy_async();
-        mbar_arrive(&bar[B_VFULL + vb]);
-        if (c == nch - 1 && t + 1 < my_tiles) {
-          // the next tile's inputs: U is free (this chunk's S landed, so every product reading U is done)
-          const int64_t e1 = (tile + gridDim.x) * TC_M + m;
-          gather_tile<KP>(E, P, e1, e1 < E, grp, m, masked, rmap, x, u_hi, u_lo);
-          fence_proxy_async();
-          mbar_arrive(&bar[B_UFULL]);
-        }
       }
-      if (!ok) break;
       // epilogue of tile t: this thread's quarter of the element's output nodes, TMEM -> element vectors
-      if (!mbar_wait_abortable(&bar[B_YFULL + yb], (uint32_t)((t >> 1) & 1), abort_flag)) { ok = false; break; }
-      tc_fence_after();
+      if (ok) ok = mbar_wait_abortable(&bar[B_YFULL + yb], (uint32_t)((t >> 1) & 1), abort_flag);
+      ok = __all_sync(0xffffffffu, ok);
+      if (ok) {
+        tc_fence_after();
 #pragma unroll
-      for (int j0 = 0; j0 < NP / TC_GROUPS; j0 += 4) {
-        const int n0 = grp * (NP / TC_GROUPS) + j0;
-        float y4[4];
-        tmem_ld4(tmem + lane_base + TC_YCOL0 + 128u * yb + (uint32_t)n0, y4);
+        for (int j0 = 0; j0 < NP / TC_GROUPS; j0 += 4) {
+          const int n0 = grp * (NP / TC_GROUPS) + j0;
+          float y4[4];
+          tmem_ld4(tmem + lane_base + TC_YCOL0 + 128u * yb + (uint32_t)n0, y4);
 #pragma unroll
-        for (int j = 0; j < 4; ++j)
-          if (valid && n0 + j < P) Ye[(int64_t)(n0 + j) * E + e] = y4[j];
+          for (int j = 0; j < 4; ++j)
+            if (valid && n0 + j < P) Ye[(int64_t)(n0 + j) * E + e] = y4[j];
+        }
+        tc_fence_before();
+        mbar_arrive(&bar[B_YFREE + yb]);
       }
-      tc_fence_before();
-      mbar_arrive(&bar[B_YFREE + yb]);
+      if (!compute_all(ok)) {
+        ok = false;
+        break;
+      }
     }
     if (QPRE) cp_async_wait_all();   // no copy into shared memory may outlive the block
     if (!ok) {
@@ -613,8 +678,8 @@ static int launch_tc(ceed_nt_t h, const float *tabs, const float *qd, const doub
   if (sms == 0) CEED_CUDA_CHECK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device));
   const int64_t ntiles = (h->E + TC_M - 1) / TC_M;
   const unsigned grid = (unsigned)std::min<int64_t>(ntiles, (int64_t)sms);
-  nt_tc_kernel<D, KP, NP, TBUF, VBUF, QPRE><<<grid, TC_BLOCK, SMEM, s>>>(h->E, h->P, h->Q, h->tc_nchunk, h->d_rmap, x,
-                                                                        tabs, qd, Ye, masked, h->d_err);
+  nt_tc_kernel<D, KP, NP, TBUF, VBUF, QPRE><<<grid, TC_BLOCK, SMEM, s>>>(h->E, h->Es, h->P, h->Q, h->tc_nchunk,
+                                                                        h->d_rmap, x, tabs, qd, Ye, masked, h->d_err);
   CEED_CUDA_CHECK(cudaGetLastError());
   return CEED_OK;
 }
@@ -626,7 +691,7 @@ struct TcBufs {
   static constexpr size_t lim = 227 * 1024;
   static constexpr size_t base = 8ull * TC_M * KP + TC_NBAR * 8 + 16;
   static constexpr size_t tbw = 4ull * chunk_words(D, KP, NP), vw = 8ull * D * TC_M * TC_QC;
-  static constexpr size_t qw = 4ull * TC_PPT * (D == 3 ? 6 : 1) * TC_COMPUTE;
+  static constexpr size_t qw = 4ull * (D == 3 ? 6 : 1) * TC_QC * TC_M;
   static constexpr int QPRE = base + tbw + vw + qw <= lim ? 1 : 0;
   static constexpr int TBUF = base + 2 * tbw + vw + QPRE * qw <= lim ? 2 : 1;
   static constexpr int VBUF = base + TBUF * tbw + 2 * vw + QPRE * qw <= lim ? 2 : 1;
