@@ -70,17 +70,33 @@ struct IDescTF32 {
                                     ((uint32_t)(M >> 4) << 24);
 };
 
-__device__ __forceinline__ void mma_tf32(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t accum) {
+// The issuing warps run their loops with all 32 lanes (so descriptors stay warp-uniform); only the
+// lane with `leader` set issues the tensor-core instruction, the commit or the copy.
+__device__ __forceinline__ void mma_tf32(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t accum,
+                                         uint32_t leader) {
   asm volatile(
-      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-      " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
-      "l"(a), "l"(b), "r"(idesc), "r"(accum)
+      "{\n .reg .pred p, l;\n setp.ne.b32 p, %4, 0;\n setp.ne.b32 l, %5, 0;\n"
+      " @l tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
+      "l"(a), "l"(b), "r"(idesc), "r"(accum), "r"(leader)
       : "memory");
 }
 
-__device__ __forceinline__ void mma_commit(uint64_t *bar) {
-  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(su32(bar))
-               : "memory");
+// Same with the A operand in tensor memory (row m of A in lane m, one TF32 value per column).
+__device__ __forceinline__ void mma_tf32_ts(uint32_t d_tmem, uint32_t a_tmem, uint64_t b, uint32_t idesc,
+                                            uint32_t accum, uint32_t leader) {
+  asm volatile(
+      "{\n .reg .pred p, l;\n setp.ne.b32 p, %4, 0;\n setp.ne.b32 l, %5, 0;\n"
+      " @l tcgen05.mma.cta_group::1.kind::tf32 [%0], [%1], %2, %3, p;\n}\n" ::"r"(d_tmem),
+      "r"(a_tmem), "l"(b), "r"(idesc), "r"(accum), "r"(leader)
+      : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t *bar, uint32_t leader) {
+  asm volatile(
+      "{\n .reg .pred l;\n setp.ne.b32 l, %1, 0;\n"
+      " @l tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n}\n" ::"r"(su32(bar)),
+      "r"(leader)
+      : "memory");
 }
 
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
@@ -101,6 +117,15 @@ __device__ __forceinline__ void tmem_ld4(uint32_t taddr, float (&v)[4]) {
   v[1] = __uint_as_float(r1);
   v[2] = __uint_as_float(r2);
   v[3] = __uint_as_float(r3);
+}
+
+// 4 consecutive 32-bit TMEM columns of this thread's lane from registers; waits for the store.
+__device__ __forceinline__ void tmem_st4(uint32_t taddr, const float (&v)[4]) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x4.b32 [%0], {%1, %2, %3, %4};\n"
+      "tcgen05.wait::st.sync.aligned;\n" ::"r"(taddr),
+      "r"(__float_as_uint(v[0])), "r"(__float_as_uint(v[1])), "r"(__float_as_uint(v[2])), "r"(__float_as_uint(v[3]))
+      : "memory");
 }
 
 __device__ __forceinline__ void bulk_load(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
@@ -148,28 +173,29 @@ constexpr int TC_BLOCK = TC_COMPUTE + 64;
 constexpr int TC_GROUPS = TC_CW / 4;            // warps per TMEM lane quadrant
 constexpr int TC_PPT = TC_QC / TC_GROUPS;       // points of a chunk per compute thread
 static_assert(TC_PPT == 4, "one float4 of points per thread and direction");
+// TMEM columns: S buffer s at 64 s (16 D used); V buffer v at 128 + 96 v (hi: 16 d + point, lo: 48 +
+// 16 d + point); Y buffer y at 320 + 96 y (NP <= 96 used).
 constexpr uint32_t TC_TMEM_ALLOC = 512;
-constexpr uint32_t TC_SCOL = 64;                // S buffer s at TMEM column 64 s
-constexpr uint32_t TC_YCOL0 = 256;              // Y buffer y at TMEM column 256 + 128 y
+constexpr uint32_t TC_SCOL = 64;
+constexpr uint32_t TC_VCOL0 = 128, TC_VSTRIDE = 96, TC_VLO = 48;
+constexpr uint32_t TC_YCOL0 = 320, TC_YSTRIDE = 96;
 
 // Shared-memory map of one block.  U: the tile's element inputs (hi, lo); T1[TBUF], T2[TBUF]: the
-// GEMM1 and GEMM2 operands of a table chunk;
-// V[VBUF]: the pointwise results (hi, lo); QS: the tile's quadrature data of the next chunk
+// GEMM1 and GEMM2 operands of a table chunk; QS: the tile's quadrature data of the next chunk
 // ([value][point][element], when QPRE); then the mbarriers, the TMEM address and an abort flag.
-template <int D, int KP, int NP, int TBUF, int VBUF, int QPRE>
+// (The pointwise results V, the A operand of GEMM2, live in tensor memory.)
+template <int D, int KP, int NP, int TBUF, int QPRE>
 struct TcLayout {
   static constexpr int U_WORDS = TC_M * KP;                // per hi/lo
   static constexpr int T1_WORDS = gt_words(D, KP);         // one GEMM1 table buffer
   static constexpr int T2_WORDS = g_words(D, NP);          // one GEMM2 table buffer
   static constexpr int TB_WORDS = T1_WORDS + T2_WORDS;     // one chunk of the global table image
-  static constexpr int V_WORDS = D * TC_M * TC_QC;         // per hi/lo
   static constexpr int QS_WORDS = QPRE * (D == 3 ? 6 : 1) * TC_QC * TC_M;   // [value][point][element]
   static constexpr size_t U_HI = 0;
   static constexpr size_t U_LO = U_HI + 4 * (size_t)U_WORDS;
   static constexpr size_t T1 = U_LO + 4 * (size_t)U_WORDS;
   static constexpr size_t T2 = T1 + 4 * (size_t)T1_WORDS * TBUF;
-  static constexpr size_t V = T2 + 4 * (size_t)T2_WORDS * TBUF;   // buffer v: hi at V + 8 V_WORDS v, lo + 4 V_WORDS
-  static constexpr size_t QS = V + 8 * (size_t)V_WORDS * VBUF;
+  static constexpr size_t QS = T2 + 4 * (size_t)T2_WORDS * TBUF;
   static constexpr size_t BARS = QS + 4 * (size_t)QS_WORDS;
   static constexpr size_t BYTES = BARS + TC_NBAR * 8 + 16;
   static_assert(BYTES <= 227 * 1024, "shared memory");
@@ -220,6 +246,11 @@ __device__ __forceinline__ bool compute_all(bool v) {
       : "r"((uint32_t)v), "n"(TC_COMPUTE)
       : "memory");
   return r != 0;
+}
+
+// Bounded wait by a whole warp, with a warp-uniform result.
+__device__ __forceinline__ bool wait_warp(uint64_t *bar, uint32_t parity, volatile int *abort_flag) {
+  return __all_sync(0xffffffffu, mbar_wait_abortable(bar, parity, abort_flag));
 }
 
 // The tile's element inputs, split into TF32 hi/lo, written to the canonical layout (row m,
@@ -299,8 +330,9 @@ __device__ __forceinline__ void tile_qdata_async(const float *__restrict__ qd, i
 }
 
 // The fused kernel, persistent (block b takes tiles b, b + gridDim.x, ...) and warp-specialized.
-//   warp 16 (one thread): streams the GEMM1 operand of each table chunk in (bulk copies), issues GEMM1
-//   warp 17 (one thread): the same for GEMM2
+//   warp 16: streams the GEMM1 operand of each table chunk in (bulk copies), issues GEMM1
+//   warp 17: the same for GEMM2
+// (the issuing warps run with all lanes; one lane issues each tensor-core instruction and copy)
 //   warps 0-15: gather inputs, apply the pointwise operator, write the element vectors
 // They hand buffers to each other through mbarriers (the tensor core signals completion through
 // tcgen05.commit).  S (TMEM) and Y (TMEM) are double-buffered, V and the tables when shared memory
@@ -309,19 +341,19 @@ __device__ __forceinline__ void tile_qdata_async(const float *__restrict__ qd, i
 // points 4 grp .. 4 grp + 3 of each chunk, every fourth input column group and a quarter of the
 // output nodes.  With QPRE, every compute thread copies its quadrature data for the next chunk into
 // its own shared-memory slots with cp.async while it works on the current one.
-template <int D, int KP, int NP, int TBUF, int VBUF, int QPRE>
+template <int D, int KP, int NP, int TBUF, int QPRE>
 __global__ void __launch_bounds__(TC_BLOCK, 1)
     nt_tc_kernel(int64_t E, int64_t Es, int P, int Q, int nch, const uint32_t *__restrict__ rmap,
                  const double *__restrict__ x, const float *__restrict__ tabs, const float *__restrict__ qd,
                  float *__restrict__ Ye, int masked, int *err) {
-  using L = TcLayout<D, KP, NP, TBUF, VBUF, QPRE>;
+  using L = TcLayout<D, KP, NP, TBUF, QPRE>;
   constexpr int NQ = D == 3 ? 6 : 1;
+  static_assert(NP <= (int)TC_YSTRIDE && 16 * D <= (int)TC_VLO, "tensor memory map");
   extern __shared__ __align__(1024) unsigned char tc_smem[];
   float *u_hi = reinterpret_cast<float *>(tc_smem + L::U_HI);
   float *u_lo = reinterpret_cast<float *>(tc_smem + L::U_LO);
   float *t1 = reinterpret_cast<float *>(tc_smem + L::T1);
   float *t2 = reinterpret_cast<float *>(tc_smem + L::T2);
-  float *vbase = reinterpret_cast<float *>(tc_smem + L::V);
   float *qslots = reinterpret_cast<float *>(tc_smem + L::QS);
   uint64_t *bar = reinterpret_cast<uint64_t *>(tc_smem + L::BARS);
   uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(tc_smem + L::BARS + TC_NBAR * 8);
@@ -356,14 +388,15 @@ __global__ void __launch_bounds__(TC_BLOCK, 1)
 
   if (warp == TC_CW) {
     // ------------------------------------------------------------------ GEMM1 tables + GEMM1 issuer
-    if (lane == 0) {
+    {
+      const uint32_t leader = lane == 0 ? 1u : 0u;
       constexpr uint32_t ID1 = IDescTF32<TC_M, 16 * D>::value;
       constexpr uint32_t SBO1 = (KP / 4) * 128;
       const uint64_t du_hi = sdesc(su32(u_hi), 128, SBO1), du_lo = sdesc(su32(u_lo), 128, SBO1);
       uint32_t filled[2] = {0u, 0u}, consumed[2] = {0u, 0u};   // T1 fills per buffer
       bool issued_any = false;
       for (int f = 0; f < TBUF && f < G; ++f) {
-        bulk_load(t1 + f * L::T1_WORDS, tabs + (size_t)(f % nch) * L::TB_WORDS, T1_BYTES, &bar[B_T1 + f]);
+        if (leader) bulk_load(t1 + f * L::T1_WORDS, tabs + (size_t)(f % nch) * L::TB_WORDS, T1_BYTES, &bar[B_T1 + f]);
         filled[f]++;
       }
       int64_t g = 0;
@@ -373,17 +406,17 @@ __global__ void __launch_bounds__(TC_BLOCK, 1)
           const uint32_t sk = (uint32_t)(g >> 1);
           if (TBUF == 1 && g >= 1) {
             // single buffer: refill it with chunk g once GEMM1 of chunk g - 1 has completed
-            if (!mbar_wait_abortable(&bar[B_SFULL + (int)((g - 1) & 1)], (uint32_t)(((g - 1) >> 1) & 1), abort_flag)) {
+            if (!wait_warp(&bar[B_SFULL + (int)((g - 1) & 1)], (uint32_t)(((g - 1) >> 1) & 1), abort_flag)) {
               ok = false;
               break;
             }
-            bulk_load(t1, tabs + (size_t)(g % nch) * L::TB_WORDS, T1_BYTES, &bar[B_T1]);
+            if (leader) bulk_load(t1, tabs + (size_t)(g % nch) * L::TB_WORDS, T1_BYTES, &bar[B_T1]);
             filled[0]++;
           }
-          if (!mbar_wait_abortable(&bar[B_T1 + tbi], consumed[tbi] & 1u, abort_flag)) { ok = false; break; }
+          if (!wait_warp(&bar[B_T1 + tbi], consumed[tbi] & 1u, abort_flag)) { ok = false; break; }
           consumed[tbi]++;
-          if (c == 0 && !mbar_wait_abortable(&bar[B_UFULL], (uint32_t)(t & 1), abort_flag)) { ok = false; break; }
-          if (g >= 2 && !mbar_wait_abortable(&bar[B_SFREE + sb], (sk - 1) & 1u, abort_flag)) { ok = false; break; }
+          if (c == 0 && !wait_warp(&bar[B_UFULL], (uint32_t)(t & 1), abort_flag)) { ok = false; break; }
+          if (g >= 2 && !wait_warp(&bar[B_SFREE + sb], (sk - 1) & 1u, abort_flag)) { ok = false; break; }
           tc_fence_after();
           // GEMM1: S [128 x 16 D] = U [128 x KP] * GT^T (all directions in one N = 16 D product)
           const uint32_t tbs = su32(t1 + tbi * L::T1_WORDS);
@@ -392,30 +425,32 @@ __global__ void __launch_bounds__(TC_BLOCK, 1)
 #pragma unroll
           for (int ks = 0; ks < KP / 8; ++ks) {
             const uint64_t o = (uint64_t)(ks * 256) >> 4;
-            mma_tf32(dcol, du_hi + o, dg_hi + o, ID1, ks > 0);
-            mma_tf32(dcol, du_hi + o, dg_lo + o, ID1, 1);
-            mma_tf32(dcol, du_lo + o, dg_hi + o, ID1, 1);
+            mma_tf32(dcol, du_hi + o, dg_hi + o, ID1, ks > 0, leader);
+            mma_tf32(dcol, du_hi + o, dg_lo + o, ID1, 1, leader);
+            mma_tf32(dcol, du_lo + o, dg_hi + o, ID1, 1, leader);
           }
-          mma_commit(&bar[B_SFULL + sb]);
+          mma_commit(&bar[B_SFULL + sb], leader);
           issued_any = true;
           if (TBUF == 2 && g >= 1 && g + 1 < G) {
             // the buffer of chunk g - 1 is free once its GEMM1 has completed: load chunk g + 1 into it
-            if (!mbar_wait_abortable(&bar[B_SFULL + (int)((g - 1) & 1)], (uint32_t)(((g - 1) >> 1) & 1), abort_flag)) {
+            if (!wait_warp(&bar[B_SFULL + (int)((g - 1) & 1)], (uint32_t)(((g - 1) >> 1) & 1), abort_flag)) {
               ok = false;
               break;
             }
             const int ob = (int)((g + 1) & 1);
-            bulk_load(t1 + ob * L::T1_WORDS, tabs + (size_t)((g + 1) % nch) * L::TB_WORDS, T1_BYTES, &bar[B_T1 + ob]);
+            if (leader) bulk_load(t1 + ob * L::T1_WORDS, tabs + (size_t)((g + 1) % nch) * L::TB_WORDS, T1_BYTES, &bar[B_T1 + ob]);
             filled[ob]++;
           }
         }
       }
       if (!ok) {
-        *abort_flag = 1;
-        atomicExch(err, (int)CEED_ERR_TIMEOUT);
+        if (leader) {
+          *abort_flag = 1;
+          atomicExch(err, (int)CEED_ERR_TIMEOUT);
+        }
         // let this thread's operations in flight finish before TMEM and shared memory are released
         if (issued_any) {
-          mma_commit(&bar[B_DRAIN1]);
+          mma_commit(&bar[B_DRAIN1], leader);
           mbar_wait_bounded(&bar[B_DRAIN1], 0u);
         }
         for (int bb = 0; bb < TBUF; ++bb)
@@ -425,71 +460,73 @@ __global__ void __launch_bounds__(TC_BLOCK, 1)
     __syncwarp();
   } else if (warp == TC_CW + 1) {
     // ------------------------------------------------------------------ GEMM2 tables + GEMM2 issuer
-    if (lane == 0) {
+    {
+      const uint32_t leader = lane == 0 ? 1u : 0u;
       constexpr uint32_t ID2 = IDescTF32<TC_M, NP>::value;
       uint32_t filled[2] = {0u, 0u}, consumed[2] = {0u, 0u};   // T2 fills per buffer
       bool issued_any = false;
       for (int f = 0; f < TBUF && f < G; ++f) {
-        bulk_load(t2 + f * L::T2_WORDS, tabs + (size_t)(f % nch) * L::TB_WORDS + L::T1_WORDS, T2_BYTES, &bar[B_T2 + f]);
+        if (leader) bulk_load(t2 + f * L::T2_WORDS, tabs + (size_t)(f % nch) * L::TB_WORDS + L::T1_WORDS, T2_BYTES, &bar[B_T2 + f]);
         filled[f]++;
       }
       int64_t g = 0;
       for (int64_t t = 0; t < my_tiles && ok; ++t) {
         const int yb = (int)(t & 1);
         for (int c = 0; c < nch && ok; ++c, ++g) {
-          const int tbi = (int)(g % TBUF), vb = (int)(g % VBUF);
-          const uint32_t vk = (uint32_t)(g / VBUF);
+          const int tbi = (int)(g % TBUF), vb = (int)(g & 1);
+          const uint32_t vk = (uint32_t)(g >> 1);
           if (TBUF == 1 && g >= 1) {
             // single buffer: refill it with chunk g once GEMM2 of chunk g - 1 has completed
-            if (!mbar_wait_abortable(&bar[B_T2FREE], (uint32_t)((g - 1) & 1), abort_flag)) { ok = false; break; }
-            bulk_load(t2, tabs + (size_t)(g % nch) * L::TB_WORDS + L::T1_WORDS, T2_BYTES, &bar[B_T2]);
+            if (!wait_warp(&bar[B_T2FREE], (uint32_t)((g - 1) & 1), abort_flag)) { ok = false; break; }
+            if (leader) bulk_load(t2, tabs + (size_t)(g % nch) * L::TB_WORDS + L::T1_WORDS, T2_BYTES, &bar[B_T2]);
             filled[0]++;
           }
-          if (!mbar_wait_abortable(&bar[B_VFULL + vb], vk & 1u, abort_flag)) { ok = false; break; }
+          if (!wait_warp(&bar[B_VFULL + vb], vk & 1u, abort_flag)) { ok = false; break; }
           if (c == 0 && t >= 2 &&
-              !mbar_wait_abortable(&bar[B_YFREE + yb], (uint32_t)(((t >> 1) - 1) & 1), abort_flag)) {
+              !wait_warp(&bar[B_YFREE + yb], (uint32_t)(((t >> 1) - 1) & 1), abort_flag)) {
             ok = false;
             break;
           }
-          if (!mbar_wait_abortable(&bar[B_T2 + tbi], consumed[tbi] & 1u, abort_flag)) { ok = false; break; }
+          if (!wait_warp(&bar[B_T2 + tbi], consumed[tbi] & 1u, abort_flag)) { ok = false; break; }
           consumed[tbi]++;
           tc_fence_after();
-          // GEMM2: Y [128 x NP] += V_d [128 x 16] * G_d [16 x NP]
-          const uint32_t vs = su32(vbase + vb * 2 * L::V_WORDS);
+          // GEMM2: Y [128 x NP] += V_d [128 x 16] * G_d [16 x NP], V_d read from tensor memory
+          const uint32_t va = tmem + TC_VCOL0 + TC_VSTRIDE * vb;
           const uint32_t gs = su32(t2 + tbi * L::T2_WORDS);
-          const uint64_t dv_hi = sdesc(vs, 128, 512), dv_lo = sdesc(vs + 4u * L::V_WORDS, 128, 512);
           const uint64_t dG_hi = sdesc(gs, 128, 512), dG_lo = sdesc(gs + 4u * D * NP * TC_QC, 128, 512);
-          const uint32_t ycol = tmem + TC_YCOL0 + 128u * yb;
+          const uint32_t ycol = tmem + TC_YCOL0 + TC_YSTRIDE * yb;
 #pragma unroll
           for (int d = 0; d < D; ++d) {
 #pragma unroll
             for (int ks = 0; ks < TC_QC / 8; ++ks) {
-              const uint64_t oa = (uint64_t)(d * TC_M * TC_QC * 4 + ks * 256) >> 4;
+              const uint32_t ao = 16u * d + 8u * ks;
               const uint64_t ob = (uint64_t)(d * NP * TC_QC * 4 + ks * 256) >> 4;
-              mma_tf32(ycol, dv_hi + oa, dG_hi + ob, ID2, (c > 0 || d > 0 || ks > 0) ? 1u : 0u);
-              mma_tf32(ycol, dv_hi + oa, dG_lo + ob, ID2, 1);
-              mma_tf32(ycol, dv_lo + oa, dG_hi + ob, ID2, 1);
+              mma_tf32_ts(ycol, va + ao, dG_hi + ob, ID2, (c > 0 || d > 0 || ks > 0) ? 1u : 0u, leader);
+              mma_tf32_ts(ycol, va + ao, dG_lo + ob, ID2, 1, leader);
+              mma_tf32_ts(ycol, va + TC_VLO + ao, dG_hi + ob, ID2, 1, leader);
             }
           }
-          mma_commit(&bar[B_VFREE + vb]);
-          mma_commit(&bar[B_T2FREE + tbi]);
-          if (c == nch - 1) mma_commit(&bar[B_YFULL + yb]);
+          mma_commit(&bar[B_VFREE + vb], leader);
+          mma_commit(&bar[B_T2FREE + tbi], leader);
+          if (c == nch - 1) mma_commit(&bar[B_YFULL + yb], leader);
           issued_any = true;
           if (TBUF == 2 && g >= 1 && g + 1 < G) {
             // the buffer of chunk g - 1 is free once its GEMM2 has completed: load chunk g + 1 into it
             const int ob = (int)((g + 1) & 1);
-            if (!mbar_wait_abortable(&bar[B_T2FREE + ob], (consumed[ob] - 1) & 1u, abort_flag)) { ok = false; break; }
-            bulk_load(t2 + ob * L::T2_WORDS, tabs + (size_t)((g + 1) % nch) * L::TB_WORDS + L::T1_WORDS, T2_BYTES,
+            if (!wait_warp(&bar[B_T2FREE + ob], (consumed[ob] - 1) & 1u, abort_flag)) { ok = false; break; }
+            if (leader) bulk_load(t2 + ob * L::T2_WORDS, tabs + (size_t)((g + 1) % nch) * L::TB_WORDS + L::T1_WORDS, T2_BYTES,
                       &bar[B_T2 + ob]);
             filled[ob]++;
           }
         }
       }
       if (!ok) {
-        *abort_flag = 1;
-        atomicExch(err, (int)CEED_ERR_TIMEOUT);
+        if (leader) {
+          *abort_flag = 1;
+          atomicExch(err, (int)CEED_ERR_TIMEOUT);
+        }
         if (issued_any) {
-          mma_commit(&bar[B_DRAIN2]);
+          mma_commit(&bar[B_DRAIN2], leader);
           mbar_wait_bounded(&bar[B_DRAIN2], 0u);
         }
         for (int bb = 0; bb < TBUF; ++bb)
@@ -519,8 +556,8 @@ __global__ void __launch_bounds__(TC_BLOCK, 1)
       const bool valid = e < E;
       const int yb = (int)(t & 1);
       for (int c = 0; c < nch; ++c, ++g) {
-        const int sb = (int)(g & 1), vb = (int)(g % VBUF);
-        const uint32_t sk = (uint32_t)(g >> 1), vk = (uint32_t)(g / VBUF);
+        const int sb = (int)(g & 1), vb = (int)(g & 1);
+        const uint32_t sk = (uint32_t)(g >> 1), vk = (uint32_t)(g >> 1);
         if (ok) ok = mbar_wait_abortable(&bar[B_SFULL + sb], sk & 1u, abort_flag);
         ok = __all_sync(0xffffffffu, ok);
         float s[D][TC_PPT];
@@ -564,20 +601,21 @@ __global__ void __launch_bounds__(TC_BLOCK, 1)
             s[0][j] *= qv[j][0];
           }
         }
-        // V buffer vb is free once the product of chunk g - VBUF that read it has completed
-        if (g >= VBUF) ok = mbar_wait_abortable(&bar[B_VFREE + vb], (vk - 1) & 1u, abort_flag);
+        // V buffer vb is free once the product of chunk g - 2 that read it has completed
+        if (g >= 2 && ok) ok = mbar_wait_abortable(&bar[B_VFREE + vb], (vk - 1) & 1u, abort_flag);
+        ok = __all_sync(0xffffffffu, ok);
         if (ok) {
-          float *v_hi = vbase + vb * 2 * L::V_WORDS, *v_lo = v_hi + L::V_WORDS;
+          tc_fence_after();
+          const uint32_t vcol = tmem + lane_base + TC_VCOL0 + TC_VSTRIDE * vb + TC_PPT * grp;
 #pragma unroll
           for (int d = 0; d < D; ++d) {
             float h4[4], l4[4];
 #pragma unroll
             for (int j = 0; j < 4; ++j) split_tf32(s[d][j], h4[j], l4[j]);
-            const int o = d * TC_M * TC_QC + canon(m, TC_PPT * grp, TC_QC);
-            st_shared4(v_hi + o, h4[0], h4[1], h4[2], h4[3]);
-            st_shared4(v_lo + o, l4[0], l4[1], l4[2], l4[3]);
+            tmem_st4(vcol + 16u * d, h4);
+            tmem_st4(vcol + TC_VLO + 16u * d, l4);
           }
-          fence_proxy_async();
+          tc_fence_before();
           mbar_arrive(&bar[B_VFULL + vb]);
           if (c == nch - 1 && t + 1 < my_tiles) {
             // the next tile's inputs: U is free (this chunk's S landed, so every product reading U is done)
@@ -597,7 +635,7 @@ __global__ void __launch_bounds__(TC_BLOCK, 1)
         for (int j0 = 0; j0 < NP / TC_GROUPS; j0 += 4) {
           const int n0 = grp * (NP / TC_GROUPS) + j0;
           float y4[4];
-          tmem_ld4(tmem + lane_base + TC_YCOL0 + 128u * yb + (uint32_t)n0, y4);
+          tmem_ld4(tmem + lane_base + TC_YCOL0 + TC_YSTRIDE * yb + (uint32_t)n0, y4);
 #pragma unroll
           for (int j = 0; j < 4; ++j)
             if (valid && n0 + j < P) Ye[(int64_t)(n0 + j) * E + e] = y4[j];
@@ -660,16 +698,16 @@ static void build_tables(const std::vector<double> &tab, int D, int P, int Q, in
   }
 }
 
-template <int D, int KP, int NP, int TBUF, int VBUF, int QPRE>
+template <int D, int KP, int NP, int TBUF, int QPRE>
 static int launch_tc(ceed_nt_t h, const float *tabs, const float *qd, const double *x, float *Ye, int masked,
                      cudaStream_t s) {
-  using L = TcLayout<D, KP, NP, TBUF, VBUF, QPRE>;
+  using L = TcLayout<D, KP, NP, TBUF, QPRE>;
   // one block per SM: the block holds 512 TMEM columns (S and Y double-buffered)
   constexpr size_t SMEM = L::BYTES > 116 * 1024 ? L::BYTES : 116 * 1024;
   static uint64_t attr_set = 0;
   const uint64_t bit = 1ull << (h->device & 63);
   if (!(attr_set & bit)) {
-    CEED_CUDA_CHECK(cudaFuncSetAttribute(nt_tc_kernel<D, KP, NP, TBUF, VBUF, QPRE>,
+    CEED_CUDA_CHECK(cudaFuncSetAttribute(nt_tc_kernel<D, KP, NP, TBUF, QPRE>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM));
     attr_set |= bit;
   }
@@ -678,23 +716,22 @@ static int launch_tc(ceed_nt_t h, const float *tabs, const float *qd, const doub
   if (sms == 0) CEED_CUDA_CHECK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device));
   const int64_t ntiles = (h->E + TC_M - 1) / TC_M;
   const unsigned grid = (unsigned)std::min<int64_t>(ntiles, (int64_t)sms);
-  nt_tc_kernel<D, KP, NP, TBUF, VBUF, QPRE><<<grid, TC_BLOCK, SMEM, s>>>(h->E, h->Es, h->P, h->Q, h->tc_nchunk,
+  nt_tc_kernel<D, KP, NP, TBUF, QPRE><<<grid, TC_BLOCK, SMEM, s>>>(h->E, h->Es, h->P, h->Q, h->tc_nchunk,
                                                                         h->d_rmap, x, tabs, qd, Ye, masked, h->d_err);
   CEED_CUDA_CHECK(cudaGetLastError());
   return CEED_OK;
 }
 
-// Buffering that fits in shared memory, in order of benefit: quadrature-data prefetch slots, a
-// second table buffer (the tables of the next chunk stream in during the current one), a second V.
+// Buffering that fits in shared memory, in order of benefit: the quadrature-data prefetch buffer,
+// then a second table buffer (the tables of the next chunk stream in during the current one).
 template <int D, int KP, int NP>
 struct TcBufs {
   static constexpr size_t lim = 227 * 1024;
   static constexpr size_t base = 8ull * TC_M * KP + TC_NBAR * 8 + 16;
-  static constexpr size_t tbw = 4ull * chunk_words(D, KP, NP), vw = 8ull * D * TC_M * TC_QC;
+  static constexpr size_t tbw = 4ull * chunk_words(D, KP, NP);
   static constexpr size_t qw = 4ull * (D == 3 ? 6 : 1) * TC_QC * TC_M;
-  static constexpr int QPRE = base + tbw + vw + qw <= lim ? 1 : 0;
-  static constexpr int TBUF = base + 2 * tbw + vw + QPRE * qw <= lim ? 2 : 1;
-  static constexpr int VBUF = base + TBUF * tbw + 2 * vw + QPRE * qw <= lim ? 2 : 1;
+  static constexpr int QPRE = base + tbw + qw <= lim ? 1 : 0;
+  static constexpr int TBUF = base + 2 * tbw + QPRE * qw <= lim ? 2 : 1;
 };
 
 template <int PP>
@@ -703,8 +740,8 @@ static int dispatch_p(ceed_nt_t h, int op, const float *qd, const double *x, flo
   const float *tabs = h->d_tc_tab[op == CEED_OP_MASS ? 0 : 1];
   using B1 = TcBufs<1, KP, NP>;
   using B3 = TcBufs<3, KP, NP>;
-  return op == CEED_OP_MASS ? launch_tc<1, KP, NP, B1::TBUF, B1::VBUF, B1::QPRE>(h, tabs, qd, x, Ye, masked, s)
-                            : launch_tc<3, KP, NP, B3::TBUF, B3::VBUF, B3::QPRE>(h, tabs, qd, x, Ye, masked, s);
+  return op == CEED_OP_MASS ? launch_tc<1, KP, NP, B1::TBUF, B1::QPRE>(h, tabs, qd, x, Ye, masked, s)
+                            : launch_tc<3, KP, NP, B3::TBUF, B3::QPRE>(h, tabs, qd, x, Ye, masked, s);
 }
 
 }  // namespace
