@@ -40,7 +40,12 @@ FP64_NOMINAL_TFLOPS = 1.25      # GB300 dense FP64 (profiling recipe's nominal t
 PROFILED_TRAFFIC_PER_LAUNCH = {
     # profiles/apply_kernel_p7_48cube_ncu.md: 503.70 MB read + 66.40 MB written per 13,824-element launch
     "apply_kernel<8,8,DIFFUSION,double,double,stage=0>[ne=1]": 570.09e6 * 32768 / 13824,
+    # same file: 503.84 MB read + 67.13 MB written per 13,824-element launch
+    "apply_kernel<8,8,DIFFUSION,double,double,stage=0>[ne=2]": 570.97e6 * 32768 / 13824,
 }
+# DRAM bytes (read + write) of one launch of the tensor-core tetrahedral kernel on the 48^3 x 6
+# degree-4 workload (profiles/nt_tc_kernel_p4_tet48_ncu.md): 2143.84 MB read + 90.39 MB written
+NT_TC_TRAFFIC_PER_LAUNCH = 2234.23e6
 WORKLOADS = {
     "c2": dict(N=64, p=7),      # the diffusion workload named by element count
     "c2a": dict(N=40, p=7),     # 22.19M DOFs: the DOF count quoted for the same workload
@@ -343,6 +348,15 @@ def run_nontensor(ceed, dev, args):
             out["runs"].append({"prec": name, "algo": label, "gemm_mode": gm, "ms": ms,
                                 "gdofs": m.n_ldof / ms / 1e6, "tflops": flops / ms / 1e9,
                                 "alg_gbs": by / ms / 1e6, "hbm_frac": by / ms / 1e6 / hbm_peak})
+        if prec == ceed.CEED_F32:
+            # the tensor-core kernel alone (without the transposed restriction), timed with CUDA events
+            ceed.ceed_nt_set_algorithm(nt, ceed.CEED_OP_DIFFUSION, prec, ceed.CEED_NT_TC)
+            tc_ms = _time_cuda(lambda: ceed.ceed_nt_apply(nt, ceed.CEED_OP_DIFFUSION, qd, prec, x, y), 5, 3)
+            out["tensor_core_roofline"] = {
+                "bound": "hbm", "kernel": "nt_tc_kernel<3,40,48>", "apply_ms": tc_ms,
+                "alg_bytes_per_apply": by, "achieved_gbs_apply": by / tc_ms / 1e6, "peak": hbm_peak,
+                "frac_apply": by / tc_ms / 1e6 / hbm_peak, "traffic_per_launch": NT_TC_TRAFFIC_PER_LAUNCH,
+                "note": "apply = tensor-core kernel + deterministic transposed restriction"}
         algo, eta, gm, tms = ceed.ceed_nt_autotune(nt, ceed.CEED_OP_DIFFUSION, qd, prec, x, y)
         out[f"autotuned_{name}"] = {"algo": ["fused", "gemm", "tensor_core"][algo], "eta": eta, "gemm_mode": gm, "ms": tms}
         del qd
