@@ -365,6 +365,32 @@ def run_nontensor(ceed, dev, args):
     return out
 
 
+def run_hp(ceed, dev, args):
+    """Conforming mixed-order space: orders 3, 5, 7 in x-slabs of a 48 x 24 x 24 perturbed lattice,
+    Gauss q = p + 2, diffusion with the sine coefficient, Dirichlet boundary; one apply = P x, the three
+    order groups' fused kernels, P^T."""
+    import torch
+    nx, ny, nz = 48, 24, 24
+    orders = np.array([3 if (e % nx) < nx // 3 else 5 if (e % nx) < 2 * nx // 3 else 7 for e in range(nx * ny * nz)])
+    m = synthetic.HexMesh(nx, ny, nz, 1, seed=0)
+    t0 = time.perf_counter()
+    h = ceed.ceed_hp_setup(nx, ny, nz, orders, torch.from_numpy(m.vertices).to(dev),
+                           q_rule=ceed.CEED_QRULE_GAUSS, dirichlet=True)
+    setup_s = time.perf_counter() - t0
+    x = torch.from_numpy(synthetic.uniform(h.n_true, seed=1)).to(dev)
+    y = torch.empty_like(x)
+    out = {"workload": f"orders 3/5/7 in x-slabs of {nx}x{ny}x{nz} hexahedra, Gauss q=p+2, conforming (minimum rule)",
+           "n_true": h.n_true, "n_elem_nodes": h.n_rows, "setup_s": setup_s, "runs": []}
+    for name, prec in (("f64", ceed.CEED_F64), ("f32", ceed.CEED_F32)):
+        ceed.ceed_hp_build_qdata(h, ceed.CEED_OP_DIFFUSION, ceed.CEED_COEFF_SINE, prec=prec)
+        ms = _time_cuda(lambda: ceed.ceed_hp_apply(h, ceed.CEED_OP_DIFFUSION, prec, x, y,
+                                                   flags=ceed.CEED_APPLY_DIRICHLET), 5, 3)
+        out["runs"].append({"prec": name, "ms": ms, "gdofs_true": h.n_true / ms / 1e6,
+                            "gdofs_elem_nodes": h.n_rows / ms / 1e6})
+    h.close()
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -384,6 +410,7 @@ def main():
     ap.add_argument("--adjoint", type=int, default=1, help="measure the adjoint kernels")
     ap.add_argument("--df", type=int, default=1, help="measure the double-float FP64-accurate operator")
     ap.add_argument("--nontensor", type=int, default=1, help="measure the non-tensor (tetrahedral) operator")
+    ap.add_argument("--hp", type=int, default=1, help="measure the conforming mixed-order (hp) operator")
     ap.add_argument("--nt-profile", default=None, choices=["fused64", "fused32", "gemm32", "tc"],
                     help="profiling case: three tetrahedral diffusion applies with one algorithm, then exit")
     args = ap.parse_args()
@@ -598,6 +625,11 @@ def main():
     if args.nontensor:
         nontensor = run_nontensor(ceed, dev, args)
 
+    # ---------------- conforming mixed-order (hp) space: orders 3, 5, 7 joined at their interfaces
+    hp = None
+    if args.hp:
+        hp = run_hp(ceed, dev, args)
+
     # ---------------- CPU oracle on a bounded sample (rank 0, N = 1 only)
     cpu = None
     if rank == 0 and ws == 1 and args.cpu_sample > 0:
@@ -637,6 +669,7 @@ def main():
             "batched": batched,
             "adjoint": adjoint,
             "nontensor": nontensor,
+            "hp": hp,
             "cpu_baseline": cpu,
         }
         print(json.dumps(line), flush=True)

@@ -361,6 +361,45 @@ int ceed_nt_autotune(ceed_nt_t h, int op, const void *qdata, int prec, const dou
  * expired (the launch then left its element vectors incomplete). */
 int ceed_nt_status(ceed_nt_t h, void *stream);
 
+/* ---------------------------------------------------------------- conforming hp (variable order) */
+
+/* Mixed-order elements joined into one continuous space (the mixed-order workload of the batched
+ * apply, with conforming interfaces): a structured nx x ny x nz lattice of hexahedra, element
+ * e = ex + nx (ey + ny ez) of order orders[e].  Minimum rule: every face and edge carries the lowest
+ * order of the elements sharing it; the space is {u continuous, u|_e in Q_{p_e}, u on a face or
+ * edge in Q of that entity's order}.  It is the image of a conforming prolongation P from true dofs
+ * to element nodes (an element node takes the value of the polynomial of the lowest-dimensional
+ * entity it lies on: that entity's GLL Lagrange interpolant, composed through lower-order edges).
+ * Operator on true dofs: y = P^T blockdiag(A_e) P x, A_e the element matrices of Section 2 (each
+ * order group applied by the fused tensor-product kernels).
+ * True-dof numbering: vertices (i, j, k) with i fastest; edges along x, then y, then z, each axis by
+ * lower vertex with i fastest, interior nodes in increasing coordinate; faces normal to x, y, z, by
+ * lower corner, interior nodes with the lower in-plane axis fastest; element interiors in element
+ * order, node a fastest.  Element-node rows (ceed_hp_prolong): order groups by ascending order,
+ * elements by ascending index, nodes a + P (b + P c).  The handle owns P, P^T, per-group meshes,
+ * quadrature data and two element-vector work arrays. */
+typedef struct ceed_hp_s *ceed_hp_t;
+typedef struct {
+  int32_t nx, ny, nz;          /* elements per direction */
+  const int32_t *orders;       /* host [nx ny nz], each in 1..8 */
+  const double *vertices;      /* device [E][8][3] trilinear element maps (as for ceed_mesh_desc) */
+  int32_t q_rule;              /* GLL (Q = p+1) or GAUSS (Q = p+2), every element */
+  int32_t dirichlet;           /* nonzero: the true dofs on the lattice boundary are Dirichlet dofs */
+} ceed_hp_desc;
+/* Build the space (host) and the per-order meshes.  Synchronizes `stream`.  Errors: INVALID, OOM, CUDA. */
+int ceed_hp_setup(const ceed_hp_desc *desc, ceed_hp_t *out, void *stream);
+int ceed_hp_destroy(ceed_hp_t h);
+/* Number of true dofs, of element-node rows, of order groups. */
+int ceed_hp_info(ceed_hp_t h, int64_t *n_true, int64_t *n_rows, int32_t *n_groups);
+/* Quadrature data of every order group (handle-owned) for (op, prec F64 or F32); coefficients ONE,
+ * CONST or SINE.  Synchronizes `stream`. */
+int ceed_hp_build_qdata(ceed_hp_t h, int op, int coeff_kind, const double *coeff, int prec, void *stream);
+/* Element vectors u_elem = P x (device FP64 [n_rows]); asynchronous. */
+int ceed_hp_prolong(ceed_hp_t h, const double *x, double *u_elem, void *stream);
+/* y = P^T A P x on true dofs (device FP64 [n_true]); `prec` selects the quadrature data and the
+ * arithmetic of the element kernels; CEED_APPLY_DIRICHLET masks the Dirichlet dofs.  Asynchronous. */
+int ceed_hp_apply(ceed_hp_t h, int op, int prec, const double *x, double *y, unsigned flags, void *stream);
+
 /* ---------------------------------------------------------------- vectors */
 
 /* Deterministic dot product of two device FP64 vectors; the result is written to *out

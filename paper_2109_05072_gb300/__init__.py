@@ -63,6 +63,11 @@ class _NtDesc(ctypes.Structure):
                 ("dirichlet", ctypes.c_void_p)]
 
 
+class _HpDesc(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("nz", ctypes.c_int32), ("orders", ctypes.c_void_p),
+                ("vertices", ctypes.c_void_p), ("q_rule", ctypes.c_int32), ("dirichlet", ctypes.c_int32)]
+
+
 class _CgReport(ctypes.Structure):
     _fields_ = [("iterations", ctypes.c_int32), ("outer_iterations", ctypes.c_int32),
                 ("rel_residual", ctypes.c_double), ("seconds", ctypes.c_double)]
@@ -122,6 +127,12 @@ def _load():
                                                  ctypes.POINTER(ctypes.c_float)]),
         "ceed_nt_autotune": (ctypes.c_int, [vp, ctypes.c_int, vp, ctypes.c_int, vp, vp, ctypes.c_int, vp]),
         "ceed_nt_status": (ctypes.c_int, [vp, vp]),
+        "ceed_hp_setup": (ctypes.c_int, [ctypes.POINTER(_HpDesc), ctypes.POINTER(vp), vp]),
+        "ceed_hp_destroy": (ctypes.c_int, [vp]),
+        "ceed_hp_info": (ctypes.c_int, [vp, ctypes.POINTER(i64), ctypes.POINTER(i64), ctypes.POINTER(i32)]),
+        "ceed_hp_build_qdata": (ctypes.c_int, [vp, ctypes.c_int, ctypes.c_int, vp, ctypes.c_int, vp]),
+        "ceed_hp_prolong": (ctypes.c_int, [vp, vp, vp, vp]),
+        "ceed_hp_apply": (ctypes.c_int, [vp, ctypes.c_int, ctypes.c_int, vp, vp, u32, vp]),
         "ceed_dot_workspace_bytes": (sz, [i64]),
         "ceed_dot": (ctypes.c_int, [vp, vp, i64, vp, vp, vp]),
         "ceed_dot_noalloc_max_n": (i64, []),
@@ -508,6 +519,63 @@ def ceed_nt_autotune(nt: NonTensor, op, qdata, prec, x, y, include_tf32=False, s
 
 def ceed_nt_status(nt: NonTensor, stream=None):
     _check(_lib.ceed_nt_status(nt.handle, _stream(stream)))
+
+
+class Hp:
+    """Owns a ceed_hp_t (conforming variable-order space and operator)."""
+
+    def __init__(self, handle):
+        self.handle = handle
+        nt, nr, ng = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int32()
+        _check(_lib.ceed_hp_info(handle, ctypes.byref(nt), ctypes.byref(nr), ctypes.byref(ng)))
+        self.n_true, self.n_rows, self.n_groups = nt.value, nr.value, ng.value
+
+    def close(self):
+        if self.handle:
+            _lib.ceed_hp_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def ceed_hp_setup(nx, ny, nz, orders, vertices, q_rule=CEED_QRULE_GLL, dirichlet=True, stream=None) -> Hp:
+    """orders: host int array [nx ny nz]; vertices: CUDA float64 tensor [E, 8, 3]."""
+    import numpy as np
+    o = np.ascontiguousarray(orders, dtype=np.int32)
+    assert o.size == nx * ny * nz and vertices.dtype == torch.float64
+    d = _HpDesc(nx, ny, nz, o.ctypes.data_as(ctypes.c_void_p), _ptr(vertices), q_rule, int(bool(dirichlet)))
+    h = ctypes.c_void_p()
+    _check(_lib.ceed_hp_setup(ctypes.byref(d), ctypes.byref(h), _stream(stream)))
+    return Hp(h)
+
+
+def ceed_hp_destroy(hp: Hp):
+    hp.close()
+
+
+def ceed_hp_info(hp: Hp):
+    return hp.n_true, hp.n_rows, hp.n_groups
+
+
+def ceed_hp_build_qdata(hp: Hp, op, coeff_kind, coeff=None, prec=CEED_F64, stream=None):
+    if coeff_kind == CEED_COEFF_CONST:
+        cval = (ctypes.c_double * 1)(float(coeff))
+        cptr = ctypes.cast(cval, ctypes.c_void_p)
+    else:
+        cptr = None
+    _check(_lib.ceed_hp_build_qdata(hp.handle, op, coeff_kind, cptr, prec, _stream(stream)))
+
+
+def ceed_hp_prolong(hp: Hp, x, u_elem, stream=None):
+    _check(_lib.ceed_hp_prolong(hp.handle, _ptr(x), _ptr(u_elem), _stream(stream)))
+
+
+def ceed_hp_apply(hp: Hp, op, prec, x, y, flags=0, stream=None):
+    _check(_lib.ceed_hp_apply(hp.handle, op, prec, _ptr(x), _ptr(y), flags, _stream(stream)))
 
 
 def ceed_dot_workspace_bytes(n: int) -> int:
