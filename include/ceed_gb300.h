@@ -249,6 +249,9 @@ typedef struct {
   double coarse_tol;        /* 0 -> 3e-2 */
   int32_t coarse_max_iter;  /* 0 -> 500 */
   int32_t prec_lo;          /* precision of qdata_lo (F32, BF16, F16, F32_GEO) */
+  int32_t smoother;         /* 0: Chebyshev on D^{-1} A (Jacobi); 1: Chebyshev on M A with the overlapping
+                               Schwarz smoother M of ceed_schwarz_create (levels must be GLL collocated) */
+  int32_t smoother_coeff;   /* smoother 1: coefficient kind for the element means (ONE or SINE) */
 } ceed_pmg_opts;
 
 int ceed_pmg_create(int nlevels, const ceed_mesh_t *meshes, const void *const *qdata64, const void *const *qdata_lo,
@@ -261,6 +264,23 @@ int ceed_pmg_restrict(ceed_pmg_t pmg, int level, const double *rf, double *rc, v
 /* lambda_max estimate of D^{-1} A used for level l's smoother. */
 int ceed_pmg_info(ceed_pmg_t pmg, int level, double *lambda_max);
 int ceed_pmg_destroy(ceed_pmg_t pmg);
+
+/* Overlapping Schwarz smoother with fast diagonalization (Section 1's Schwarz/fast-diagonalization
+ * preconditioning; the method of Lottes and Fischer, J. Sci. Comput. 24, 2005).  Each element's local
+ * problem is its own GLL nodes with Dirichlet conditions one node into each neighbour; its operator
+ * is replaced by the separable operator of a box with the element's mean side lengths h_d (mean of the
+ * four element edges along each reference axis) and mean coefficient k (over its GLL nodes):
+ *   A_e = k (B_z (x) B_y (x) A_x + B_z (x) A_y (x) B_x + A_z (x) B_y (x) B_x),  A_d = (2/h_d) A^, B_d = (h_d/2) B^,
+ * (A^, B^) the GLL stiffness and mass of three reference elements side by side restricted to the
+ * middle one, inverted by fast diagonalization (A^ S = B^ S L, S^T B^ S = I).  The smoother is
+ * z = sum_e R_e^T W A_e^{-1} W R_e r, W = diag(multiplicity^{-1/2}) (symmetric), FP32 arithmetic.
+ * Requires a GLL collocated mesh with one component.  Coefficient ONE, CONST (host value) or SINE. */
+typedef struct ceed_schwarz_s *ceed_schwarz_t;
+int ceed_schwarz_create(ceed_mesh_t mesh, int coeff_kind, const double *coeff, ceed_schwarz_t *out, void *stream);
+/* z = M r (device FP64 [n_ldof], no overlap); CEED_APPLY_DIRICHLET: zero on Dirichlet nodes in r and z.
+ * Asynchronous; one kernel launch per colour (colour-ordered, deterministic). */
+int ceed_schwarz_apply(ceed_schwarz_t sw, const double *r, double *z, unsigned flags, void *stream);
+int ceed_schwarz_destroy(ceed_schwarz_t sw);
 
 /* ---------------------------------------------------------------- adjoint */
 

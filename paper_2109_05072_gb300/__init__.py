@@ -53,7 +53,8 @@ class _CgOpts(ctypes.Structure):
 
 class _PmgOpts(ctypes.Structure):
     _fields_ = [("smooth_degree", ctypes.c_int32), ("smooth_ratio", ctypes.c_double), ("eig_iters", ctypes.c_int32),
-                ("coarse_tol", ctypes.c_double), ("coarse_max_iter", ctypes.c_int32), ("prec_lo", ctypes.c_int32)]
+                ("coarse_tol", ctypes.c_double), ("coarse_max_iter", ctypes.c_int32), ("prec_lo", ctypes.c_int32),
+                ("smoother", ctypes.c_int32), ("smoother_coeff", ctypes.c_int32)]
 
 
 class _NtDesc(ctypes.Structure):
@@ -127,6 +128,9 @@ def _load():
                                                  ctypes.POINTER(ctypes.c_float)]),
         "ceed_nt_autotune": (ctypes.c_int, [vp, ctypes.c_int, vp, ctypes.c_int, vp, vp, ctypes.c_int, vp]),
         "ceed_nt_status": (ctypes.c_int, [vp, vp]),
+        "ceed_schwarz_create": (ctypes.c_int, [vp, ctypes.c_int, vp, ctypes.POINTER(vp), vp]),
+        "ceed_schwarz_apply": (ctypes.c_int, [vp, vp, vp, u32, vp]),
+        "ceed_schwarz_destroy": (ctypes.c_int, [vp]),
         "ceed_hp_setup": (ctypes.c_int, [ctypes.POINTER(_HpDesc), ctypes.POINTER(vp), vp]),
         "ceed_hp_destroy": (ctypes.c_int, [vp]),
         "ceed_hp_info": (ctypes.c_int, [vp, ctypes.POINTER(i64), ctypes.POINTER(i64), ctypes.POINTER(i32)]),
@@ -375,11 +379,14 @@ class Pmg:
 
 
 def ceed_pmg_create(meshes, qdata64, qdata_lo=None, prec_lo=CEED_F32, smooth_degree=0, smooth_ratio=0.0,
-                    eig_iters=0, coarse_tol=0.0, coarse_max_iter=0, stream=None) -> Pmg:
+                    eig_iters=0, coarse_tol=0.0, coarse_max_iter=0, smoother=0, smoother_coeff=CEED_COEFF_SINE,
+                    stream=None) -> Pmg:
+    """smoother 0: Chebyshev-Jacobi; 1: Chebyshev on the overlapping Schwarz smoother."""
     n = len(meshes)
     arr = lambda items: (ctypes.c_void_p * n)(*items)
     lo = arr([_ptr(q).value if q is not None else None for q in qdata_lo]) if qdata_lo is not None else None
-    o = _PmgOpts(smooth_degree, smooth_ratio, eig_iters, coarse_tol, coarse_max_iter, prec_lo)
+    o = _PmgOpts(smooth_degree, smooth_ratio, eig_iters, coarse_tol, coarse_max_iter, prec_lo, smoother,
+                 smoother_coeff)
     h = ctypes.c_void_p()
     _check(_lib.ceed_pmg_create(n, arr([m.handle for m in meshes]), arr([_ptr(q).value for q in qdata64]), lo,
                                 ctypes.byref(o), ctypes.byref(h), _stream(stream)))
@@ -519,6 +526,42 @@ def ceed_nt_autotune(nt: NonTensor, op, qdata, prec, x, y, include_tf32=False, s
 
 def ceed_nt_status(nt: NonTensor, stream=None):
     _check(_lib.ceed_nt_status(nt.handle, _stream(stream)))
+
+
+class Schwarz:
+    """Owns a ceed_schwarz_t and keeps its mesh alive."""
+
+    def __init__(self, handle, mesh):
+        self.handle, self._mesh = handle, mesh
+
+    def close(self):
+        if self.handle:
+            _lib.ceed_schwarz_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def ceed_schwarz_create(mesh: Mesh, coeff_kind=CEED_COEFF_SINE, coeff=None, stream=None) -> Schwarz:
+    cptr = None
+    if coeff_kind == CEED_COEFF_CONST:
+        cval = (ctypes.c_double * 1)(float(coeff))
+        cptr = ctypes.cast(cval, ctypes.c_void_p)
+    h = ctypes.c_void_p()
+    _check(_lib.ceed_schwarz_create(mesh.handle, coeff_kind, cptr, ctypes.byref(h), _stream(stream)))
+    return Schwarz(h, mesh)
+
+
+def ceed_schwarz_apply(sw: Schwarz, r, z, flags=0, stream=None):
+    _check(_lib.ceed_schwarz_apply(sw.handle, _ptr(r), _ptr(z), flags, _stream(stream)))
+
+
+def ceed_schwarz_destroy(sw: Schwarz):
+    sw.close()
 
 
 class Hp:

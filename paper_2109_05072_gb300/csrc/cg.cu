@@ -393,6 +393,8 @@ __global__ void scale_kernel(double *__restrict__ v, const double *__restrict__ 
   CEEDGB_GRID4(v[k] = f * dinv[k] * w[k];)
 }
 
+__global__ void scal_kernel(double *__restrict__ v, int64_t n, double f) { CEEDGB_GRID4(v[k] *= f;) }
+
 __global__ void seed_kernel(double *__restrict__ v, int64_t n) {
   CEEDGB_GRID4({
     uint64_t z = (uint64_t)k * 0x9E3779B97F4A7C15ull + 0x632BE59BD9B4E019ull;
@@ -430,6 +432,8 @@ struct PmgLevel {
   int64_t n = 0;
   ApplyReq op;              // smoothing operator (masked)
   double *x = nullptr, *b = nullptr, *r = nullptr, *d = nullptr, *q = nullptr, *dinv = nullptr;
+  double *z = nullptr;      // Schwarz smoother: M r
+  ceed_schwarz_t sw = nullptr;
   double lam = 1.0;
 };
 
@@ -460,9 +464,65 @@ static double host_dot(const double *x, const double *y, int64_t n, double *part
   return h;
 }
 
+__global__ void cheb_res_kernel(double *__restrict__ x, double *__restrict__ r, const double *__restrict__ b,
+                                const double *__restrict__ q, int64_t n, int zero_x) {
+  CEEDGB_GRID4({
+    r[k] = zero_x ? b[k] : b[k] - q[k];
+    if (zero_x) x[k] = 0.0;
+  })
+}
+
+// Chebyshev step with a preconditioner application z = M r: x += d; r -= A d (q = A d); then, after
+// z = M r, d = c1 d + c2 z.
+__global__ void cheb_xr_kernel(double *__restrict__ x, double *__restrict__ r, const double *__restrict__ d,
+                               const double *__restrict__ q, int64_t n) {
+  CEEDGB_GRID4({
+    x[k] += d[k];
+    r[k] -= q[k];
+  })
+}
+
+__global__ void cheb_dir_kernel(double *__restrict__ d, const double *__restrict__ z, int64_t n, double c1, double c2) {
+  CEEDGB_GRID4(d[k] = c1 * d[k] + c2 * z[k];)
+}
+
+// Chebyshev smoothing on M A with the Schwarz smoother M (same recurrence as the Jacobi version).
+static int pmg_cheb_schwarz(ceed_pmg_s *P, int l, int degree, double lo, double hi, bool zero_x, cudaStream_t s) {
+  PmgLevel &L = P->lv[l];
+  const double theta = 0.5 * (hi + lo), delta = 0.5 * (hi - lo), sigma = theta / delta;
+  double rho = 1.0 / sigma;
+  if (!zero_x) {
+    ApplyReq a = L.op;
+    a.x = L.x;
+    a.y = L.q;
+    if (int st = launch_apply(L.mesh, a, s)) return st;
+  }
+  cheb_res_kernel<<<red_blocks(L.n), RED_THREADS, 0, s>>>(L.x, L.r, L.b, L.q, L.n, zero_x);
+  if (int st = launch_schwarz(L.sw, L.r, L.z, 1, s)) return st;
+  cheb_dir_kernel<<<red_blocks(L.n), RED_THREADS, 0, s>>>(L.d, L.z, L.n, 0.0, 1.0 / theta);
+  for (int k = 0; k < degree; ++k) {
+    if (k == degree - 1) {
+      axpy_kernel<<<stream_blocks(L.n), 256, 0, s>>>(L.x, L.d, L.n);
+      break;
+    }
+    ApplyReq a = L.op;
+    a.x = L.d;
+    a.y = L.q;
+    if (int st = launch_apply(L.mesh, a, s)) return st;
+    cheb_xr_kernel<<<red_blocks(L.n), RED_THREADS, 0, s>>>(L.x, L.r, L.d, L.q, L.n);
+    if (int st = launch_schwarz(L.sw, L.r, L.z, 1, s)) return st;
+    const double rho_new = 1.0 / (2.0 * sigma - rho);
+    cheb_dir_kernel<<<red_blocks(L.n), RED_THREADS, 0, s>>>(L.d, L.z, L.n, rho_new * rho, 2.0 * rho_new / delta);
+    rho = rho_new;
+  }
+  CEED_CUDA_CHECK(cudaGetLastError());
+  return CEED_OK;
+}
+
 // Chebyshev smoothing of A x = b on level l (x0 = 0 or the current x), `degree` products with A.
 static int pmg_cheb(ceed_pmg_s *P, int l, int degree, double lo, double hi, bool zero_x, cudaStream_t s) {
   PmgLevel &L = P->lv[l];
+  if (L.sw) return pmg_cheb_schwarz(P, l, degree, lo, hi, zero_x, s);
   const double theta = 0.5 * (hi + lo), delta = 0.5 * (hi - lo), sigma = theta / delta;
   double rho = 1.0 / sigma;
   if (!zero_x) {
@@ -794,6 +854,8 @@ extern "C" int ceed_dot_noalloc(const double *x, const double *y, int64_t n, dou
 // ---------------------------------------------------------------- p-multigrid API
 static void pmg_free(ceed_pmg_s *P) {
   if (!P) return;
+  for (int l = 0; l < 4; ++l)
+    if (P->lv[l].sw) ceed_schwarz_destroy(P->lv[l].sw);
   for (void *a : P->allocs) cudaFree(a);
   delete P;
 }
@@ -818,6 +880,10 @@ extern "C" int ceed_pmg_create(int nlevels, const ceed_mesh_t *meshes, const voi
   if (P->o.eig_iters <= 0) P->o.eig_iters = 20;
   if (P->o.coarse_tol <= 0) P->o.coarse_tol = 3e-2;
   if (P->o.coarse_max_iter <= 0) P->o.coarse_max_iter = 500;
+  if (P->o.smoother != 0 && P->o.smoother != 1) {
+    delete P;
+    return fail(CEED_ERR_INVALID, "p-multigrid smoother: 0 (Jacobi) or 1 (Schwarz)");
+  }
   P->L = nlevels;
   auto dalloc = [&](size_t bytes, void **ptr) -> int {
     cudaError_t e = cudaMalloc(ptr, bytes);
@@ -841,6 +907,10 @@ extern "C" int ceed_pmg_create(int nlevels, const ceed_mesh_t *meshes, const voi
       if (!st) st = dalloc(L.n * sizeof(double), (void **)v);
     if (!st) st = ceed_jacobi_diagonal(L.mesh, CEED_OP_DIFFUSION, qdata64[l], CEED_F64, L.dinv, CEED_APPLY_DIRICHLET, stream);
     if (!st) invert_kernel<<<stream_blocks(L.n), 256, 0, s>>>(L.dinv, L.n);
+    if (!st && P->o.smoother == 1 && l + 1 < nlevels) {
+      st = dalloc(L.n * sizeof(double), (void **)&L.z);
+      if (!st) st = ceed_schwarz_create(L.mesh, P->o.smoother_coeff, nullptr, &L.sw, stream);
+    }
   }
   if (!st) st = dalloc(RED_MAX_BLOCKS * sizeof(double), (void **)&P->part);
   if (!st) st = dalloc(sizeof(double), (void **)&P->dsum);
@@ -864,6 +934,15 @@ extern "C" int ceed_pmg_create(int nlevels, const ceed_mesh_t *meshes, const voi
       a.y = L.q;
       st = launch_apply(L.mesh, a, s);
       if (st) break;
+      if (L.sw) {   // lambda_max of M A
+        st = launch_schwarz(L.sw, L.q, L.d, 1, s);
+        if (st) break;
+        const double nd = std::sqrt(host_dot(L.d, L.d, L.n, P->part, P->dsum, s, &st));
+        lam = nd / nx;
+        copy_kernel<<<stream_blocks(L.n), 256, 0, s>>>(L.x, L.d, L.n);
+        scal_kernel<<<stream_blocks(L.n), 256, 0, s>>>(L.x, L.n, 1.0 / nd);
+        continue;
+      }
       scale_kernel<<<red_blocks(L.n), RED_THREADS, 0, s>>>(L.d, L.dinv, L.q, L.n, 1.0);
       const double nd = std::sqrt(host_dot(L.d, L.d, L.n, P->part, P->dsum, s, &st));
       lam = nd / nx;

@@ -141,6 +141,9 @@ int launch_apply_qf32geo(ceed_mesh_t m, const ApplyReq &r, cudaStream_t s);
 int launch_apply_df(ceed_mesh_t m, const ApplyReq &r, cudaStream_t s);
 int launch_apply(ceed_mesh_t m, const ApplyReq &r, cudaStream_t s);
 
+// overlapping Schwarz smoother (schwarz.cu)
+int launch_schwarz(ceed_schwarz_t sw, const double *r, double *z, int masked, cudaStream_t s);
+
 // p-multigrid transfers (pmg_kernels.cu)
 int check_transfer_pair(ceed_mesh_t coarse, ceed_mesh_t fine);
 int launch_prolong(ceed_mesh_t coarse, ceed_mesh_t fine, const double *uc, double *uf, int add, cudaStream_t s);
