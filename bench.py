@@ -593,9 +593,10 @@ def main():
             lv_meshes.append(mc)
             lv_q64.append(q64c)
             lv_q32.append(q32c)
-        for name, qlo in (("pmg_fp64_smoothers", None), ("pmg_fp32_smoothers", lv_q32)):
+        for name, qlo, smoother in (("pmg_fp64_smoothers", None, 0), ("pmg_fp32_smoothers", lv_q32, 0),
+                                    ("pmg_schwarz_fp32_smoothers", lv_q32, 1)):
             t1 = time.perf_counter()
-            pmg = ceed.ceed_pmg_create(lv_meshes, lv_q64, qlo, prec_lo=ceed.CEED_F32)
+            pmg = ceed.ceed_pmg_create(lv_meshes, lv_q64, qlo, prec_lo=ceed.CEED_F32, smoother=smoother)
             setup_s = time.perf_counter() - t1
             st, repp = ceed.ceed_cg_solve(mesh, qd64, ceed.CEED_F64, b, xs, mode=ceed.CEED_CG_FP64, tol=1e-10,
                                           max_iter=2000, op=ceed.CEED_OP_DIFFUSION, pmg=pmg, raise_on_error=False)
