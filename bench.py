@@ -564,15 +564,22 @@ def main():
         st, rep64 = ceed.ceed_cg_solve(mesh, qd64, ceed.CEED_F64, b, xs, mode=ceed.CEED_CG_FP64, tol=1e-10,
                                        max_iter=20000, op=ceed.CEED_OP_DIFFUSION, raise_on_error=False)
         cg["fp64_to_1e-10"] = dict(rep64, status=st)
-        for name, prec in (("f32", ceed.CEED_F32), ("bf16", ceed.CEED_BF16), ("f32geo", ceed.CEED_F32_GEO)):
+        # low-precision inner operators: iterative refinement (restarted inner PCG to 1e-4 per pass) and
+        # reliable updates (one PCG run, true FP64 residual put in place at every 10x decrease)
+        for name, prec, modes in (("f32", ceed.CEED_F32, ("", "reliable")), ("bf16", ceed.CEED_BF16, ("reliable",)),
+                                  ("f32geo", ceed.CEED_F32_GEO, ("reliable",)),
+                                  ("f64df", ceed.CEED_F64_DF, ("reliable",))):
             qlo = ceed.alloc_qdata(mesh, ceed.CEED_OP_DIFFUSION, prec, dev)
             ceed.ceed_build_qdata(mesh, ceed.CEED_OP_DIFFUSION, ceed.CEED_COEFF_SINE, None, prec, qlo)
-            st, repm = ceed.ceed_cg_solve(mesh, qd64, ceed.CEED_F64, b, xs, mode=ceed.CEED_CG_MIXED, tol=1e-10,
-                                          max_iter=40000, op=ceed.CEED_OP_DIFFUSION, qdata_lo=qlo, prec_lo=prec,
-                                          inner_tol=1e-4, raise_on_error=False)
-            cg[f"mixed_{name}_to_1e-10"] = dict(repm, status=st)
-            if rep64["seconds"] > 0 and repm["seconds"] > 0:
-                cg[f"mixed_{name}_speedup"] = rep64["seconds"] / repm["seconds"]
+            for mode in modes:
+                key = f"mixed_{name}" + (f"_{mode}" if mode else "")
+                st, repm = ceed.ceed_cg_solve(mesh, qd64, ceed.CEED_F64, b, xs,
+                                              mode=ceed.CEED_CG_MIXED_RELIABLE if mode else ceed.CEED_CG_MIXED,
+                                              tol=1e-10, max_iter=8000 if mode else 40000, op=ceed.CEED_OP_DIFFUSION, qdata_lo=qlo,
+                                              prec_lo=prec, inner_tol=1e-4, raise_on_error=False)
+                cg[f"{key}_to_1e-10"] = dict(repm, status=st)
+                if rep64["seconds"] > 0 and repm["seconds"] > 0:
+                    cg[f"{key}_speedup"] = rep64["seconds"] / repm["seconds"]
             del qlo
         # p-multigrid-preconditioned (flexible) CG: levels p = 7, 3, 1 on the same elements, Chebyshev-Jacobi
         # smoothing (degree 3) with FP64 or FP32-arithmetic level operators, Jacobi-PCG on the p = 1 level

@@ -188,7 +188,7 @@ int ceed_batch_destroy(ceed_batch_t batch);
 
 /* ---------------------------------------------------------------- CG solver */
 
-typedef enum { CEED_CG_FP64 = 0, CEED_CG_MIXED = 1 } ceed_cg_mode;
+typedef enum { CEED_CG_FP64 = 0, CEED_CG_MIXED = 1, CEED_CG_MIXED_RELIABLE = 2 } ceed_cg_mode;
 
 typedef struct ceed_pmg_s *ceed_pmg_t;
 
@@ -206,11 +206,13 @@ typedef struct {
   int32_t use_x0;         /* nonzero: x holds the initial guess; else x0 = 0 */
   ceed_pmg_t pmg;         /* FP64 mode: non-NULL -> flexible CG preconditioned by one p-multigrid
                              V-cycle per iteration instead of Jacobi */
+  double reliable_delta;  /* MIXED_RELIABLE: replace the recurrence residual by the true FP64 residual
+                             each time it has fallen by this factor; 0 -> 0.1, else in (0, 1) */
 } ceed_cg_opts;
 
 typedef struct {
   int32_t iterations;       /* FP64 CG iterations, or inner iterations summed over refinements */
-  int32_t outer_iterations; /* MIXED: refinement steps (FP64 residual evaluations) */
+  int32_t outer_iterations; /* MIXED: refinement steps; MIXED_RELIABLE: FP64 true-residual evaluations */
   double rel_residual;      /* ||b - A x|| / ||b|| with the FP64 operator at exit */
   double seconds;           /* wall time of the solve, measured with CUDA events */
 } ceed_cg_report;
@@ -221,7 +223,12 @@ size_t ceed_cg_workspace_bytes(ceed_mesh_t mesh, const ceed_cg_opts *opts);
 /* Solve A x = b with Jacobi-preconditioned CG (Section 1) on the Dirichlet-masked operator.
  * FP64 mode: all arithmetic FP64.  MIXED mode: iterative refinement, outer residual
  * r = b - A x with the FP64 operator (qdata, prec), inner PCG with the low-precision operator
- * (opts->qdata_lo, FP32 contractions) and FP64 vectors, dot products and updates; x += d.
+ * (opts->qdata_lo, FP32 contractions, or the double-float operator of F64_DF) and FP64 vectors,
+ * dot products and updates; x += d; each inner pass reduces its residual by inner_tol, or by less
+ * when that is all the tolerance still needs.  MIXED_RELIABLE mode: one PCG run with the
+ * low-precision operator and FP64 vectors whose recurrence residual is replaced by the true FP64
+ * residual b - A x each time it has fallen by reliable_delta (reliable updates, Sleijpen and
+ * van der Vorst 1996), keeping the search direction; it stops when the true residual meets tol.
  * b, x: device FP64 [n_ldof] (ncomp = 1).  work: device, ceed_cg_workspace_bytes bytes,
  * 256-byte aligned.  Synchronizes `stream`.  Returns NOT_CONVERGED (report filled) on the cap,
  * NONFINITE on a NaN/Inf reduction. */

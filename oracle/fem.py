@@ -271,6 +271,47 @@ def pcg(apply_fn, b, dinv, tol: float = 1e-10, maxit: int = 10000, x0=None):
     return x, it, hist[-1], np.array(hist)
 
 
+def pcg_reliable(apply_lo, apply_hi, b, dinv, tol: float = 1e-10, delta: float = 0.1, maxit: int = 10000):
+    """PCG run with an inexact operator `apply_lo` and reliable updates (Sleijpen and van der Vorst,
+    "Reliable updated residuals in hybrid Bi-CG methods", Computing 56, 1996): the reading of the
+    mixed-precision CG of Section 1's solver in which the Krylov process is never restarted.
+
+    The recurrence residual follows apply_lo; each time its norm has fallen by `delta` since the
+    last replacement (or has reached the tolerance), the true residual b - apply_hi(x) is computed,
+    the run stops if it meets tol, and otherwise it replaces the recurrence residual before the
+    step's beta: z = D^{-1} r and beta = r.z / r.z_old come from the true residual, and the new
+    direction p = z + beta p continues the same Krylov process.  x0 = 0.  Returns (x, iterations,
+    true relative residual, number of true-residual evaluations).
+    """
+    x = np.zeros_like(b)
+    nb = np.linalg.norm(b)
+    r = b.copy()
+    z = dinv * r
+    p = z.copy()
+    rz = r @ z
+    ref = np.linalg.norm(r)
+    evals, it = 1, 0
+    true_rel = ref / nb
+    while it < maxit and true_rel > tol:
+        q = apply_lo(p)
+        alpha = rz / (p @ q)
+        x += alpha * p
+        r -= alpha * q
+        it += 1
+        nr = np.linalg.norm(r)
+        if nr <= tol * nb or nr <= delta * ref:
+            r = b - apply_hi(x)
+            evals += 1
+            true_rel = np.linalg.norm(r) / nb
+            ref = np.linalg.norm(r)
+            if true_rel <= tol:
+                break
+        z = dinv * r
+        rz_new = r @ z
+        p = z + (rz_new / rz) * p
+        rz = rz_new
+    return x, it, true_rel, evals
+
 def exact_solution(X):
     """u*(x) = sin(pi x) sin(pi y) sin(pi z): smooth, zero on the boundary of the unit cube."""
     s = np.sin(np.pi * X)

@@ -25,7 +25,7 @@ CEED_QRULE_GLL, CEED_QRULE_GAUSS = 0, 1
 CEED_OP_MASS, CEED_OP_DIFFUSION = 0, 1
 CEED_COEFF_ONE, CEED_COEFF_CONST, CEED_COEFF_SINE, CEED_COEFF_PER_QPT = 0, 1, 2, 3
 CEED_APPLY_DIRICHLET = 1
-CEED_CG_FP64, CEED_CG_MIXED = 0, 1
+CEED_CG_FP64, CEED_CG_MIXED, CEED_CG_MIXED_RELIABLE = 0, 1, 2
 CEED_NT_FUSED, CEED_NT_GEMM, CEED_NT_TC = 0, 1, 2
 
 PREC_BYTES = {CEED_F64: 8, CEED_F32: 4, CEED_BF16: 2, CEED_F16: 2, CEED_F32_GEO: 4, CEED_F64_DF: 8}
@@ -48,7 +48,8 @@ class _CgOpts(ctypes.Structure):
     _fields_ = [("mode", ctypes.c_int32), ("max_iter", ctypes.c_int32), ("max_outer", ctypes.c_int32),
                 ("check_every", ctypes.c_int32), ("fixed_iters", ctypes.c_int32), ("op", ctypes.c_int32),
                 ("tol", ctypes.c_double), ("inner_tol", ctypes.c_double), ("qdata_lo", ctypes.c_void_p),
-                ("prec_lo", ctypes.c_int32), ("use_x0", ctypes.c_int32), ("pmg", ctypes.c_void_p)]
+                ("prec_lo", ctypes.c_int32), ("use_x0", ctypes.c_int32), ("pmg", ctypes.c_void_p),
+                ("reliable_delta", ctypes.c_double)]
 
 
 class _PmgOpts(ctypes.Structure):

@@ -7,6 +7,7 @@
 // deterministic: a fixed grid writes per-block partial sums that one block adds in fixed order.
 #include <algorithm>
 #include <cmath>
+#include <cstddef>
 #include <cstring>
 #include <mutex>
 #include <new>
@@ -165,23 +166,46 @@ __global__ void finalize_beta_kernel(const double *__restrict__ part_rz, const d
   }
 }
 
+// Residual replacement of the reliable-update CG, after an iteration that stopped before its beta
+// step: rz and rr of the replaced residual from partials, beta = rz_new / rz_old (the p update
+// that follows uses the true residual's z).
+__global__ void replace_finalize_kernel(const double *__restrict__ part_rz, const double *__restrict__ part_rr,
+                                        int nb, Scalars *sc) {
+  __shared__ double sh[RED_THREADS];
+  double a = 0.0, b = 0.0;
+  for (int i = threadIdx.x; i < nb; i += RED_THREADS) {
+    a += part_rz[i];
+    b += part_rr[i];
+  }
+  a = block_sum(a, sh);
+  b = block_sum(b, sh);
+  if (threadIdx.x == 0) {
+    sc->beta = a / sc->rz;
+    sc->rz = a;
+    sc->rr = b;
+    sc->nonfinite = (!finite(a) || !finite(b) || !finite(sc->beta)) ? 1 : 0;
+    sc->done = sc->nonfinite || b == 0.0;
+  }
+}
+
 __global__ void pupdate_kernel(double *__restrict__ p, const double *__restrict__ z, int64_t n, const Scalars *sc) {
   if (sc->done) return;
   const double beta = sc->beta;
   CEEDGB_GRID4(p[k] = z[k] + beta * p[k];)
 }
 
-// CG start from r (already holding the initial residual): z = dinv r, p = z, partials of r.z, r.r
+// CG start from r (already holding the initial residual): z = dinv r, p = z (set_p), partials of
+// r.z, r.r.  Without set_p (residual replacement of the reliable-update CG) the direction p is kept.
 __global__ void start_kernel(const double *__restrict__ r, double *__restrict__ z, double *__restrict__ p,
                              const double *__restrict__ dinv, int64_t n, double *__restrict__ part_rz,
-                             double *__restrict__ part_rr) {
+                             double *__restrict__ part_rr, int set_p) {
   __shared__ double sh[RED_THREADS];
   double arz[4] = {0.0, 0.0, 0.0, 0.0}, arr[4] = {0.0, 0.0, 0.0, 0.0};
   CEEDGB_GRID4({
     const double ri = r[k];
     const double zi = dinv[k] * ri;
     z[k] = zi;
-    p[k] = zi;
+    if (set_p) p[k] = zi;
     arz[u_] += ri * zi;
     arr[u_] += ri * ri;
   })
@@ -294,6 +318,34 @@ static int read_scalars(Scalars *h, const Scalars *d, cudaStream_t s) {
   return CEED_OK;
 }
 
+// One PCG iteration on the device scalars (no host round trip): q = A p, alpha, x/r/z update, beta,
+// p update.  no_stop: the tolerance test never ends the iteration (the host decides).
+static int pcg_iteration(ceed_mesh_t m, const ApplyReq &op, double *y, const Work &w, int64_t n, bool no_stop,
+                         cudaStream_t s) {
+  const int nb = red_blocks(n);
+  // q = A p.  FP64 operator: p . q is summed by the apply itself (each node's last writer adds
+  // p_i q_i), saving two vector passes at no cost to the FP64-pipe-bound kernel.  FP32 operators
+  // keep the separate reduction (FP64 products inside them would cost more than the passes).
+  ApplyReq a = op;
+  a.x = w.p;
+  a.y = w.q;
+  const bool fuse = (op.prec == CEED_F64);
+  a.dot_part = fuse ? w.pq_part : nullptr;
+  int64_t npart = 0;
+  a.dot_n = &npart;
+  if (int st = launch_apply(m, a, s)) return st;
+  if (fuse) {
+    finalize_alpha_kernel<<<1, 1024, 0, s>>>(w.pq_part, npart, w.sc);
+  } else {
+    dot_partial_kernel<<<nb, RED_THREADS, 0, s>>>(w.p, w.q, n, w.part1, w.sc);
+    finalize_alpha_kernel<<<1, 1024, 0, s>>>(w.part1, nb, w.sc);
+  }
+  update_kernel<<<nb, RED_THREADS, 0, s>>>(y, w.r, w.z, w.p, w.q, w.dinv, n, w.part1, w.part2, w.sc);
+  finalize_beta_kernel<<<1, RED_THREADS, 0, s>>>(w.part1, w.part2, nb, w.sc, no_stop ? 1 : 0);
+  pupdate_kernel<<<stream_blocks(n), 256, 0, s>>>(w.p, w.z, n, w.sc);
+  return CEED_OK;
+}
+
 // Run PCG on A y = rhs (y starts at 0; rhs in w.r on entry), with the given operator.
 // Stops when ||r|| <= tol ||ref|| (ref = rhs), or after max_iter iterations, or exactly `fixed` iterations.
 static int pcg_run(ceed_mesh_t m, const ApplyReq &op, double *y, const Work &w, int64_t n, double tol, int max_iter,
@@ -304,35 +356,15 @@ static int pcg_run(ceed_mesh_t m, const ApplyReq &op, double *y, const Work &w, 
   h.tol2 = tol * tol;
   CEED_CUDA_CHECK(cudaMemcpyAsync(&w.sc->tol2, &h.tol2, sizeof(double), cudaMemcpyHostToDevice, s));
   zero_kernel<<<stream_blocks(n), 256, 0, s>>>(y, n);
-  start_kernel<<<nb, RED_THREADS, 0, s>>>(w.r, w.z, w.p, w.dinv, n, w.part1, w.part2);
+  start_kernel<<<nb, RED_THREADS, 0, s>>>(w.r, w.z, w.p, w.dinv, n, w.part1, w.part2, 1);
   start_finalize_kernel<<<1, RED_THREADS, 0, s>>>(w.part1, w.part2, nb, w.sc, 1, fixed > 0);
   CEED_CUDA_CHECK(cudaGetLastError());
   const int cap = fixed > 0 ? fixed : max_iter;
   int it = 0;
   while (it < cap) {
     const int batch = std::min(cap - it, fixed > 0 ? cap : check_every);
-    for (int b = 0; b < batch; ++b) {
-      // q = A p.  FP64 operator: p . q is summed by the apply itself (each node's last writer adds
-      // p_i q_i), saving two vector passes at no cost to the FP64-pipe-bound kernel.  FP32 operators
-      // keep the separate reduction (FP64 products inside them would cost more than the passes).
-      ApplyReq a = op;
-      a.x = w.p;
-      a.y = w.q;
-      const bool fuse = (op.prec == CEED_F64);
-      a.dot_part = fuse ? w.pq_part : nullptr;
-      int64_t npart = 0;
-      a.dot_n = &npart;
-      if (int st = launch_apply(m, a, s)) return st;
-      if (fuse) {
-        finalize_alpha_kernel<<<1, 1024, 0, s>>>(w.pq_part, npart, w.sc);
-      } else {
-        dot_partial_kernel<<<nb, RED_THREADS, 0, s>>>(w.p, w.q, n, w.part1, w.sc);
-        finalize_alpha_kernel<<<1, 1024, 0, s>>>(w.part1, nb, w.sc);
-      }
-      update_kernel<<<nb, RED_THREADS, 0, s>>>(y, w.r, w.z, w.p, w.q, w.dinv, n, w.part1, w.part2, w.sc);
-      finalize_beta_kernel<<<1, RED_THREADS, 0, s>>>(w.part1, w.part2, nb, w.sc, fixed > 0);
-      pupdate_kernel<<<stream_blocks(n), 256, 0, s>>>(w.p, w.z, n, w.sc);
-    }
+    for (int b = 0; b < batch; ++b)
+      if (int st = pcg_iteration(m, op, y, w, n, fixed > 0, s)) return st;
     CEED_CUDA_CHECK(cudaGetLastError());
     it += batch;
     if (int st = read_scalars(&h, w.sc, s)) return st;
@@ -362,6 +394,77 @@ static int residual(ceed_mesh_t m, const ApplyReq &op, const double *b, const do
   return CEED_OK;
 }
 
+
+// Jacobi-PCG on A x = b run with the low-precision operator `lo`, with reliable updates (residual
+// replacement; Sleijpen and van der Vorst, Computing 56, 1996): x and every vector stay FP64.  The
+// device stops an iteration before its beta step once the recurrence residual has fallen by `delta`
+// since the last replacement (or has met the tolerance); the host then evaluates the true residual
+// b - A x with the FP64 operator `hi`, stops if it meets tol, and otherwise puts it in place of the
+// recurrence residual and completes the stopped step with it (z = D^{-1} r, beta = r.z / r.z_old,
+// p = z + beta p), so the Krylov process is not restarted.  x holds the initial guess.  Counts:
+// iterations, true-residual evaluations.
+static int reliable_run(ceed_mesh_t m, const ApplyReq &hi, const ApplyReq &lo, const double *b, double *x,
+                        const Work &w, int64_t n, double bb, double tol, double delta, int max_iter, int check_every,
+                        cudaStream_t s, int *iters_out, int *evals_out, double *rel_out, int *nonfinite) {
+  const int nb = red_blocks(n);
+  *iters_out = 0;
+  *evals_out = 1;
+  *nonfinite = 0;
+  double rr = 0.0;
+  if (int st = residual(m, hi, b, x, w.q, w.r, n, w.part1, &w.sc->rr_out, s, &rr)) return st;
+  *rel_out = std::sqrt(rr / bb);
+  if (!std::isfinite(rr)) {
+    *nonfinite = 1;
+    return CEED_OK;
+  }
+  if (*rel_out <= tol) return CEED_OK;
+  // device stop threshold: rr <= tol2 * bb with tol2 = max(tol^2, delta^2 rr_ref / bb)
+  auto set_stop = [&](double rr_ref) -> int {
+    static_assert(offsetof(Scalars, tol2) == offsetof(Scalars, bb) + sizeof(double), "Scalars layout");
+    const double v[2] = {bb, std::max(tol * tol, delta * delta * rr_ref / bb)};  // Scalars::bb, ::tol2
+    CEED_CUDA_CHECK(cudaMemcpyAsync(&w.sc->bb, v, sizeof(v), cudaMemcpyHostToDevice, s));
+    CEED_CUDA_CHECK(cudaStreamSynchronize(s));  // v lives on this stack frame
+    return CEED_OK;
+  };
+  if (int st = set_stop(rr)) return st;
+  start_kernel<<<nb, RED_THREADS, 0, s>>>(w.r, w.z, w.p, w.dinv, n, w.part1, w.part2, 1);
+  start_finalize_kernel<<<1, RED_THREADS, 0, s>>>(w.part1, w.part2, nb, w.sc, 0, 0);
+  CEED_CUDA_CHECK(cudaGetLastError());
+  Scalars h{};
+  int it = 0;
+  // every batch completes at least one iteration (a replacement leaves done = 0), so the batch count
+  // bound only guards against a stuck state
+  for (int batches = 0; it < max_iter && batches <= max_iter; ++batches) {
+    const int batch = std::min(max_iter - it, check_every);
+    for (int k = 0; k < batch; ++k)
+      if (int st = pcg_iteration(m, lo, x, w, n, false, s)) return st;
+    CEED_CUDA_CHECK(cudaGetLastError());
+    if (int st = read_scalars(&h, w.sc, s)) return st;
+    it = h.iters;  // completed iterations since the start (replacements do not reset the count)
+    if (h.nonfinite) {
+      *nonfinite = 1;
+      break;
+    }
+    // the true residual is evaluated at every stop and at the cap, so *rel_out describes the final x
+    if (!h.done && it < max_iter) continue;
+    if (int st = residual(m, hi, b, x, w.q, w.r_out, n, w.part1, &w.sc->rr_out, s, &rr)) return st;
+    *evals_out += 1;
+    *rel_out = std::sqrt(rr / bb);
+    if (!std::isfinite(rr)) {
+      *nonfinite = 1;
+      break;
+    }
+    if (*rel_out <= tol || !h.done) break;  // converged, or at the cap
+    copy_kernel<<<stream_blocks(n), 256, 0, s>>>(w.r, w.r_out, n);
+    if (int st = set_stop(rr)) return st;
+    start_kernel<<<nb, RED_THREADS, 0, s>>>(w.r, w.z, w.p, w.dinv, n, w.part1, w.part2, 0);
+    replace_finalize_kernel<<<1, RED_THREADS, 0, s>>>(w.part1, w.part2, nb, w.sc);
+    pupdate_kernel<<<stream_blocks(n), 256, 0, s>>>(w.p, w.z, n, w.sc);
+    CEED_CUDA_CHECK(cudaGetLastError());
+  }
+  *iters_out = it;
+  return CEED_OK;
+}
 
 // ---------------------------------------------------------------- p-multigrid (V-cycle)
 __global__ void cheb_init_kernel(double *__restrict__ x, double *__restrict__ r, double *__restrict__ d,
@@ -657,6 +760,7 @@ static void fill_defaults(const ceed_cg_opts *in, ceed_cg_opts *o) {
   if (o->check_every <= 0) o->check_every = 10;
   if (o->tol <= 0) o->tol = 1e-10;
   if (o->inner_tol <= 0) o->inner_tol = 1e-4;
+  if (o->reliable_delta == 0.0) o->reliable_delta = 0.1;
 }
 
 extern "C" size_t ceed_cg_workspace_bytes(ceed_mesh_t m, const ceed_cg_opts *opts) {
@@ -675,10 +779,15 @@ extern "C" int ceed_cg_solve(ceed_mesh_t m, const void *qdata, int prec, const d
   if (((uintptr_t)work & 255) != 0) return fail(CEED_ERR_INVALID, "workspace must be 256-byte aligned");
   ceed_cg_opts o;
   fill_defaults(opts_in, &o);
-  const bool mixed = o.mode == CEED_CG_MIXED;
+  if (o.mode != CEED_CG_FP64 && o.mode != CEED_CG_MIXED && o.mode != CEED_CG_MIXED_RELIABLE)
+    return fail(CEED_ERR_INVALID, "unknown CG mode");
+  const bool reliable = o.mode == CEED_CG_MIXED_RELIABLE;
+  const bool mixed = o.mode == CEED_CG_MIXED || reliable;
   if (mixed && (!o.qdata_lo || (o.prec_lo != CEED_F32 && o.prec_lo != CEED_BF16 && o.prec_lo != CEED_F16 &&
-                                 o.prec_lo != CEED_F32_GEO)))
-    return fail(CEED_ERR_INVALID, "MIXED mode needs qdata_lo in F32, BF16, F16 or F32_GEO");
+                                 o.prec_lo != CEED_F32_GEO && o.prec_lo != CEED_F64_DF)))
+    return fail(CEED_ERR_INVALID, "MIXED modes need qdata_lo in F32, BF16, F16, F32_GEO or F64_DF");
+  if (reliable && !(o.reliable_delta > 0.0 && o.reliable_delta < 1.0))
+    return fail(CEED_ERR_INVALID, "reliable_delta must lie in (0, 1)");
   if (o.op != CEED_OP_MASS && o.op != CEED_OP_DIFFUSION) return fail(CEED_ERR_INVALID, "unknown operator");
   const int64_t n = m->n_ldof;
   if (work_bytes < layout(n, m->E, mixed, nullptr, nullptr)) return fail(CEED_ERR_INVALID, "workspace too small");
@@ -724,7 +833,19 @@ extern "C" int ceed_cg_solve(ceed_mesh_t m, const void *qdata, int prec, const d
     oplo.prec = o.prec_lo;
     oplo.qdata = o.qdata_lo;
   }
-  if (o.fixed_iters > 0) {
+  if (reliable && o.fixed_iters <= 0) {
+    if (!o.use_x0) zero_kernel<<<stream_blocks(n), 256, 0, s>>>(x, n);
+    int iters = 0, evals = 0, nonfin = 0;
+    double rel = 0.0;
+    if (int st = reliable_run(m, op64, oplo, b, x, w, n, bb, o.tol, o.reliable_delta, o.max_iter, o.check_every, s,
+                              &iters, &evals, &rel, &nonfin))
+      return st;
+    report->iterations = iters;
+    report->outer_iterations = evals;
+    report->rel_residual = rel;
+    if (nonfin) status = fail(CEED_ERR_NONFINITE, "non-finite value in a CG reduction");
+    else if (!(rel <= o.tol)) status = fail(CEED_ERR_NOT_CONVERGED, "CG reached its iteration cap");
+  } else if (o.fixed_iters > 0) {
     // exactly fixed_iters PCG iterations from x0 = 0 with the FP64 operator (timing runs)
     copy_kernel<<<stream_blocks(n), 256, 0, s>>>(w.r, b, n);
     int iters = 0, nonfin = 0;
@@ -754,7 +875,9 @@ extern "C" int ceed_cg_solve(ceed_mesh_t m, const void *qdata, int prec, const d
         break;
       }
       copy_kernel<<<stream_blocks(n), 256, 0, s>>>(w.r, w.r_out, n);
-      const double inner = mixed ? o.inner_tol : std::min(0.5, 0.5 * o.tol / report->rel_residual);
+      // no pass aims further than half of what remains to the tolerance: MIXED passes reduce by
+      // inner_tol, except a last one that needs less
+      const double inner = std::min(0.5, std::max(mixed ? o.inner_tol : 0.0, 0.5 * o.tol / report->rel_residual));
       int iters = 0, nonfin = 0;
       if (!mixed && o.pmg) {
         // p-multigrid-preconditioned flexible CG on A d = r_out

@@ -63,7 +63,7 @@ def test_cg_fp64_matches_direct_solve(ceed, N, p):
     mesh.close()
 
 
-@pytest.mark.parametrize("prec_lo", [1, 2, 3, 4])
+@pytest.mark.parametrize("prec_lo", [1, 2, 3, 4, 5])
 def test_mixed_refinement_reaches_fp64_tolerance(ceed, prec_lo):
     N, p = 3, 5
     m, mesh, qd, b = _setup(ceed, N, p)
@@ -79,6 +79,80 @@ def test_mixed_refinement_reaches_fp64_tolerance(ceed, prec_lo):
     print(f"mixed prec {prec_lo}: outer {rep['outer_iterations']} inner {rep['iterations']}")
     mesh.close()
 
+
+@pytest.mark.parametrize("prec_lo", [1, 2, 4, 5])
+def test_mixed_reliable_reaches_fp64_tolerance(ceed, prec_lo):
+    # reliable updates: one PCG run with the low-precision operator, true FP64 residual put in place
+    # at every 10x decrease; it reaches the FP64 tolerance in about the FP64 iteration count and in no
+    # more iterations than restarted refinement with the same inner operator
+    N, p = 3, 5
+    m, mesh, qd, b = _setup(ceed, N, p)
+    A, bref, xref = _oracle_solution(m, p)
+    qlo = ceed.alloc_qdata(mesh, ceed.CEED_OP_DIFFUSION, prec_lo)
+    ceed.ceed_build_qdata(mesh, ceed.CEED_OP_DIFFUSION, ceed.CEED_COEFF_SINE, None, prec_lo, qlo)
+    x = torch.empty_like(b)
+    st, rep = ceed.ceed_cg_solve(mesh, qd, ceed.CEED_F64, b, x, mode=ceed.CEED_CG_MIXED_RELIABLE, tol=1e-10,
+                                 op=ceed.CEED_OP_DIFFUSION, qdata_lo=qlo, prec_lo=prec_lo, max_iter=5000)
+    assert st == ceed.CEED_OK and rep["rel_residual"] <= 1e-10
+    xh = x.cpu().numpy()
+    assert np.linalg.norm(bref - A @ xh) <= 1.5e-10 * np.linalg.norm(bref)
+    assert rel_err(xh, xref) <= 1e-8
+    assert rep["outer_iterations"] >= 2
+    _, rep64 = ceed.ceed_cg_solve(mesh, qd, ceed.CEED_F64, b, torch.empty_like(b), mode=ceed.CEED_CG_FP64,
+                                  tol=1e-10, op=ceed.CEED_OP_DIFFUSION)
+    _, repm = ceed.ceed_cg_solve(mesh, qd, ceed.CEED_F64, b, torch.empty_like(b), mode=ceed.CEED_CG_MIXED,
+                                 tol=1e-10, op=ceed.CEED_OP_DIFFUSION, qdata_lo=qlo, prec_lo=prec_lo)
+    # host checks every 10 iterations: up to 9 iterations past each trigger
+    assert rep["iterations"] <= 1.3 * rep64["iterations"] + 10, (rep, rep64)
+    assert rep["iterations"] <= repm["iterations"] + 10, (rep, repm)
+    print(f"prec {prec_lo}: reliable {rep['iterations']} ({rep['outer_iterations']} true residuals), "
+          f"refinement {repm['iterations']}, fp64 {rep64['iterations']}")
+    mesh.close()
+
+
+def test_mixed_modes_reject_bad_options(ceed):
+    N, p = 2, 3
+    m, mesh, qd, b = _setup(ceed, N, p)
+    x = torch.empty_like(b)
+    with pytest.raises(ceed.CeedError):          # no low-precision operator
+        ceed.ceed_cg_solve(mesh, qd, ceed.CEED_F64, b, x, mode=ceed.CEED_CG_MIXED_RELIABLE)
+    qlo = ceed.alloc_qdata(mesh, ceed.CEED_OP_DIFFUSION, ceed.CEED_F32)
+    ceed.ceed_build_qdata(mesh, ceed.CEED_OP_DIFFUSION, ceed.CEED_COEFF_SINE, None, ceed.CEED_F32, qlo)
+    for delta in (-0.5, 1.0, 2.0):
+        with pytest.raises(ceed.CeedError):
+            ceed.ceed_cg_solve(mesh, qd, ceed.CEED_F64, b, x, mode=ceed.CEED_CG_MIXED_RELIABLE, qdata_lo=qlo,
+                               prec_lo=ceed.CEED_F32, reliable_delta=delta)
+    with pytest.raises(ceed.CeedError):
+        ceed.ceed_cg_solve(mesh, qd, ceed.CEED_F64, b, x, mode=7)
+    mesh.close()
+    # an iteration cap reports NOT_CONVERGED with the true residual of the final x filled in (this
+    # problem needs about 110 iterations)
+    m, mesh, qd, b = _setup(ceed, 3, 5)
+    qlo = ceed.alloc_qdata(mesh, ceed.CEED_OP_DIFFUSION, ceed.CEED_F32)
+    ceed.ceed_build_qdata(mesh, ceed.CEED_OP_DIFFUSION, ceed.CEED_COEFF_SINE, None, ceed.CEED_F32, qlo)
+    x = torch.empty_like(b)
+    st, rep = ceed.ceed_cg_solve(mesh, qd, ceed.CEED_F64, b, x, mode=ceed.CEED_CG_MIXED_RELIABLE, qdata_lo=qlo,
+                                 prec_lo=ceed.CEED_F32, max_iter=10, op=ceed.CEED_OP_DIFFUSION, raise_on_error=False)
+    assert st == ceed.CEED_ERR_NOT_CONVERGED and rep["iterations"] == 10
+    A, bref, _ = _oracle_solution(m, 5)
+    true_rel = np.linalg.norm(bref - A @ x.cpu().numpy()) / np.linalg.norm(bref)
+    assert 0 < rep["rel_residual"] < 1 and abs(rep["rel_residual"] - true_rel) <= 1e-6 * true_rel
+    mesh.close()
+
+
+def test_mixed_reliable_on_an_exactly_converging_problem(ceed):
+    # a small symmetric problem whose Krylov space closes within a few iterations: the recurrence
+    # residual reaches zero, the device stops and the host certifies with the true residual
+    m, mesh, qd, b = _setup(ceed, 2, 3)
+    qlo = ceed.alloc_qdata(mesh, ceed.CEED_OP_DIFFUSION, ceed.CEED_F32)
+    ceed.ceed_build_qdata(mesh, ceed.CEED_OP_DIFFUSION, ceed.CEED_COEFF_SINE, None, ceed.CEED_F32, qlo)
+    x = torch.empty_like(b)
+    st, rep = ceed.ceed_cg_solve(mesh, qd, ceed.CEED_F64, b, x, mode=ceed.CEED_CG_MIXED_RELIABLE, qdata_lo=qlo,
+                                 prec_lo=ceed.CEED_F32, tol=1e-10, op=ceed.CEED_OP_DIFFUSION)
+    A, bref, _ = _oracle_solution(m, 3)
+    assert np.linalg.norm(bref - A @ x.cpu().numpy()) <= 1.5e-10 * np.linalg.norm(bref)
+    assert st == ceed.CEED_OK and rep["rel_residual"] <= 1e-10
+    mesh.close()
 
 def test_cg_fixed_iterations_and_cap(ceed):
     m, mesh, qd, b = _setup(ceed, 3, 4)

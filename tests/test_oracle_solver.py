@@ -44,6 +44,37 @@ def test_pcg_exact_in_n_steps_small():
     np.testing.assert_allclose(x, np.linalg.solve(A, b), rtol=1e-14)
 
 
+def test_reliable_pcg_with_exact_operator_is_pcg():
+    # with apply_lo = apply_hi the replaced residual equals the recurrence one up to rounding, so the
+    # reliable-update run takes the ordinary PCG iterates
+    m, sp_, G, Am, b, d = _problem(3, 3)
+    A = lambda v: Am @ v
+    x0, it0, _, _ = fem.pcg(A, b, 1.0 / d, tol=1e-10, maxit=2000)
+    x1, it1, rel1, evals = fem.pcg_reliable(A, A, b, 1.0 / d, tol=1e-10, delta=0.1)
+    assert rel1 <= 1e-10 and evals >= 10
+    assert abs(it1 - it0) <= 1
+    np.testing.assert_allclose(x1, x0, rtol=0, atol=1e-9 * np.abs(x0).max())
+
+
+def test_reliable_pcg_recovers_fp64_accuracy_from_a_perturbed_operator():
+    # the inner operator carries relative errors of 1e-6 in its entries (far coarser than FP32
+    # rounding of the matrix-free operator): plain PCG on it stalls near the perturbation level in
+    # the true residual, residual replacement reaches 1e-10 in about the exact iteration count
+    m, sp_, G, Am, b, d = _problem(3, 4)
+    rng = np.random.default_rng(5)
+    E = Am.copy()
+    E.data = E.data * (1.0 + 1e-6 * rng.uniform(-1, 1, size=E.data.size))
+    E = 0.5 * (E + E.T)
+    lo, hi = (lambda v: E @ v), (lambda v: Am @ v)
+    _, it_exact, _, _ = fem.pcg(hi, b, 1.0 / d, tol=1e-10, maxit=5000)
+    x_plain, _, _, _ = fem.pcg(lo, b, 1.0 / d, tol=1e-12, maxit=5000)
+    plain_true = np.linalg.norm(b - Am @ x_plain) / np.linalg.norm(b)
+    x, it, rel, evals = fem.pcg_reliable(lo, hi, b, 1.0 / d, tol=1e-10, delta=0.1)
+    assert plain_true > 1e-9
+    assert rel <= 1e-10 and np.linalg.norm(b - Am @ x) <= 1e-10 * np.linalg.norm(b)
+    assert it <= 1.25 * it_exact + 5, (it, it_exact)
+    assert evals >= 3
+
 def test_manufactured_source_closed_form():
     # f = -div(k grad u*) checked against a finite-difference divergence of k grad u* at a few points
     rng = np.random.default_rng(0)
