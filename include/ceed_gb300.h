@@ -133,6 +133,16 @@ int ceed_apply_mass(ceed_mesh_t mesh, const void *qdata, int prec, const double 
 int ceed_apply_diffusion(ceed_mesh_t mesh, const void *qdata, int prec, const double *x, double *y,
                          int nrhs, unsigned flags, void *stream);
 
+/* Host-buffer form of the two actions, for callers whose vectors live in host memory: copies
+ * x_host into the caller's device buffer x_dev, applies the operator `op` (CEED_OP_MASS or
+ * CEED_OP_DIFFUSION; qdata, prec, nrhs, flags as for ceed_apply_mass / ceed_apply_diffusion) into
+ * y_dev, and copies y_dev into y_host, all on `stream`, and returns once y_host holds the result
+ * (synchronizes `stream`).  x_host, y_host: host FP64 [n_ldof * ncomp * nrhs]; page-locked memory
+ * copies at full link bandwidth, pageable memory goes through the driver's staging.  x_dev, y_dev:
+ * device FP64 of the same size, caller-owned, not overlapping.  Errors: INVALID, CUDA. */
+int ceed_apply_host(ceed_mesh_t mesh, int op, const void *qdata, int prec, const double *x_host, double *y_host,
+                    double *x_dev, double *y_dev, int nrhs, unsigned flags, void *stream);
+
 /* Autotuner (the batched-apply design calls for tile shape and elements per block chosen by
  * measurement): runs every variant of the fused apply kernel -- elements per thread block
  * (1, 2, 4, ... up to 256 threads and 32 elements) x quadrature-data staging (TMA bulk copy into shared memory,

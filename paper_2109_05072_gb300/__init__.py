@@ -89,6 +89,8 @@ def _load():
         "ceed_build_qdata": (ctypes.c_int, [vp, ctypes.c_int, ctypes.c_int, vp, ctypes.c_int, vp, vp]),
         "ceed_apply_mass": (ctypes.c_int, [vp, vp, ctypes.c_int, vp, vp, ctypes.c_int, u32, vp]),
         "ceed_apply_diffusion": (ctypes.c_int, [vp, vp, ctypes.c_int, vp, vp, ctypes.c_int, u32, vp]),
+        "ceed_apply_host": (ctypes.c_int, [vp, ctypes.c_int, vp, ctypes.c_int, vp, vp, vp, vp, ctypes.c_int, u32,
+                                           vp]),
         "ceed_jacobi_diagonal": (ctypes.c_int, [vp, ctypes.c_int, vp, ctypes.c_int, vp, u32, vp]),
         "ceed_set_apply_variant": (ctypes.c_int, [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int]),
         "ceed_autotune_apply": (ctypes.c_int, [vp, ctypes.c_int, vp, ctypes.c_int, vp, vp, ctypes.c_int,
@@ -169,6 +171,13 @@ def _ptr(t):
         raise ValueError("expected a CUDA tensor (the library computes on the GPU only)")
     if not t.is_contiguous():
         raise ValueError("expected a contiguous tensor")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _host_ptr(t):
+    """Address of a contiguous FP64 host tensor (a host buffer of ceed_apply_host)."""
+    if not isinstance(t, torch.Tensor) or t.is_cuda or not t.is_contiguous() or t.dtype != torch.float64:
+        raise ValueError("expected a contiguous float64 host tensor")
     return ctypes.c_void_p(t.data_ptr())
 
 
@@ -254,6 +263,17 @@ def ceed_apply_mass(mesh: Mesh, qdata, prec, x, y, nrhs=1, flags=0, stream=None)
 
 def ceed_apply_diffusion(mesh: Mesh, qdata, prec, x, y, nrhs=1, flags=0, stream=None):
     _check(_lib.ceed_apply_diffusion(mesh.handle, _ptr(qdata), prec, _ptr(x), _ptr(y), nrhs, flags, _stream(stream)))
+
+
+def ceed_apply_host(mesh: Mesh, op, qdata, prec, x_host, y_host, x_dev, y_dev, nrhs=1, flags=0, stream=None):
+    """y_host = A x_host through the device buffers x_dev, y_dev (copies and apply on `stream`; returns when
+    y_host holds the result)."""
+    n = mesh.n_ldof * mesh.ncomp * nrhs
+    for t in (x_host, y_host, x_dev, y_dev):
+        if t.numel() < n:
+            raise ValueError("buffer smaller than n_ldof * ncomp * nrhs")
+    _check(_lib.ceed_apply_host(mesh.handle, op, _ptr(qdata), prec, _host_ptr(x_host), _host_ptr(y_host), _ptr(x_dev),
+                                _ptr(y_dev), nrhs, flags, _stream(stream)))
 
 
 def ceed_autotune_apply(mesh: Mesh, op, qdata, prec, x, y, nrhs=1, stream=None):

@@ -485,6 +485,22 @@ extern "C" int ceed_apply_diffusion(ceed_mesh_t m, const void *qdata, int prec, 
   return apply_common(m, CEED_OP_DIFFUSION, qdata, prec, x, y, nrhs, flags, stream);
 }
 
+extern "C" int ceed_apply_host(ceed_mesh_t m, int op, const void *qdata, int prec, const double *x_host,
+                               double *y_host, double *x_dev, double *y_dev, int nrhs, unsigned flags, void *stream) {
+  if (int st = check_mesh(m)) return st;
+  if (!x_host || !y_host || !x_dev || !y_dev) return fail(CEED_ERR_INVALID, "null host or device buffer");
+  if (x_dev == y_dev) return fail(CEED_ERR_INVALID, "x_dev and y_dev must not alias");
+  if (op != CEED_OP_MASS && op != CEED_OP_DIFFUSION) return fail(CEED_ERR_INVALID, "unknown operator");
+  if (nrhs < 1) return fail(CEED_ERR_INVALID, "nrhs must be >= 1");
+  const size_t bytes = (size_t)m->n_ldof * (size_t)m->ncomp * (size_t)nrhs * sizeof(double);
+  cudaStream_t s = (cudaStream_t)stream;
+  CEED_CUDA_CHECK(cudaMemcpyAsync(x_dev, x_host, bytes, cudaMemcpyHostToDevice, s));
+  if (int st = apply_common(m, op, qdata, prec, x_dev, y_dev, nrhs, flags, stream)) return st;
+  CEED_CUDA_CHECK(cudaMemcpyAsync(y_host, y_dev, bytes, cudaMemcpyDeviceToHost, s));
+  CEED_CUDA_CHECK(cudaStreamSynchronize(s));
+  return CEED_OK;
+}
+
 // ---------------------------------------------------------------------------------------------
 // Autotuner for the apply kernel: times every (elements per block, staging) variant on the
 // caller's mesh, quadrature data and vectors, and keeps the fastest for (op, prec) in the handle.

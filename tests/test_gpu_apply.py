@@ -246,3 +246,35 @@ def test_apply_double_float_matches_oracle(ceed, p, qkind, op):
     Y = _apply(ceed, mesh, op, qd, ceed.CEED_F64_DF, X.reshape(-1), nrhs=3).reshape(m.n_ldof, 3)
     assert rel_err(Y, fem.apply(sp_, m.elem_dofs, qref, X, kind)) <= 1e-12
     mesh.close()
+
+
+@pytest.mark.parametrize("pinned", [True, False])
+def test_host_buffer_apply(ceed, pinned):
+    # the host-buffer entry point runs the same kernels as the device form: bitwise-identical output,
+    # and the oracle's action within the FP64 parity bound
+    m = synthetic.HexMesh(3, 2, 2, 4, seed=4)
+    mesh = gpu_mesh(ceed, m, "gll", ncomp=1)
+    qd = _qdata(ceed, mesh, "diffusion", ceed.CEED_F64)
+    nrhs = 2
+    xh = torch.from_numpy(synthetic.uniform(m.n_ldof * nrhs, seed=9))
+    yh = torch.full_like(xh, float("nan"))
+    if pinned:
+        xh, yh = xh.pin_memory(), yh.pin_memory()
+    xd = torch.empty(m.n_ldof * nrhs, dtype=torch.float64, device="cuda")
+    yd = torch.empty_like(xd)
+    ceed.ceed_apply_host(mesh, ceed.CEED_OP_DIFFUSION, qd, ceed.CEED_F64, xh, yh, xd, yd, nrhs=nrhs)
+    y_ref = torch.empty_like(xd)
+    ceed.ceed_apply_diffusion(mesh, qd, ceed.CEED_F64, xh.cuda(), y_ref, nrhs=nrhs)
+    torch.cuda.synchronize()
+    assert torch.equal(yh, y_ref.cpu())
+    sp_, qref = oracle_qdata(m, "gll", "diffusion", "sine")
+    X = xh.numpy().reshape(m.n_ldof, nrhs)
+    Y = yh.numpy().reshape(m.n_ldof, nrhs)
+    for c in range(nrhs):
+        assert rel_err(Y[:, c], fem.apply(sp_, m.elem_dofs, qref, np.ascontiguousarray(X[:, c]), fem.DIFFUSION)) <= 1e-12
+    with pytest.raises(ValueError):          # device tensor passed as a host buffer
+        ceed.ceed_apply_host(mesh, ceed.CEED_OP_DIFFUSION, qd, ceed.CEED_F64, xd, yh, xd, yd, nrhs=nrhs)
+    with pytest.raises(ceed.CeedError):      # aliased device buffers
+        ceed.ceed_apply_host(mesh, ceed.CEED_OP_DIFFUSION, qd, ceed.CEED_F64, xh, yh, xd, xd, nrhs=nrhs)
+    mesh.close()
+
