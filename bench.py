@@ -157,6 +157,23 @@ def dist_env():
     return ws, rank, local
 
 
+def max_over_ranks(value: float, ws: int, device) -> float:
+    """The largest of the ranks' values (the job's time is its slowest replica's); identity at N = 1."""
+    if ws <= 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank: float, ws: int, ms: float, scale: float = 1e-6) -> float:
+    """Units all ranks processed per millisecond x scale (GDOF/s for DOFs with the default scale):
+    every replica processes the same units, and ms is the max over ranks."""
+    return ws * units_per_rank / ms * scale
+
+
 def run_reference(args):
     ws, rank, _ = dist_env()
     if rank != 0:
@@ -463,12 +480,7 @@ def main():
         e1.record(stream)
         torch.cuda.synchronize()
         barrier()
-        ms = e0.elapsed_time(e1)
-        if ws > 1:
-            import torch.distributed as dist
-            t = torch.tensor([ms], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ms = t.item()
+        ms = max_over_ranks(e0.elapsed_time(e1), ws, dev)
         return ms / steps
 
     # ---------------- headline: FP64 apply (variant chosen by the library's autotuner first)
@@ -479,7 +491,7 @@ def main():
     apply64 = lambda: ceed.ceed_apply_diffusion(mesh, qd64, ceed.CEED_F64, x, y)
     with ClockSampler(local) as clk:
         ms64 = timed(apply64, args.steps, args.warmup)
-    gdofs64 = ws * n_apply / ms64 / 1e6
+    gdofs64 = whole_job_rate(n_apply, ws, ms64)
     reads, flops_el = cost_per_element(p)
     hbm_peak, hbm_kind = load_peaks()
     bytes64 = algorithmic_bytes(m, 8)
@@ -506,7 +518,7 @@ def main():
         torch.cuda.synchronize()
         rel = float(torch.linalg.vector_norm(ydf - y) / torch.linalg.vector_norm(y))
         relmax = float((ydf - y).abs().max() / y.abs().max())
-        f64df = {"gdofs": ws * n_apply / ms_df / 1e6, "ms": ms_df, "dtype": "f32x2 (double-float, compensated dot)",
+        f64df = {"gdofs": whole_job_rate(n_apply, ws, ms_df), "ms": ms_df, "dtype": "f32x2 (double-float, compensated dot)",
                  "rel_l2_vs_fp64": rel, "rel_max_vs_fp64": relmax,
                  "flops_tflops_paper_model": flops_el * m.n_elem / (ms_df * 1e-3) / 1e12,
                  "hbm_gbs": algorithmic_bytes(m, 8) / (ms_df * 1e-3) / 1e9,
@@ -525,7 +537,7 @@ def main():
             variants[name] = {"elems_per_block": ne, "tma_staging": st, "tuning_ms": tms}
         ms = timed(lambda: ceed.ceed_apply_diffusion(mesh, qlo, prec, x, y), args.steps, args.warmup)
         by = algorithmic_bytes(m, qb, geo=(prec == ceed.CEED_F32_GEO))
-        mixed[name] = {"gdofs": ws * m.n_ldof / ms / 1e6, "ms": ms, "alg_bytes": by,
+        mixed[name] = {"gdofs": whole_job_rate(m.n_ldof, ws, ms), "ms": ms, "alg_bytes": by,
                        "hbm_gbs": by / (ms * 1e-3) / 1e9, "hbm_frac": by / (ms * 1e-3) / 1e9 / hbm_peak}
         del qlo
     torch.cuda.empty_cache()
@@ -668,7 +680,7 @@ def main():
             "fp64_accurate_fp32_pipe": f64df,
             "mixed_apply": mixed,
             "apply_variants": variants,
-            "e2e": {"value": ws * n_apply / ms_e2e / 1e6,
+            "e2e": {"value": whole_job_rate(n_apply, ws, ms_e2e),
                     "unit": "GDOF/s", "h2d_bytes_per_step": 8 * len(x_host), "d2h_bytes_per_step": 8 * len(x_host),
                     "call": "ceed_apply_host (pinned host x, y; copies and apply inside the timed region)"},
             "gpu_launches": args.steps * launches_per_apply,
