@@ -305,6 +305,41 @@ def run_adjoint(ceed, dev, args):
     return out
 
 
+def run_cg_c4(ceed, dev, args):
+    """CG to a true relative residual of 1e-10 on 80^3 elements, p = 7 (176,558,481 DOFs): FP64
+    Jacobi-PCG, mixed refinement and reliable updates with the FP32 operator; the mixed solutions'
+    difference from the FP64 solution is reported."""
+    import torch
+    wl = WORKLOADS["c4"]
+    m = synthetic.cube_mesh(wl["N"], wl["p"], seed=0)
+    mesh = ceed.ceed_setup_mesh(m.n_elem, m.n_ldof, wl["p"], torch.from_numpy(m.elem_dofs).to(dev),
+                                torch.from_numpy(m.vertices).to(dev), torch.from_numpy(m.boundary).to(dev))
+    q64 = ceed.alloc_qdata(mesh, ceed.CEED_OP_DIFFUSION, ceed.CEED_F64, dev)
+    ceed.ceed_build_qdata(mesh, ceed.CEED_OP_DIFFUSION, ceed.CEED_COEFF_SINE, None, ceed.CEED_F64, q64)
+    q32 = ceed.alloc_qdata(mesh, ceed.CEED_OP_DIFFUSION, ceed.CEED_F32, dev)
+    ceed.ceed_build_qdata(mesh, ceed.CEED_OP_DIFFUSION, ceed.CEED_COEFF_SINE, None, ceed.CEED_F32, q32)
+    b = torch.empty(m.n_ldof, dtype=torch.float64, device=dev)
+    ceed.ceed_manufactured_rhs(mesh, ceed.CEED_COEFF_SINE, b, flags=ceed.CEED_APPLY_DIRICHLET)
+    out = {"workload": f"{wl['N']}^3, p={wl['p']}, n_ldof={m.n_ldof}"}
+    x64 = torch.empty_like(b)
+    st, rep = ceed.ceed_cg_solve(mesh, q64, ceed.CEED_F64, b, x64, mode=ceed.CEED_CG_FP64, tol=1e-10,
+                                 max_iter=20000, op=ceed.CEED_OP_DIFFUSION, raise_on_error=False)
+    out["fp64_to_1e-10"] = dict(rep, status=st)
+    xm = torch.empty_like(b)
+    for name, mode in (("mixed_f32", ceed.CEED_CG_MIXED), ("mixed_f32_reliable", ceed.CEED_CG_MIXED_RELIABLE)):
+        st, repm = ceed.ceed_cg_solve(mesh, q64, ceed.CEED_F64, b, xm, mode=mode, tol=1e-10, max_iter=20000,
+                                      op=ceed.CEED_OP_DIFFUSION, qdata_lo=q32, prec_lo=ceed.CEED_F32,
+                                      raise_on_error=False)
+        diff = float(torch.linalg.vector_norm(xm - x64) / torch.linalg.vector_norm(x64))
+        out[f"{name}_to_1e-10"] = dict(repm, status=st, rel_diff_from_fp64_solution=diff)
+        if rep["seconds"] > 0 and repm["seconds"] > 0:
+            out[f"{name}_speedup"] = rep["seconds"] / repm["seconds"]
+    mesh.close()
+    del q64, q32, b, x64, xm
+    torch.cuda.empty_cache()
+    return out
+
+
 def nt_workload(ceed, dev, p=4, q=5, N=48):
     """Degree-p tetrahedra, 6 per cube of the perturbed N^3 lattice, conical rule with q points per direction."""
     import torch
@@ -428,6 +463,8 @@ def main():
     ap.add_argument("--df", type=int, default=1, help="measure the double-float FP64-accurate operator")
     ap.add_argument("--nontensor", type=int, default=1, help="measure the non-tensor (tetrahedral) operator")
     ap.add_argument("--hp", type=int, default=1, help="measure the conforming mixed-order (hp) operator")
+    ap.add_argument("--cg-c4", type=int, default=0,
+                    help="also run CG to 1e-10 on 80^3 elements, p = 7 (FP64 vs mixed; about three minutes)")
     ap.add_argument("--nt-profile", default=None, choices=["fused64", "fused32", "gemm32", "tc"],
                     help="profiling case: three tetrahedral diffusion applies with one algorithm, then exit")
     args = ap.parse_args()
@@ -649,6 +686,11 @@ def main():
     if args.hp:
         hp = run_hp(ceed, dev, args)
 
+    # ---------------- CG on the 176.6M-DOF mesh (opt-in: minutes of solver time)
+    cg_c4 = None
+    if args.cg_c4:
+        cg_c4 = run_cg_c4(ceed, dev, args)
+
     # ---------------- CPU oracle on a bounded sample (rank 0, N = 1 only)
     cpu = None
     if rank == 0 and ws == 1 and args.cpu_sample > 0:
@@ -690,6 +732,7 @@ def main():
             "adjoint": adjoint,
             "nontensor": nontensor,
             "hp": hp,
+            "cg_80cube": cg_c4,
             "cpu_baseline": cpu,
         }
         print(json.dumps(line), flush=True)
