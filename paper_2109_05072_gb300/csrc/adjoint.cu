@@ -238,11 +238,7 @@ template <int P, bool ADJ>
 static int run_kop(ceed_mesh_t m, KArgs a, cudaStream_t s) {
   constexpr int NE = kop_ne<P>();
   const size_t smem = NE * kop_elem_smem<P, ADJ>();
-  static size_t configured = 0;
-  if (smem > configured) {
-    CEED_CUDA_CHECK(cudaFuncSetAttribute(kop_kernel<P, ADJ>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    configured = smem;
-  }
+  if (int st = ensure_dynamic_smem((const void *)kop_kernel<P, ADJ>, smem)) return st;
   for (int c = 0; c < m->n_colors; ++c) {
     a.e_begin = m->color_start[c];
     a.e_count = m->color_start[c + 1] - a.e_begin;

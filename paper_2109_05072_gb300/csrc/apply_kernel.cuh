@@ -576,12 +576,7 @@ apply_kernel(const ApplyArgs a, const OpTab<T> tab) {
 template <int P, int Q, int OP, typename T, typename TQ, bool STAGE>
 int launch_variant(ceed_mesh_t m, const OpTab<T> &tab, const ApplyReq &r, int ne, cudaStream_t s) {
   const size_t smem = (size_t)ne * apply_elem_smem<P, Q, OP, T, TQ, STAGE>();
-  static size_t configured = 0;  // per instantiation: the largest dynamic shared memory requested so far
-  if (smem > configured) {
-    CEED_CUDA_CHECK(cudaFuncSetAttribute(apply_kernel<P, Q, OP, T, TQ, STAGE>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    configured = smem;
-  }
+  if (int st = ensure_dynamic_smem((const void *)apply_kernel<P, Q, OP, T, TQ, STAGE>, smem)) return st;
   const dim3 block(Q * Q * ne);
   ApplyArgs a;
   a.emap = m->d_emap;

@@ -114,6 +114,9 @@ int cuda_fail(cudaError_t e, const char *where);
   } while (0)
 
 int check_mesh(ceed_mesh_t m);
+// Raises the dynamic shared-memory limit of kernel `func` to at least `bytes` on the current device
+// (the opt-in is a per-context attribute), once per (kernel, device, size); thread-safe.
+int ensure_dynamic_smem(const void *func, size_t bytes);
 int nq_of(const ceed_mesh_t m);
 size_t prec_size(int prec);
 

@@ -2,8 +2,11 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <map>
 #include <memory>
+#include <mutex>
 #include <new>
+#include <utility>
 
 #include "internal.h"
 
@@ -19,6 +22,21 @@ int fail(int status, const std::string &msg) {
 int cuda_fail(cudaError_t e, const char *where) {
   g_last_error = std::string(where) + ": " + cudaGetErrorString(e);
   return e == cudaErrorMemoryAllocation ? CEED_ERR_OOM : CEED_ERR_CUDA;
+}
+
+int ensure_dynamic_smem(const void *func, size_t bytes) {
+  if (bytes <= 48 * 1024) return CEED_OK;
+  int dev = 0;
+  CEED_CUDA_CHECK(cudaGetDevice(&dev));
+  static std::mutex mu;
+  static std::map<std::pair<const void *, int>, size_t> raised;  // (kernel, device) -> limit set so far
+  std::lock_guard<std::mutex> lock(mu);
+  size_t &cur = raised[{func, dev}];
+  if (bytes > cur) {
+    CEED_CUDA_CHECK(cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+    cur = bytes;
+  }
+  return CEED_OK;
 }
 
 int check_mesh(ceed_mesh_t m) {

@@ -370,12 +370,7 @@ static size_t nt_fused_smem(int P, int D, size_t tsize) {
 template <typename T, int D>
 static int launch_fused(ceed_nt_t h, const T *tab, const T *qd, const double *x, T *Ye, int masked, cudaStream_t s) {
   const size_t sm = nt_fused_smem(h->P, D, sizeof(T));
-  static uint64_t attr_set = 0;  // per device (bit = device ordinal): the opt-in is per context
-  const uint64_t bit = 1ull << (h->device & 63);
-  if (!(attr_set & bit)) {
-    CEED_CUDA_CHECK(cudaFuncSetAttribute(nt_fused_kernel<T, D>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
-    attr_set |= bit;
-  }
+  if (int st = ensure_dynamic_smem((const void *)nt_fused_kernel<T, D>, 227 * 1024)) return st;
   const unsigned grid = (unsigned)((h->E + NT_NE - 1) / NT_NE);
   nt_fused_kernel<T, D><<<grid, NT_NE * NT_WARPS, sm, s>>>(h->E, h->Es, h->P, h->Q, h->d_rmap, x, tab, qd, Ye, masked);
   CEED_CUDA_CHECK(cudaGetLastError());

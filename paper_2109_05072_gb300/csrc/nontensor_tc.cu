@@ -704,16 +704,9 @@ static int launch_tc(ceed_nt_t h, const float *tabs, const float *qd, const doub
   using L = TcLayout<D, KP, NP, TBUF, QPRE>;
   // one block per SM: the block holds 512 TMEM columns (S and Y double-buffered)
   constexpr size_t SMEM = L::BYTES > 116 * 1024 ? L::BYTES : 116 * 1024;
-  static uint64_t attr_set = 0;
-  const uint64_t bit = 1ull << (h->device & 63);
-  if (!(attr_set & bit)) {
-    CEED_CUDA_CHECK(cudaFuncSetAttribute(nt_tc_kernel<D, KP, NP, TBUF, QPRE>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM));
-    attr_set |= bit;
-  }
-  static int nsm[64] = {0};
-  int &sms = nsm[h->device & 63];
-  if (sms == 0) CEED_CUDA_CHECK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device));
+  if (int st = ensure_dynamic_smem((const void *)nt_tc_kernel<D, KP, NP, TBUF, QPRE>, SMEM)) return st;
+  int sms = 0;
+  CEED_CUDA_CHECK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device));
   const int64_t ntiles = (h->E + TC_M - 1) / TC_M;
   const unsigned grid = (unsigned)std::min<int64_t>(ntiles, (int64_t)sms);
   nt_tc_kernel<D, KP, NP, TBUF, QPRE><<<grid, TC_BLOCK, SMEM, s>>>(h->E, h->Es, h->P, h->Q, h->tc_nchunk,

@@ -302,11 +302,7 @@ static int run_elemvec(ceed_mesh_t m, ElemVecArgs a, cudaStream_t s) {
   a.coords = iso ? m->d_coords : nullptr;
   if (iso) a.iso = make_iso_tab(m);
   const size_t shm = ((size_t)nq_of(m) + MAX_Q * MAX_P + (iso ? iso_smem_doubles(m->P, m->Q) : 0)) * sizeof(double);
-  static size_t configured = 48 * 1024;
-  if (shm > configured) {
-    CEED_CUDA_CHECK(cudaFuncSetAttribute(elemvec_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
-    configured = shm;
-  }
+  if (int st = ensure_dynamic_smem((const void *)elemvec_kernel, shm)) return st;
   const int threads = iso ? ISO_THREADS : 128;
   for (int c = 0; c < m->n_colors; ++c) {
     a.e_begin = m->color_start[c];
