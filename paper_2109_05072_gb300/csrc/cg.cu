@@ -325,7 +325,8 @@ static int pcg_iteration(ceed_mesh_t m, const ApplyReq &op, double *y, const Wor
   const int nb = red_blocks(n);
   // q = A p.  FP64 operator: p . q is summed by the apply itself (each node's last writer adds
   // p_i q_i), saving two vector passes at no cost to the FP64-pipe-bound kernel.  FP32 operators
-  // keep the separate reduction (FP64 products inside them would cost more than the passes).
+  // keep the separate reduction: with the fused sum (FP64 products and a block reduction inside
+  // the FP32 kernel) the mixed CG at 64^3, p = 7 measured 3-9% slower than with the two passes.
   ApplyReq a = op;
   a.x = w.p;
   a.y = w.q;
