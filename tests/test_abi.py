@@ -43,3 +43,42 @@ def test_last_error_without_gpu():
     assert ceed._lib.ceed_setup_mesh(None, None, None) == ceed.CEED_ERR_INVALID
     assert "null" in ceed.ceed_last_error()
     assert ceed.ceed_dot_noalloc_max_n() == 32768 * 8192
+
+
+def test_binding_covers_the_header_exactly():
+    # the binding declares a ctypes signature for every C entry point and for nothing else
+    import paper_2109_05072_gb300 as ceed
+    assert set(ceed._SIGNATURES) == set(_declared())
+
+
+def test_binding_refuses_host_tensors():
+    # device arguments must be CUDA tensors: there is no CPU path to fall back to
+    torch = __import__("pytest").importorskip("torch")
+    import pytest
+    import paper_2109_05072_gb300 as ceed
+    with pytest.raises(ValueError):
+        ceed._ptr(torch.zeros(4, dtype=torch.float64))
+    with pytest.raises(ValueError):          # host buffers of ceed_apply_host must be FP64
+        ceed._host_ptr(torch.zeros(4, dtype=torch.float32))
+    assert ceed._host_ptr(torch.zeros(4, dtype=torch.float64)).value != 0
+
+
+def test_import_fails_loudly_without_the_library():
+    import subprocess
+    import sys
+    # the build module is loaded on its own and registered first, so that the package's
+    # `from .build import LIB` sees the missing path
+    code = ("import importlib.util, os, sys; sys.path.insert(0, %r)\n"
+            "spec = importlib.util.spec_from_file_location('paper_2109_05072_gb300.build',\n"
+            "    os.path.join(sys.path[0], 'paper_2109_05072_gb300', 'build.py'))\n"
+            "b = importlib.util.module_from_spec(spec); spec.loader.exec_module(b)\n"
+            "b.LIB = '/nonexistent/libceedgb.so'\n"
+            "sys.modules['paper_2109_05072_gb300.build'] = b\n"
+            "try:\n"
+            "    import paper_2109_05072_gb300\n"
+            "except ImportError as e:\n"
+            "    print('refused:', e)\n"
+            "else:\n"
+            "    print('imported')\n") % ROOT
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, timeout=300)
+    assert "refused:" in r.stdout and "not built" in r.stdout, r.stdout + r.stderr
