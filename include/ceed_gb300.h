@@ -133,7 +133,8 @@ int ceed_apply_mass(ceed_mesh_t mesh, const void *qdata, int prec, const double 
 int ceed_apply_diffusion(ceed_mesh_t mesh, const void *qdata, int prec, const double *x, double *y,
                          int nrhs, unsigned flags, void *stream);
 
-/* Host-buffer form of the two actions, for callers whose vectors live in host memory: copies
+/* Host-buffer form of the two actions (Section 2's A_L u_L, as ceed_apply_mass / ceed_apply_diffusion),
+ * for callers whose vectors live in host memory: copies
  * x_host into the caller's device buffer x_dev, applies the operator `op` (CEED_OP_MASS or
  * CEED_OP_DIFFUSION; qdata, prec, nrhs, flags as for ceed_apply_mass / ceed_apply_diffusion) into
  * y_dev, and copies y_dev into y_host, all on `stream`, and returns once y_host holds the result
