@@ -82,3 +82,38 @@ def test_import_fails_loudly_without_the_library():
             "    print('imported')\n") % ROOT
     r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, timeout=300)
     assert "refused:" in r.stdout and "not built" in r.stdout, r.stdout + r.stderr
+
+
+def test_struct_layouts_match_header(tmp_path):
+    # every ctypes mirror of a header struct has the C layout: gcc compiles a probe against the
+    # header that prints sizeof and each field's offset, compared with ctypes' own
+    import ctypes
+    import shutil
+    import subprocess
+    import pytest
+    if shutil.which("gcc") is None:
+        pytest.skip("gcc not available")
+    import paper_2109_05072_gb300 as ceed
+    mirrors = {"ceed_mesh_desc": ceed._MeshDesc, "ceed_cg_opts": ceed._CgOpts, "ceed_cg_report": ceed._CgReport,
+               "ceed_pmg_opts": ceed._PmgOpts, "ceed_nt_desc": ceed._NtDesc, "ceed_hp_desc": ceed._HpDesc}
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "ceed_gb300.h"', "int main(void) {"]
+    for cname, cls in mirrors.items():
+        lines.append('  printf("%s size %%zu\\n", sizeof(%s));' % (cname, cname))
+        for fname, _ in cls._fields_:
+            lines.append('  printf("%s %s %%zu\\n", offsetof(%s, %s));' % (cname, fname, cname, fname))
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-std=c11", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True,
+                   capture_output=True, timeout=120)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True, timeout=60).stdout.split("\n")
+    got = {}
+    for line in out:
+        if line.strip():
+            cname, field, value = line.split()
+            got[(cname, field)] = int(value)
+    for cname, cls in mirrors.items():
+        assert got[(cname, "size")] == ctypes.sizeof(cls), cname
+        for fname, _ in cls._fields_:
+            assert got[(cname, fname)] == getattr(cls, fname).offset, (cname, fname)
