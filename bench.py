@@ -86,16 +86,23 @@ class ClockSampler:
          "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
          "clocks_event_reasons.sw_power_cap")
 
-    def __init__(self, index=0):
+    def __init__(self, index=0, period_ms=100, first_sample_s=5.0):
         self.index, self.samples, self.proc = index, [], None
+        self.period_ms, self.first_sample_s = period_ms, first_sample_s
 
     def __enter__(self):
         try:
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", str(self.period_ms)],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.thread = threading.Thread(target=self._read, daemon=True)
             self.thread.start()
+            # nvidia-smi takes a while to start: wait for its first line, so that the region that
+            # follows (warm-up and timed steps, all under load) is sampled from its start
+            t0 = time.perf_counter()
+            while not self.samples and self.proc.poll() is None and time.perf_counter() - t0 < self.first_sample_s:
+                time.sleep(0.01)
+            self.samples.clear()
         except Exception:
             self.proc = None
         return self
