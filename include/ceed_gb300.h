@@ -206,14 +206,14 @@ typedef struct ceed_pmg_s *ceed_pmg_t;
 typedef struct {
   int32_t mode;           /* ceed_cg_mode */
   int32_t max_iter;       /* cap on (inner) iterations in total; 0 -> 10000 */
-  int32_t max_outer;      /* MIXED: cap on refinement steps; 0 -> 50 */
-  int32_t check_every;    /* host convergence check period in iterations; 0 -> 25 */
+  int32_t max_outer;      /* MIXED: cap on refinement steps; 0 -> 50 (MIXED_RELIABLE: unused) */
+  int32_t check_every;    /* host convergence check period in iterations; 0 -> 10 */
   int32_t fixed_iters;    /* > 0: run exactly this many FP64 iterations (no tolerance stop) */
   int32_t op;             /* ceed_op of the operator (DIFFUSION for the bake-off CG) */
   double tol;             /* stop when ||b - A x||_2 <= tol ||b||_2; 0 -> 1e-10 */
   double inner_tol;       /* MIXED: inner relative reduction; 0 -> 1e-4 */
-  const void *qdata_lo;   /* MIXED: quadrature data for the inner operator */
-  int32_t prec_lo;        /* MIXED: its precision (F32, BF16, F16 or F32_GEO) */
+  const void *qdata_lo;   /* MIXED, MIXED_RELIABLE: quadrature data for the low-precision operator */
+  int32_t prec_lo;        /* MIXED, MIXED_RELIABLE: its precision (F32, BF16, F16, F32_GEO or F64_DF) */
   int32_t use_x0;         /* nonzero: x holds the initial guess; else x0 = 0 */
   ceed_pmg_t pmg;         /* FP64 mode: non-NULL -> flexible CG preconditioned by one p-multigrid
                              V-cycle per iteration instead of Jacobi */
