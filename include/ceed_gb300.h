@@ -74,7 +74,7 @@ typedef enum { CEED_COEFF_ONE = 0, CEED_COEFF_CONST = 1, CEED_COEFF_SINE = 2, CE
 
 typedef struct {
   int64_t n_elem;            /* E >= 1 */
-  int64_t n_ldof;            /* nodes in the L-vector, < 2^30 */
+  int64_t n_ldof;            /* nodes in the L-vector, < 2^29 */
   int32_t p;                 /* polynomial order, 1..8 */
   int32_t q_rule;            /* ceed_qrule */
   int32_t n_qpts_1d;         /* Q; 0 selects the default (p+1 for GLL, p+2 for GAUSS); GAUSS needs Q = p+2 */
@@ -279,7 +279,7 @@ int ceed_pmg_vcycle(ceed_pmg_t pmg, const double *r, double *z, void *stream);
 /* Transfers between levels l+1 (coarse) and l (fine): uf = P uc, rc = P^T rf. */
 int ceed_pmg_prolong(ceed_pmg_t pmg, int level, const double *uc, double *uf, void *stream);
 int ceed_pmg_restrict(ceed_pmg_t pmg, int level, const double *rf, double *rc, void *stream);
-/* lambda_max estimate of D^{-1} A used for level l's smoother. */
+/* lambda_max estimate used for level l's smoother: of D^{-1} A (smoother 0) or of M A (smoother 1). */
 int ceed_pmg_info(ceed_pmg_t pmg, int level, double *lambda_max);
 int ceed_pmg_destroy(ceed_pmg_t pmg);
 
