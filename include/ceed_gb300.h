@@ -262,7 +262,7 @@ int ceed_cg_solve(ceed_mesh_t mesh, const void *qdata, int prec, const double *b
  * vectors at creation (several n_ldof-sized FP64 vectors per level).  Synchronizes `stream`. */
 typedef struct {
   int32_t smooth_degree;    /* 0 -> 4 */
-  double smooth_ratio;      /* 0 -> 10 */
+  double smooth_ratio;      /* <= 1 -> 10 */
   int32_t eig_iters;        /* 0 -> 20 */
   double coarse_tol;        /* 0 -> 3e-2 */
   int32_t coarse_max_iter;  /* 0 -> 500 */
