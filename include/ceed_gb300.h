@@ -294,6 +294,11 @@ int ceed_pmg_destroy(ceed_pmg_t pmg);
  * z = sum_e R_e^T W A_e^{-1} W R_e r, W = diag(multiplicity^{-1/2}) (symmetric), FP32 arithmetic.
  * Requires a GLL collocated mesh with one component.  Coefficient ONE, CONST (host value) or SINE. */
 typedef struct ceed_schwarz_s *ceed_schwarz_t;
+/* The smoother's 1D fast-diagonalization basis for order p (1..8), in FP64 (the smoother keeps an
+ * FP32 copy): S [P][P] with S[a * P + i] eigenvector i at GLL node a, lambda [P], such that
+ * A^ S = B^ S diag(lambda) and S^T B^ S = I for the (A^, B^) above; eigenvalues in no particular
+ * order.  Host arrays, no GPU work.  Errors: INVALID. */
+int ceed_schwarz_fdm_1d(int p, double *S, double *lambda);
 int ceed_schwarz_create(ceed_mesh_t mesh, int coeff_kind, const double *coeff, ceed_schwarz_t *out, void *stream);
 /* z = M r (device FP64 [n_ldof], no overlap); CEED_APPLY_DIRICHLET: zero on Dirichlet nodes in r and z.
  * Asynchronous; one kernel launch per colour (colour-ordered, deterministic). */

@@ -92,6 +92,7 @@ def _load():
         "ceed_apply_host": (ctypes.c_int, [vp, ctypes.c_int, vp, ctypes.c_int, vp, vp, vp, vp, ctypes.c_int, u32,
                                            vp]),
         "ceed_jacobi_diagonal": (ctypes.c_int, [vp, ctypes.c_int, vp, ctypes.c_int, vp, u32, vp]),
+        "ceed_schwarz_fdm_1d": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(dbl), ctypes.POINTER(dbl)]),
         "ceed_set_apply_variant": (ctypes.c_int, [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int]),
         "ceed_autotune_apply": (ctypes.c_int, [vp, ctypes.c_int, vp, ctypes.c_int, vp, vp, ctypes.c_int,
                                                ctypes.POINTER(i32), ctypes.POINTER(i32),
@@ -465,6 +466,15 @@ def ceed_simplex_basis(p: int, q: int):
     ptr = lambda a: a.ctypes.data_as(ctypes.c_void_p)
     _check(_lib.ceed_simplex_basis(p, q, ptr(interp), ptr(grad), ptr(qw), ptr(qref)))
     return interp, grad, qw, qref
+
+
+def ceed_schwarz_fdm_1d(p: int):
+    """The Schwarz smoother's 1D fast-diagonalization basis in FP64: (S [P, P], lambda [P])."""
+    import numpy as np
+    S, lam = np.empty((p + 1, p + 1)), np.empty(p + 1)
+    dp = ctypes.POINTER(ctypes.c_double)
+    _check(_lib.ceed_schwarz_fdm_1d(p, S.ctypes.data_as(dp), lam.ctypes.data_as(dp)))
+    return S, lam
 
 
 class NonTensor:

@@ -80,8 +80,9 @@ void jacobi_eig(int n, std::vector<double> C, std::vector<double> &V, std::vecto
   for (int i = 0; i < n; ++i) d[i] = C[i * n + i];
 }
 
-// The 1D fast-diagonalization basis of order p = P - 1 on GLL nodes.
-void fdm_tables(int P, SchwarzTab &tab) {
+// The 1D fast-diagonalization basis of order p = P - 1 on GLL nodes, in FP64: S[a * P + i] is
+// eigenvector i at node a, lam[i] its eigenvalue.
+void fdm_1d(int P, double *S_out, double *lam_out) {
   double x[MAX_P], w[MAX_P];
   gll_rule(P, x, w);
   // differentiation matrix D[q][j] = l_j'(x_q) of the Lagrange basis on the GLL nodes
@@ -123,7 +124,15 @@ void fdm_tables(int P, SchwarzTab &tab) {
     for (int j = 0; j < P; ++j) C[i * P + j] = A[i * P + j] / std::sqrt(B[i] * B[j]);
   jacobi_eig(P, C, V, lam);
   for (int a = 0; a < P; ++a)
-    for (int i = 0; i < P; ++i) tab.S[a * P + i] = (float)(V[a * P + i] / std::sqrt(B[a]));
+    for (int i = 0; i < P; ++i) S_out[a * P + i] = V[a * P + i] / std::sqrt(B[a]);
+  for (int i = 0; i < P; ++i) lam_out[i] = lam[i];
+}
+
+// The kernel's FP32 copy of the tables.
+void fdm_tables(int P, SchwarzTab &tab) {
+  double S[MAX_P * MAX_P], lam[MAX_P];
+  fdm_1d(P, S, lam);
+  for (int k = 0; k < P * P; ++k) tab.S[k] = (float)S[k];
   for (int i = 0; i < P; ++i) tab.lam[i] = (float)lam[i];
 }
 
@@ -289,6 +298,13 @@ int launch_schwarz(ceed_schwarz_t sw, const double *r, double *z, int masked, cu
 }  // namespace ceedgb
 
 using namespace ceedgb;
+
+extern "C" int ceed_schwarz_fdm_1d(int p, double *S, double *lambda) {
+  if (p < 1 || p + 1 > MAX_P) return fail(CEED_ERR_INVALID, "p outside 1..8");
+  if (!S || !lambda) return fail(CEED_ERR_INVALID, "null output array");
+  fdm_1d(p + 1, S, lambda);
+  return CEED_OK;
+}
 
 extern "C" int ceed_schwarz_create(ceed_mesh_t mesh, int coeff_kind, const double *coeff, ceed_schwarz_t *out,
                                    void *stream) {
