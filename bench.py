@@ -9,8 +9,11 @@ quadrature operator, transposed contractions, atomic-free scatter); inputs are r
 far larger than L2 (x 0.72 GB, quadrature data 6.4 GB), so no L2 flush is needed.
 
 Beside the headline it measures the FP32-arithmetic operator (FP32 and BF16 quadrature data), the
-end-to-end call with host buffers, 100 Jacobi-PCG iterations, CG time to a relative residual of
-1e-10 in FP64 and with mixed-precision refinement, and the CPU oracle on a bounded sample.
+double-float FP64-accurate operator, the end-to-end host-buffer call (ceed_apply_host), 100
+Jacobi-PCG iterations, CG time to a relative residual of 1e-10 in FP64, with mixed-precision
+refinement and with reliable updates, p-multigrid CG, the batched mixed-order apply, the adjoint,
+the tetrahedral and hp operators, and the CPU oracle on a bounded sample; --cg-c4 1 adds CG on
+80^3 elements (176.6M DOFs).
 
 --impl reference times the CPU oracle (dense per-element quadrature, no sum factorization) on the
 host cores, on a bounded sample of the same workload per step.
