@@ -429,6 +429,14 @@ typedef struct {
   int32_t q_rule;              /* GLL (Q = p+1) or GAUSS (Q = p+2), every element */
   int32_t dirichlet;           /* nonzero: the true dofs on the lattice boundary are Dirichlet dofs */
 } ceed_hp_desc;
+/* The space alone, on the host (no GPU work): for the lattice and orders (host [nx ny nz], 1..8)
+ * of an hp description, the true-dof count, the element-node row count and the nonzeros of P; when
+ * row_ptr, col, val and dirichlet are all given (else all NULL), also the CSR of P (row_ptr
+ * [n_rows + 1], col [nnz], val [nnz]; rows as for ceed_hp_prolong) and dirichlet [n_true] (1 on the
+ * lattice boundary).  The same construction ceed_hp_setup uploads.  Errors: INVALID, OOM. */
+int ceed_hp_prolongation(int32_t nx, int32_t ny, int32_t nz, const int32_t *orders, int64_t *n_true,
+                         int64_t *n_rows, int64_t *nnz, int64_t *row_ptr, int64_t *col, double *val,
+                         uint8_t *dirichlet);
 /* Build the space (host) and the per-order meshes.  Synchronizes `stream`.  Errors: INVALID, OOM, CUDA. */
 int ceed_hp_setup(const ceed_hp_desc *desc, ceed_hp_t *out, void *stream);
 int ceed_hp_destroy(ceed_hp_t h);

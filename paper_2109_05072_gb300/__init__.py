@@ -93,6 +93,8 @@ def _load():
                                            vp]),
         "ceed_jacobi_diagonal": (ctypes.c_int, [vp, ctypes.c_int, vp, ctypes.c_int, vp, u32, vp]),
         "ceed_schwarz_fdm_1d": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(dbl), ctypes.POINTER(dbl)]),
+        "ceed_hp_prolongation": (ctypes.c_int, [i32, i32, i32, vp, ctypes.POINTER(i64), ctypes.POINTER(i64),
+                                                ctypes.POINTER(i64), vp, vp, vp, vp]),
         "ceed_set_apply_variant": (ctypes.c_int, [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int]),
         "ceed_autotune_apply": (ctypes.c_int, [vp, ctypes.c_int, vp, ctypes.c_int, vp, vp, ctypes.c_int,
                                                ctypes.POINTER(i32), ctypes.POINTER(i32),
@@ -466,6 +468,24 @@ def ceed_simplex_basis(p: int, q: int):
     ptr = lambda a: a.ctypes.data_as(ctypes.c_void_p)
     _check(_lib.ceed_simplex_basis(p, q, ptr(interp), ptr(grad), ptr(qw), ptr(qref)))
     return interp, grad, qw, qref
+
+
+def ceed_hp_prolongation(nx: int, ny: int, nz: int, orders):
+    """The conforming prolongation of an hp lattice, built on the host: (n_true, row_ptr, col, val, dirichlet)."""
+    import numpy as np
+    o = np.ascontiguousarray(np.asarray(orders, dtype=np.int32).reshape(-1))
+    if o.size != nx * ny * nz:
+        raise ValueError("one order per element")
+    nt, nr, nnz = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+    optr = o.ctypes.data_as(ctypes.c_void_p)
+    _check(_lib.ceed_hp_prolongation(nx, ny, nz, optr, ctypes.byref(nt), ctypes.byref(nr), ctypes.byref(nnz),
+                                     None, None, None, None))
+    rp, col = np.empty(nr.value + 1, dtype=np.int64), np.empty(nnz.value, dtype=np.int64)
+    val, d = np.empty(nnz.value), np.empty(nt.value, dtype=np.uint8)
+    ptr = lambda a: a.ctypes.data_as(ctypes.c_void_p)
+    _check(_lib.ceed_hp_prolongation(nx, ny, nz, optr, ctypes.byref(nt), ctypes.byref(nr), ctypes.byref(nnz),
+                                     ptr(rp), ptr(col), ptr(val), ptr(d)))
+    return nt.value, rp, col, val, d
 
 
 def ceed_schwarz_fdm_1d(p: int):

@@ -349,23 +349,109 @@ int upload(T **dst, const std::vector<T> &src, cudaStream_t s) {
   return CEED_OK;
 }
 
+// The host part of the space: true-dof count, order groups (ascending order, element lists) and
+// the CSR of P with rows in group order, plus the Dirichlet flag of every true dof.
+struct HostP {
+  int64_t n_true = 0, rows = 0;
+  std::vector<int> porders;
+  std::vector<std::vector<int64_t>> members;
+  std::vector<int64_t> prow, pcol;
+  std::vector<double> pval;
+  std::vector<uint8_t> dir;
+};
+
+int build_host_p(int nx, int ny, int nz, const std::vector<int> &ord, HostP &H) {
+  const int64_t E = (int64_t)nx * ny * nz;
+  try {
+    Builder B(nx, ny, nz, ord);
+    B.orders_and_numbering();
+    H.n_true = B.nT;
+    if (B.nT >= ((int64_t)1 << 40)) return fail(CEED_ERR_INVALID, "mesh too large");
+    H.porders.assign(ord.begin(), ord.end());
+    std::sort(H.porders.begin(), H.porders.end());
+    H.porders.erase(std::unique(H.porders.begin(), H.porders.end()), H.porders.end());
+    H.members.assign(H.porders.size(), {});
+    for (int64_t e = 0; e < E; ++e)
+      H.members[std::lower_bound(H.porders.begin(), H.porders.end(), ord[e]) - H.porders.begin()].push_back(e);
+    H.rows = 0;
+    for (size_t g = 0; g < H.porders.size(); ++g)
+      H.rows += (int64_t)H.members[g].size() * (H.porders[g] + 1) * (H.porders[g] + 1) * (H.porders[g] + 1);
+    H.prow.assign(H.rows + 1, 0);
+    H.pcol.clear();
+    H.pval.clear();
+    H.pcol.reserve(H.rows + H.rows / 2);
+    H.pval.reserve(H.rows + H.rows / 2);
+    Row r;
+    int64_t ri = 0;
+    for (size_t g = 0; g < H.porders.size(); ++g) {
+      const int P = H.porders[g] + 1;
+      for (int64_t e : H.members[g])
+        for (int c = 0; c < P; ++c)
+          for (int b = 0; b < P; ++b)
+            for (int a = 0; a < P; ++a) {
+              r.t.clear();
+              B.node_row(e, a, b, c, r);
+              for (auto &kv : r.t) {
+                H.pcol.push_back(kv.first);
+                H.pval.push_back(kv.second);
+              }
+              H.prow[++ri] = (int64_t)H.pcol.size();
+            }
+    }
+    B.boundary(H.dir);
+  } catch (...) {
+    return fail(CEED_ERR_OOM, "host allocation while building the conforming prolongation");
+  }
+  return CEED_OK;
+}
+
+int check_orders(int nx, int ny, int nz, const int32_t *orders, std::vector<int> &ord) {
+  if (nx < 1 || ny < 1 || nz < 1) return fail(CEED_ERR_INVALID, "nx, ny, nz must be >= 1");
+  if (!orders) return fail(CEED_ERR_INVALID, "orders (host) are required");
+  const int64_t E = (int64_t)nx * ny * nz;
+  ord.resize(E);
+  for (int64_t e = 0; e < E; ++e) {
+    ord[e] = orders[e];
+    if (ord[e] < 1 || ord[e] > 8) return fail(CEED_ERR_INVALID, "orders must be in 1..8");
+  }
+  return CEED_OK;
+}
+
 }  // namespace
 }  // namespace ceedgb
 
 using namespace ceedgb;
 
+extern "C" int ceed_hp_prolongation(int32_t nx, int32_t ny, int32_t nz, const int32_t *orders, int64_t *n_true,
+                                    int64_t *n_rows, int64_t *nnz, int64_t *row_ptr, int64_t *col, double *val,
+                                    uint8_t *dirichlet) {
+  if (!n_true || !n_rows || !nnz) return fail(CEED_ERR_INVALID, "null size output");
+  const bool fill = row_ptr || col || val || dirichlet;
+  if (fill && !(row_ptr && col && val && dirichlet)) return fail(CEED_ERR_INVALID, "give all four arrays or none");
+  std::vector<int> ord;
+  if (int st = check_orders(nx, ny, nz, orders, ord)) return st;
+  HostP H;
+  if (int st = build_host_p(nx, ny, nz, ord, H)) return st;
+  *n_true = H.n_true;
+  *n_rows = H.rows;
+  *nnz = (int64_t)H.pcol.size();
+  if (fill) {
+    std::memcpy(row_ptr, H.prow.data(), H.prow.size() * sizeof(int64_t));
+    std::memcpy(col, H.pcol.data(), H.pcol.size() * sizeof(int64_t));
+    std::memcpy(val, H.pval.data(), H.pval.size() * sizeof(double));
+    std::memcpy(dirichlet, H.dir.data(), H.dir.size() * sizeof(uint8_t));
+  }
+  return CEED_OK;
+}
+
 extern "C" int ceed_hp_setup(const ceed_hp_desc *desc, ceed_hp_t *out, void *stream) {
   if (!desc || !out) return fail(CEED_ERR_INVALID, "null descriptor or output");
   *out = nullptr;
-  if (desc->nx < 1 || desc->ny < 1 || desc->nz < 1) return fail(CEED_ERR_INVALID, "nx, ny, nz must be >= 1");
-  if (!desc->orders || !desc->vertices) return fail(CEED_ERR_INVALID, "orders (host) and vertices (device) are required");
+  if (!desc->vertices) return fail(CEED_ERR_INVALID, "vertices (device) are required");
   if (desc->q_rule != CEED_QRULE_GLL && desc->q_rule != CEED_QRULE_GAUSS) return fail(CEED_ERR_INVALID, "unknown rule");
+  std::vector<int> ord;
+  if (int st = check_orders(desc->nx, desc->ny, desc->nz, desc->orders, ord)) return st;
   const int64_t E = (int64_t)desc->nx * desc->ny * desc->nz;
-  std::vector<int> ord(E);
-  for (int64_t e = 0; e < E; ++e) {
-    ord[e] = desc->orders[e];
-    if (ord[e] < 1 || ord[e] > 8) return fail(CEED_ERR_INVALID, "orders must be in 1..8");
-  }
   cudaStream_t s = (cudaStream_t)stream;
   std::unique_ptr<ceed_hp_s, HpFree> h(new (std::nothrow) ceed_hp_s());
   if (!h) return fail(CEED_ERR_OOM, "host allocation");
@@ -377,61 +463,30 @@ extern "C" int ceed_hp_setup(const ceed_hp_desc *desc, ceed_hp_t *out, void *str
   h->q_rule = desc->q_rule;
   h->dirichlet = desc->dirichlet != 0;
 
-  Builder B(desc->nx, desc->ny, desc->nz, ord);
-  B.orders_and_numbering();
-  h->n_true = B.nT;
-  if (B.nT >= ((int64_t)1 << 40)) return fail(CEED_ERR_INVALID, "mesh too large");
-
-  // order groups (ascending order), element lists, E-vector row offsets
-  std::vector<int> porders(ord.begin(), ord.end());
-  std::sort(porders.begin(), porders.end());
-  porders.erase(std::unique(porders.begin(), porders.end()), porders.end());
-  std::vector<std::vector<int64_t>> members(porders.size());
-  for (int64_t e = 0; e < E; ++e)
-    members[std::lower_bound(porders.begin(), porders.end(), ord[e]) - porders.begin()].push_back(e);
+  // P (CSR, rows in group order), the order groups and the Dirichlet flags, built on the host
+  HostP H;
+  if (int st = build_host_p(desc->nx, desc->ny, desc->nz, ord, H)) return st;
+  h->n_true = H.n_true;
   int64_t rows = 0;
-  for (size_t g = 0; g < porders.size(); ++g) {
+  for (size_t g = 0; g < H.porders.size(); ++g) {
     ceed_hp_s::Group G;
-    G.p = porders[g];
-    G.n_elem = (int64_t)members[g].size();
+    G.p = H.porders[g];
+    G.n_elem = (int64_t)H.members[g].size();
     G.row0 = rows;
     rows += G.n_elem * (G.p + 1) * (G.p + 1) * (G.p + 1);
     h->groups.push_back(G);
   }
   h->n_rows = rows;
-
-  // P (CSR, rows in group order) and P^T
-  std::vector<int64_t> prow(rows + 1, 0), pcol;
-  std::vector<double> pval;
-  std::vector<uint8_t> dir;
-  try {
-    pcol.reserve(rows + rows / 2);
-    pval.reserve(rows + rows / 2);
-    Row r;
-    int64_t ri = 0;
-    for (size_t g = 0; g < porders.size(); ++g) {
-      const int P = porders[g] + 1;
-      for (int64_t e : members[g])
-        for (int c = 0; c < P; ++c)
-          for (int b = 0; b < P; ++b)
-            for (int a = 0; a < P; ++a) {
-              r.t.clear();
-              B.node_row(e, a, b, c, r);
-              for (auto &kv : r.t) {
-                pcol.push_back(kv.first);
-                pval.push_back(kv.second);
-              }
-              prow[++ri] = (int64_t)pcol.size();
-            }
-    }
-    B.boundary(dir);
-  } catch (...) {
-    return fail(CEED_ERR_OOM, "host allocation while building the conforming prolongation");
-  }
-  std::vector<int64_t> trow(B.nT + 1, 0), tcol(pcol.size());
+  const std::vector<int> &porders = H.porders;
+  const std::vector<std::vector<int64_t>> &members = H.members;
+  const std::vector<int64_t> &prow = H.prow, &pcol = H.pcol;
+  const std::vector<double> &pval = H.pval;
+  const std::vector<uint8_t> &dir = H.dir;
+  // P^T (CSR), each true dof's entries in ascending row order
+  std::vector<int64_t> trow(H.n_true + 1, 0), tcol(pcol.size());
   std::vector<double> tval(pcol.size());
   for (int64_t c : pcol) trow[c + 1]++;
-  for (int64_t i = 0; i < B.nT; ++i) trow[i + 1] += trow[i];
+  for (int64_t i = 0; i < H.n_true; ++i) trow[i + 1] += trow[i];
   {
     std::vector<int64_t> fill(trow.begin(), trow.end() - 1);
     for (int64_t r = 0; r < rows; ++r)
