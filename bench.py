@@ -36,7 +36,7 @@ import numpy as np  # noqa: E402
 import synthetic  # noqa: E402
 
 METRIC = "diffusion apply GDOF/s at p=7 (FP64 vs mixed), % HBM roofline, CG time-to-1e-10"
-FP64_NOMINAL_TFLOPS = 1.25      # GB300 dense FP64 (profiling recipe's nominal table)
+FP64_NOMINAL_TFLOPS = 1.25      # GB300 dense FP64 (nominal table), reported beside the measured peak
 # DRAM bytes (read + write) per launch of the FP64 apply kernel variant, from one ncu capture of the
 # current kernel on the 48^3 mesh (13,824 elements per colour launch), scaled by elements to a 64^3
 # colour launch (32,768 elements); keyed by variant, empty until a capture of the current kernel.
@@ -249,7 +249,14 @@ def _time_cuda(fn, steps, warmup):
     return e0.elapsed_time(e1) / steps
 
 
-def run_batched(ceed, dev, args):
+def batched_model_flops(p, N):
+    """Section 2 cost model for one column of an N^3 mesh of order p with q = p + 2 Gauss points: the
+    contraction term doubled for the interpolation passes (2 x 12 P^4) plus 15 Q^3 pointwise flops."""
+    P, Q = p + 1, p + 3
+    return N ** 3 * (24 * P ** 4 + 15 * Q ** 3)
+
+
+def run_batched(ceed, dev, args, peaks=None):
     """Three independent meshes of order 3, 5, 7 (Gauss q = p+2: 5, 7, 9 points) on 48^3, 40^3, 32^3
     elements, 3-component diffusion, FP64, applied by one persistent launch replayed from a CUDA graph."""
     import torch
@@ -265,8 +272,10 @@ def run_batched(ceed, dev, args):
         qds.append(qd)
         nodes.append(m.n_ldof)
     out = {"meshes": [f"p={p}, {N}^3, Gauss q={p + 2}, n_ldof={n}" for (p, N), n in zip(specs, nodes)],
-           "ncomp": 3, "dtype": "f64", "runs": []}
-    for nrhs in (1, 4, 16):
+           "ncomp": 3, "dtype": "f64", "runs": [],
+           "model": "per element and column 24 P^4 + 15 Q^3 flops (Section 2 model, contraction term doubled "
+                    "for q = p + 2); fp64_frac against the measured FP64 FMA rate"}
+    for nrhs in (1, 4, 8, 16):
         xs = [torch.from_numpy(synthetic.uniform(n * 3 * nrhs, seed=7 + k)).to(dev) for k, n in enumerate(nodes)]
         ys = [torch.empty_like(x) for x in xs]
         batch = ceed.ceed_batch_create(meshes, qds, ceed.CEED_F64, ceed.CEED_OP_DIFFUSION, xs, ys, nrhs=nrhs)
@@ -275,8 +284,12 @@ def run_batched(ceed, dev, args):
         ms = _time_cuda(lambda: ceed.ceed_batch_apply(batch), 5, 3)
         ceed.ceed_batch_status(batch)
         dofs = sum(nodes) * 3 * nrhs
-        out["runs"].append({"nrhs": nrhs, "ms_per_apply": ms, "gdofs": dofs / ms / 1e6, "threads": threads,
-                            "tma_staging": stage, "grid": grid, "launches_per_apply": 1})
+        flops = sum(batched_model_flops(p, N) for p, N in specs) * 3 * nrhs
+        row = {"nrhs": nrhs, "ms_per_apply": ms, "gdofs": dofs / ms / 1e6, "threads": threads,
+               "tma_staging": stage, "grid": grid, "launches_per_apply": 1, "model_tflops": flops / ms / 1e9}
+        if peaks and peaks.get("f64"):
+            row["fp64_frac"] = row["model_tflops"] / peaks["f64"]["tflops"]
+        out["runs"].append(row)
         batch.close()
         del xs, ys
         torch.cuda.empty_cache()
@@ -453,6 +466,41 @@ def run_hp(ceed, dev, args):
     return out
 
 
+def compact_summary(line):
+    """The headline numbers of every leg in a few hundred bytes (GDOF/s, fractions, CG seconds)."""
+    r = lambda v, d=3: None if v is None else round(v, d)
+    out = {"fp64_gdofs": r(line["value"]), "fp64_frac_of_measured_fp64": r(line["roofline"]["frac"]),
+           "fp64_hbm_frac": r(line["roofline"]["hbm_frac"])}
+    df = line.get("fp64_accurate_fp32_pipe")
+    if df:
+        out["df_gdofs"] = r(df["gdofs"])
+        out["df_hbm_frac"] = r(df["roofline"]["frac"])
+        out["df_rel_l2_vs_fp64"] = df["rel_l2_vs_fp64"]
+    for k, v in (line.get("mixed_apply") or {}).items():
+        out[f"{k}_gdofs"] = r(v["gdofs"])
+        out[f"{k}_hbm_frac"] = r(v["hbm_frac"])
+    cg = line.get("cg") or {}
+    if cg:
+        f = cg.get("fp64_to_1e-10", {})
+        out["cg_fp64_s"] = r(f.get("seconds"))
+        out["cg_fp64_iters"] = f.get("iterations")
+        for key in ("mixed_f32", "mixed_f32_reliable", "mixed_f64df_reliable", "pmg_fp32_smoothers"):
+            d = cg.get(f"{key}_to_1e-10")
+            if d:
+                out[f"cg_{key}_s"] = r(d.get("seconds"))
+                out[f"cg_{key}_iters"] = d.get("iterations")
+                out[f"cg_{key}_rel_res"] = d.get("rel_residual")
+                sp = cg.get(f"{key}_speedup") or cg.get(f"{key}_speedup_vs_fp64_jacobi")
+                out[f"cg_{key}_speedup"] = r(sp)
+    b = line.get("batched")
+    if b:
+        out["batched_gdofs_by_nrhs"] = {str(x["nrhs"]): r(x["gdofs"]) for x in b["runs"]}
+        out["batched_fp64_frac_by_nrhs"] = {str(x["nrhs"]): r(x.get("fp64_frac")) for x in b["runs"]}
+    pk = line.get("peaks_measured") or {}
+    out["peak_tflops"] = {k: r(v["tflops"]) for k, v in pk.items()}
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -530,6 +578,13 @@ def main():
         ms = max_over_ranks(e0.elapsed_time(e1), ws, dev)
         return ms / steps
 
+    # ---------------- arithmetic peaks of this GPU, measured now (the roofline denominators of the
+    # FP64 operator and of the FP32-pipe operators): independent FMA chains on every SM
+    peaks = {}
+    for name, kind in (("f64", 0), ("f32", 1), ("f32x2", 2)):
+        tf, per_clk, mhz = ceed.ceed_fma_throughput(kind)
+        peaks[name] = {"tflops": tf, "fma_per_clk_per_sm": per_clk, "sm_mhz": mhz}
+
     # ---------------- headline: FP64 apply (variant chosen by the library's autotuner first)
     variants = {}
     if args.autotune:
@@ -565,12 +620,19 @@ def main():
         torch.cuda.synchronize()
         rel = float(torch.linalg.vector_norm(ydf - y) / torch.linalg.vector_norm(y))
         relmax = float((ydf - y).abs().max() / y.abs().max())
+        vdf = variants.get("f64_df", {"elems_per_block": 0, "tma_staging": 1})
+        kid_df = (f"apply_kernel<8,8,DIFFUSION,DF,DF,stage={vdf['tma_staging']}>[ne={vdf['elems_per_block']}]")
         f64df = {"gdofs": whole_job_rate(n_apply, ws, ms_df), "ms": ms_df, "dtype": "f32x2 (double-float, compensated dot)",
                  "rel_l2_vs_fp64": rel, "rel_max_vs_fp64": relmax,
                  "flops_tflops_paper_model": flops_el * m.n_elem / (ms_df * 1e-3) / 1e12,
-                 "hbm_gbs": algorithmic_bytes(m, 8) / (ms_df * 1e-3) / 1e9,
-                 "hbm_frac": algorithmic_bytes(m, 8) / (ms_df * 1e-3) / 1e9 / hbm_peak,
-                 "speedup_vs_native_fp64": ms64 / ms_df}
+                 "speedup_vs_native_fp64": ms64 / ms_df,
+                 "roofline": {"bound": "hbm", "achieved": bytes64 / launches_per_apply / (ms_df / launches_per_apply * 1e-3) / 1e9,
+                              "peak": hbm_peak, "unit": "GB/s",
+                              "frac": bytes64 / (ms_df * 1e-3) / 1e9 / hbm_peak,
+                              "traffic": PROFILED_TRAFFIC_PER_LAUNCH.get(kid_df) if N == 64 else None,
+                              "kernel": kid_df, "alg_bytes_per_launch": bytes64 / launches_per_apply,
+                              "ms_per_launch": ms_df / launches_per_apply, "peak_kind": f"{hbm_kind} copy bandwidth",
+                              "fp32_peak_tflops_measured": peaks["f32"]["tflops"]}}
         del qdf, ydf
         torch.cuda.empty_cache()
 
@@ -679,7 +741,7 @@ def main():
     # ---------------- batched apply: p = 3, 5, 7 meshes (Gauss q = p+2), 3 components, 1..16 RHS, one launch
     batched = None
     if args.batched:
-        batched = run_batched(ceed, dev, args)
+        batched = run_batched(ceed, dev, args, peaks)
 
     # ---------------- adjoint: L = 0.5 ||A(k) x - b||^2, p = 4 and 8 on 32^3, geometry stored vs recomputed
     adjoint = None
@@ -720,12 +782,14 @@ def main():
                        "n_ldof": n_apply,
                        "n_elem": N ** 3, "l2": "inputs larger than L2 (qdata 6.4 GB), no flush",
                        "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU"},
-            "roofline": {"bound": "alu", "achieved": achieved_tf, "peak": FP64_NOMINAL_TFLOPS, "unit": "TFLOP/s",
-                         "frac": achieved_tf / FP64_NOMINAL_TFLOPS,
+            "roofline": {"bound": "alu", "achieved": achieved_tf, "peak": peaks["f64"]["tflops"], "unit": "TFLOP/s",
+                         "frac": achieved_tf / peaks["f64"]["tflops"],
                          "traffic": PROFILED_TRAFFIC_PER_LAUNCH.get(kernel_id) if N == 64 else None,
                          "alg_bytes_per_launch": bytes64 / launches_per_apply,
                          "kernel": kernel_id,
-                         "peak_kind": "nominal FP64 (no FP64 entry in MEASURED_PEAKS.json)",
+                         "peak_kind": "measured in this run: FP64 FMA chains on every SM (ceed_fma_throughput), "
+                                      f"{peaks['f64']['sm_mhz']:.0f} MHz; nominal {FP64_NOMINAL_TFLOPS}",
+                         "peak_nominal": FP64_NOMINAL_TFLOPS,
                          "flops_per_launch": flops_launch, "ms_per_launch": ms_launch,
                          "hbm_gbs": bytes64 / (ms64 * 1e-3) / 1e9, "hbm_peak": hbm_peak, "hbm_peak_kind": hbm_kind,
                          "hbm_frac": bytes64 / (ms64 * 1e-3) / 1e9 / hbm_peak},
@@ -744,7 +808,9 @@ def main():
             "hp": hp,
             "cg_80cube": cg_c4,
             "cpu_baseline": cpu,
+            "peaks_measured": peaks,
         }
+        line["summary"] = compact_summary(line)   # last key: the short record of every leg
         print(json.dumps(line), flush=True)
     if ws > 1:
         import torch.distributed as dist

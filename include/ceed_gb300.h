@@ -477,6 +477,32 @@ int ceed_dot(const double *x, const double *y, int64_t n, double *out, void *wor
 int64_t ceed_dot_noalloc_max_n(void);
 int ceed_dot_noalloc(const double *x, const double *y, int64_t n, double *out, void *stream);
 
+/* ---------------------------------------------------------------- status, limits, measurement */
+
+/* Synchronizes `stream` and reports whether a bounded device wait of an earlier apply on this mesh
+ * gave up (the TMA copy of an element's quadrature data did not land within the wait limit): then
+ * it clears the flag and returns CEED_ERR_TIMEOUT, and the y of those applies is incomplete
+ * (elements whose wait gave up write nothing).  CEED_OK otherwise. */
+int ceed_mesh_status(ceed_mesh_t mesh, void *stream);
+
+/* Iteration limits of the bounded device-side waits (not an operation of the paper; failure
+ * handling): copy_polls bounds each apply kernel's wait for its quadrature-data copy, barrier_polls
+ * the persistent batched launch's grid barrier between colours.  A wait that runs out records
+ * CEED_ERR_TIMEOUT (read by ceed_mesh_status / ceed_batch_status) and the kernel finishes without
+ * hanging.  A negative value restores the default (2^22 and 2^25 polls); 0 makes the wait give up
+ * at once (a test uses this to drive the timeout path); values above the defaults are INVALID.
+ * Process-wide; applies to launches issued afterwards (a batch's CUDA graph keeps the limits it was
+ * captured with: re-create the batch or re-run ceed_batch_autotune to pick up new ones). */
+int ceed_set_wait_limits(int64_t copy_polls, int64_t barrier_polls);
+
+/* Arithmetic-throughput measurement (not an operation of the paper; it gives the operators'
+ * roofline denominators): kind 0 = FP64 FMA, 1 = FP32 FMA, 2 = packed two-lane FP32 FMA
+ * (fma.rn.f32x2).  Runs independent FMA chains on every SM (64 warps per SM, about 50-100 ms per
+ * run, best of three) on `stream` and returns TFLOP/s (2 flops per FMA), FMAs per clock per SM and
+ * the SM clock in MHz seen by one block during the run (either pointer may be NULL).  Synchronizes
+ * `stream`.  Errors: INVALID, CUDA. */
+int ceed_fma_throughput(int kind, double *tflops, double *fma_per_clk_sm, double *sm_mhz, void *stream);
+
 /* Thread-local message for the last failing call on this thread ("" if none). */
 const char *ceed_last_error(void);
 

@@ -120,6 +120,10 @@ def _load():
         "ceed_batch_autotune": (ctypes.c_int, [vp, ctypes.POINTER(ctypes.c_float), vp]),
         "ceed_batch_info": (ctypes.c_int, [vp, ctypes.POINTER(i32), ctypes.POINTER(i32), ctypes.POINTER(ctypes.c_uint32)]),
         "ceed_batch_status": (ctypes.c_int, [vp, vp]),
+        "ceed_mesh_status": (ctypes.c_int, [vp, vp]),
+        "ceed_set_wait_limits": (ctypes.c_int, [i64, i64]),
+        "ceed_fma_throughput": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(dbl), ctypes.POINTER(dbl),
+                                               ctypes.POINTER(dbl), vp]),
         "ceed_batch_destroy": (ctypes.c_int, [vp]),
         "ceed_simplex_sizes": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.POINTER(i32), ctypes.POINTER(i32)]),
         "ceed_simplex_basis": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, vp, vp, vp, vp]),
@@ -382,6 +386,21 @@ def ceed_batch_status(batch: Batch, stream=None):
 
 def ceed_batch_destroy(batch: Batch):
     batch.close()
+
+
+def ceed_mesh_status(mesh: Mesh, stream=None):
+    _check(_lib.ceed_mesh_status(mesh.handle, _stream(stream)))
+
+
+def ceed_set_wait_limits(copy_polls: int = -1, barrier_polls: int = -1):
+    _check(_lib.ceed_set_wait_limits(copy_polls, barrier_polls))
+
+
+def ceed_fma_throughput(kind: int, stream=None):
+    """(TFLOP/s, FMAs per clock per SM, SM MHz) of kind 0 = FP64, 1 = FP32, 2 = FP32x2 FMA chains."""
+    tf, per_clk, mhz = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+    _check(_lib.ceed_fma_throughput(kind, ctypes.byref(tf), ctypes.byref(per_clk), ctypes.byref(mhz), _stream(stream)))
+    return tf.value, per_clk.value, mhz.value
 
 
 class Pmg:

@@ -81,10 +81,10 @@ __device__ __forceinline__ void tma_bulk_load(void *dst, const void *src, uint32
                : "memory");
 }
 
-// Bounded wait on phase `parity`: returns false if the copy did not land within the limit.
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
+// Bounded wait on phase `parity`: returns false if the copy did not land within `limit` polls.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, int limit = WAIT_COPY_DEFAULT) {
   const uint32_t a = smem_u32(bar);
-  for (int it = 0; it < (1 << 22); ++it) {
+  for (int it = 0; it < limit; ++it) {
     uint32_t ok;
     asm volatile(
         "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
@@ -141,8 +141,7 @@ __device__ __forceinline__ T dot3(T g1, T a, T g2, T b, T g3, T c) {
 }
 template <>
 __device__ __forceinline__ DF dot3<DF>(DF g1, DF a, DF g2, DF b, DF g3, DF c) {
-  DFAcc A{0.f, 0.f};
-  acc_mac(A, g1, a);
+  DFAcc A = acc_first(g1, a);
   acc_mac(A, g2, b);
   acc_mac(A, g3, c);
   return acc_get(A);
@@ -154,9 +153,7 @@ __device__ __forceinline__ T qmul(T q, T u) {
 }
 template <>
 __device__ __forceinline__ DF qmul<DF>(DF q, DF u) {
-  DFAcc A{0.f, 0.f};
-  acc_mac(A, q, u);
-  return acc_get(A);
+  return acc_get(acc_first(q, u));
 }
 template <typename T>
 __device__ __forceinline__ T add3(T a, T b, T c) {
@@ -180,10 +177,13 @@ __device__ __forceinline__ void eo_apply(const EOMat<DF> &M, const DF *v, DF *ou
   }
 #pragma unroll
   for (int i = 0; i < HO; ++i) {
-    DFAcc A{0.f, 0.f}, B{0.f, 0.f};
-    if (NI & 1) acc_mac(A, M.cmid[i], v[HI]);
+    // each sum starts from its first exact product (the same terms in the same order as a sum
+    // started from zero, without the TwoSum against zero)
+    DFAcc A = (NI & 1) ? acc_first(M.cmid[i], v[HI]) : acc_first(M.E[i * EO_H], e[0]);
+    DFAcc B = acc_first(M.O[i * EO_H], o[0]);
+    if (NI & 1) acc_mac(A, M.E[i * EO_H], e[0]);
 #pragma unroll
-    for (int j = 0; j < HI; ++j) {
+    for (int j = 1; j < HI; ++j) {
       acc_mac(A, M.E[i * EO_H + j], e[j]);
       acc_mac(B, M.O[i * EO_H + j], o[j]);
     }
@@ -192,10 +192,10 @@ __device__ __forceinline__ void eo_apply(const EOMat<DF> &M, const DF *v, DF *ou
     out[NO - 1 - i] = (S > 0) ? df_sub(a, b) : df_sub(b, a);
   }
   if constexpr (NO & 1) {
-    DFAcc C{0.f, 0.f};
-    if (NI & 1) acc_mac(C, M.cc, v[HI]);
+    DFAcc C = (NI & 1) ? acc_first(M.cc, v[HI]) : acc_first(M.rmid[0], (S > 0) ? e[0] : o[0]);
+    if (NI & 1) acc_mac(C, M.rmid[0], (S > 0) ? e[0] : o[0]);
 #pragma unroll
-    for (int j = 0; j < HI; ++j) acc_mac(C, M.rmid[j], (S > 0) ? e[j] : o[j]);
+    for (int j = 1; j < HI; ++j) acc_mac(C, M.rmid[j], (S > 0) ? e[j] : o[j]);
     out[HO] = acc_get(C);
   }
 }
@@ -247,6 +247,7 @@ struct ApplyArgs {
   int ncol, masked;
   int ne;           // elements per thread block
   int *err;
+  int wait_limit;    // polls of the quadrature-data copy wait before it gives up (CEED_ERR_TIMEOUT)
   double *dot_part;  // optional: partial sums of x_i y_i over the nodes whose final y this block writes
   int64_t dot_base;  // index of this launch's first block in dot_part
 };
@@ -297,6 +298,7 @@ __device__ __forceinline__ void apply_block(const ApplyArgs &a, const OpTab<T> &
     for (int c = 0; c < P; ++c) idx[c] = __ldg(em + c * P * P);
   }
   bool have_q = false;
+  bool q_ok = true;  // false once this thread's copy wait gave up: the element then writes nothing
 
   for (int col = 0; col < a.ncol; ++col) {
     // ---- all global loads of the column up front: x at my nodes, old y where an earlier colour wrote
@@ -355,7 +357,8 @@ __device__ __forceinline__ void apply_block(const ApplyArgs &a, const OpTab<T> &
     // ---- quadrature-point operator
     T w[Q];
     if (STAGE && !have_q) {  // elements past the end issued no copy and do not wait
-      if (active && !mbar_wait(&bar[el], 0)) {
+      if (active && !mbar_wait(&bar[el], 0, a.wait_limit)) {
+        q_ok = false;
         if (ij == 0) *a.err = CEED_ERR_TIMEOUT;
       }
       have_q = true;
@@ -506,7 +509,7 @@ __device__ __forceinline__ void apply_block(const ApplyArgs &a, const OpTab<T> &
 
     // ---- scatter-add (E -> L), atomic-free
     if (!a.dot_part) {
-      if (active && node_thread) {
+      if (active && node_thread && q_ok) {
 #pragma unroll
         for (int c = 0; c < P; ++c) {
           const uint32_t v = idx[c];
@@ -524,7 +527,7 @@ __device__ __forceinline__ void apply_block(const ApplyArgs &a, const OpTab<T> &
       // same scatter, and x . y over the nodes whose final value this thread writes (fused CG dot:
       // the last writer of a node adds x_i y_i; a masked Dirichlet node's first writer adds x_i^2)
       double dot = 0.0;
-      if (active && node_thread) {
+      if (active && node_thread && q_ok) {
 #pragma unroll
         for (int c = 0; c < P; ++c) {
           const uint32_t v = idx[c];
@@ -556,8 +559,9 @@ __device__ __forceinline__ void apply_block(const ApplyArgs &a, const OpTab<T> &
     }
     if (col + 1 < a.ncol) __syncthreads();
   }
-  // an element that never reached the pointwise step (cannot happen today) must not leave its copy in flight
-  if (STAGE && !have_q && ij == 0 && active) mbar_wait(&bar[el], 0);
+  // the block must not exit while its copy may still be writing shared memory: an element whose
+  // wait gave up (or that never reached the pointwise step) waits once more, with the default bound
+  if (STAGE && (!have_q || !q_ok) && active) mbar_wait(&bar[el], 0);
   if constexpr (STAGE) {  // retire the barrier so the slot can be initialised again by the next block
     __syncthreads();
     if (ij == 0) asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(smem_u32(&bar[el])) : "memory");
@@ -587,6 +591,7 @@ int launch_variant(ceed_mesh_t m, const OpTab<T> &tab, const ApplyReq &r, int ne
   a.masked = r.masked;
   a.ne = ne;
   a.err = m->d_err + 1;
+  a.wait_limit = copy_wait_limit();
   a.estride = qdata_estride(OP, sizeof(TQ), Q);
   a.dot_part = (r.ncol == 1) ? r.dot_part : nullptr;
   a.dot_base = 0;

@@ -26,12 +26,13 @@ struct BatchArgs {
   int n, max_colors;
   unsigned *sync;                           // [0] arrivals, [1] generation
   int *err;
+  long long grid_wait;                      // polls of the grid barrier before it gives up
   BatchMesh m[BATCH_MAX];
   OpTab<T> tab[BATCH_MAX];
 };
 
 // Bounded grid barrier (sense by generation counter).  Returns false on timeout.
-__device__ __forceinline__ bool grid_barrier(unsigned *sync, int *err, int *ok_sh) {
+__device__ __forceinline__ bool grid_barrier(unsigned *sync, int *err, long long limit, int *ok_sh) {
   __syncthreads();
   if (threadIdx.x == 0) {
     int ok = 1;
@@ -46,7 +47,7 @@ __device__ __forceinline__ bool grid_barrier(unsigned *sync, int *err, int *ok_s
     } else {
       long long it = 0;
       while (*vgen == gen) {
-        if (++it > (1LL << 25)) {
+        if (++it > limit) {
           ok = 0;
           *err = CEED_ERR_TIMEOUT;
           break;
@@ -119,7 +120,7 @@ __global__ void __launch_bounds__(APPLY_MAX_THREADS) batch_kernel(const BatchArg
 #undef CEEDGB_BCASE
       __syncthreads();  // shared memory is reused by the next block of work
     }
-    if (c + 1 < b.max_colors && !grid_barrier(b.sync, b.err, &ok_sh)) return;
+    if (c + 1 < b.max_colors && !grid_barrier(b.sync, b.err, b.grid_wait, &ok_sh)) return;
   }
 }
 
@@ -146,6 +147,7 @@ int launch_batch(int n, ceed_mesh_t const *meshes, const ApplyReq *reqs, const O
   b.n = n;
   b.sync = sync;
   b.err = err;
+  b.grid_wait = grid_wait_limit();
   size_t smem = 0;
   const bool colloc = meshes[0]->Q == meshes[0]->P;
   for (int k = 0; k < n; ++k) {
@@ -166,6 +168,7 @@ int launch_batch(int n, ceed_mesh_t const *meshes, const ApplyReq *reqs, const O
     bm.a.ne = L.threads / (m->Q * m->Q);
     if (bm.a.ne < 1) return fail(CEED_ERR_INVALID, "block too small for this order");
     bm.a.err = err;
+    bm.a.wait_limit = copy_wait_limit();
     bm.a.estride = qdata_estride(OP, sizeof(TQ), m->Q);
     bm.a.dot_part = nullptr;
     bm.a.dot_base = 0;
@@ -184,9 +187,21 @@ int launch_batch(int n, ceed_mesh_t const *meshes, const ApplyReq *reqs, const O
     if (per_sm < 1) return fail(CEED_ERR_UNSUPPORTED, "batched kernel does not fit on an SM");
     unsigned grid = (unsigned)(per_sm * nsm);
     if (L.grid > 0 && L.grid < grid) grid = L.grid;
-    kernel<<<grid, L.threads, smem, s>>>(b);
+    // cooperative launch: the runtime refuses it unless every block of the grid can be resident at
+    // once, which is what the grid barrier between colours relies on (the barrier's bounded wait
+    // stays as a second line of defence)
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(L.threads);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    CEED_CUDA_CHECK(cudaLaunchKernelEx(&cfg, kernel, b));
     if (grid_used) *grid_used = grid;
-    CEED_CUDA_CHECK(cudaGetLastError());
     return CEED_OK;
   };
   if (colloc) return L.stage ? go(batch_kernel<OP, T, TQ, true, true>) : go(batch_kernel<OP, T, TQ, false, true>);

@@ -5,14 +5,16 @@
 namespace ceedgb {
 
 // FP64 -> FP32, round to nearest even, with integer instructions only.  Magnitudes below 2^-126
-// flush to signed zero; Inf/NaN map to Inf/NaN; finite values beyond the float range are not
-// expected here (L-vector entries of a PDE solve).
+// flush to signed zero (FP32 denormals are not produced); Inf/NaN map to Inf/NaN; finite values of
+// magnitude 2^128 and above become signed Inf, and values that round up past FLT_MAX carry into
+// the Inf exponent, as IEEE rounding does.
 __device__ __forceinline__ float d2f_int(double d) {
   const unsigned long long b = (unsigned long long)__double_as_longlong(d);
   const unsigned hi = (unsigned)(b >> 32), lo = (unsigned)b;
   const unsigned sign = hi & 0x80000000u;
   const int e = (int)((hi >> 20) & 0x7ffu);
   if (e == 0x7ff) return __uint_as_float(sign | 0x7f800000u | ((hi & 0xfffffu) ? 0x400000u : 0u));
+  if (e >= 1023 + 128) return __uint_as_float(sign | 0x7f800000u);
   if (e < 1023 - 126) return __uint_as_float(sign);
   const unsigned mant = ((hi & 0xfffffu) << 3) | (lo >> 29);
   const unsigned rest = lo & 0x1fffffffu;
@@ -38,13 +40,15 @@ __device__ __forceinline__ double f2d_int(float f) {
 // mantissa bits into float position; for the float range the double exponent is the float one plus
 // 896 (= 3*256 + 128), so its low 8 bits differ from the float exponent only in the top bit (XOR).
 // Rounds half up on the first dropped bit.  Magnitudes below 2^-126 give signed zero, Inf/NaN stay
-// Inf/NaN; values beyond the float range are not expected (L-vector entries).
+// Inf/NaN, finite magnitudes of 2^128 and above saturate to signed Inf (a value rounding up past
+// FLT_MAX carries into the Inf exponent by itself).
 __device__ __forceinline__ float d2f_fast(double d) {
   const unsigned hi = (unsigned)__double2hiint(d), lo = (unsigned)__double2loint(d);
   const unsigned sign = hi & 0x80000000u, mag = hi & 0x7fffffffu;
   unsigned f = ((__funnelshift_l(lo, hi, 3) & 0x7fffffffu) ^ 0x40000000u) | sign;
   f += (lo >> 28) & 1u;
   f = (mag < 0x38100000u) ? sign : f;
+  f = (mag >= 0x47f00000u) ? (sign | 0x7f800000u) : f;
   f = (mag >= 0x7ff00000u) ? (sign | 0x7f800000u | ((mag & 0xfffffu) | lo ? 0x400000u : 0u)) : f;
   return __uint_as_float(f);
 }

@@ -66,14 +66,25 @@ __device__ __forceinline__ void acc_mac(DFAcc &A, DF m, DF v) {
   A.c += q + e;
 }
 
+// First term of a Dot2 sum: the exact product split (TwoProduct) and its cross terms, with no
+// TwoSum against an empty accumulator.  Bit-identical to acc_mac on {0, 0} (TwoSum(0, p) = (p, 0)
+// exactly), but the compiler cannot drop those additions itself (0 + x differs from x for x = -0).
+__device__ __forceinline__ DFAcc acc_first(DF m, DF v) {
+  const float p = m.hi * v.hi;
+  float e = fmaf(m.hi, v.hi, -p);
+  e = fmaf(m.hi, v.lo, e);
+  e = fmaf(m.lo, v.hi, e);
+  return DFAcc{p, e};
+}
+
 __device__ __forceinline__ DF acc_get(const DFAcc &A) { return DF(A.s, A.c); }
 
 // y = sum_j M_j v_j over an NI-term row stored with stride 1 (used by the even-odd kernels).
 template <int N>
 __device__ __forceinline__ DF df_dot(const DF *m, const DF *v) {
-  DFAcc A{0.f, 0.f};
+  DFAcc A = acc_first(m[0], v[0]);
 #pragma unroll
-  for (int j = 0; j < N; ++j) acc_mac(A, m[j], v[j]);
+  for (int j = 1; j < N; ++j) acc_mac(A, m[j], v[j]);
   return acc_get(A);
 }
 

@@ -58,6 +58,14 @@ __host__ __device__ inline int64_t qdata_estride(int op, size_t elem_bytes, int 
   return ((b + 15) / 16) * 16 / (int64_t)elem_bytes;
 }
 
+// Bounded device waits: polls of a TMA copy's mbarrier, and of the persistent batched launch's grid
+// barrier, before the kernel gives up and records CEED_ERR_TIMEOUT.  ceed_set_wait_limits overrides
+// both (process-wide, for launches issued afterwards) so that tests can make the waits run out.
+constexpr int WAIT_COPY_DEFAULT = 1 << 22;
+constexpr long long WAIT_GRID_DEFAULT = 1LL << 25;
+int copy_wait_limit();
+long long grid_wait_limit();
+
 struct QRule {
   double x[MAX_Q];
   double w[MAX_Q];

@@ -1,5 +1,6 @@
 // Mesh handle: 1D bases, element colouring, colour-sorted restriction; apply entry points.
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstring>
 #include <map>
@@ -38,6 +39,11 @@ int ensure_dynamic_smem(const void *func, size_t bytes) {
   }
   return CEED_OK;
 }
+
+static std::atomic<int> g_copy_wait{WAIT_COPY_DEFAULT};
+static std::atomic<long long> g_grid_wait{WAIT_GRID_DEFAULT};
+int copy_wait_limit() { return g_copy_wait.load(std::memory_order_relaxed); }
+long long grid_wait_limit() { return g_grid_wait.load(std::memory_order_relaxed); }
 
 int check_mesh(ceed_mesh_t m) {
   if (!m) return fail(CEED_ERR_INVALID, "null mesh handle");
@@ -449,6 +455,28 @@ extern "C" int ceed_mesh_info(ceed_mesh_t m, int32_t *n_colors, int32_t *Q, int3
   if (n_colors) *n_colors = m->n_colors;
   if (Q) *Q = m->Q;
   if (P) *P = m->P;
+  return CEED_OK;
+}
+
+extern "C" int ceed_set_wait_limits(int64_t copy_polls, int64_t barrier_polls) {
+  if (copy_polls > WAIT_COPY_DEFAULT || barrier_polls > WAIT_GRID_DEFAULT)
+    return fail(CEED_ERR_INVALID, "wait limits above the defaults are not accepted");
+  g_copy_wait.store(copy_polls < 0 ? WAIT_COPY_DEFAULT : (int)copy_polls, std::memory_order_relaxed);
+  g_grid_wait.store(barrier_polls < 0 ? WAIT_GRID_DEFAULT : (long long)barrier_polls, std::memory_order_relaxed);
+  return CEED_OK;
+}
+
+extern "C" int ceed_mesh_status(ceed_mesh_t m, void *stream) {
+  if (int st = check_mesh(m)) return st;
+  cudaStream_t s = (cudaStream_t)stream;
+  int err = 0;
+  CEED_CUDA_CHECK(cudaMemcpyAsync(&err, m->d_err + 1, sizeof(int), cudaMemcpyDeviceToHost, s));
+  CEED_CUDA_CHECK(cudaStreamSynchronize(s));
+  if (err) {
+    CEED_CUDA_CHECK(cudaMemsetAsync(m->d_err + 1, 0, sizeof(int), s));
+    CEED_CUDA_CHECK(cudaStreamSynchronize(s));
+    return fail(CEED_ERR_TIMEOUT, "an apply kernel's quadrature-data copy wait gave up");
+  }
   return CEED_OK;
 }
 

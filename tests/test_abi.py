@@ -117,3 +117,12 @@ def test_struct_layouts_match_header(tmp_path):
         assert got[(cname, "size")] == ctypes.sizeof(cls), cname
         for fname, _ in cls._fields_:
             assert got[(cname, fname)] == getattr(cls, fname).offset, (cname, fname)
+
+
+def test_wait_limits_validated_on_the_host():
+    # limits above the defaults are refused before anything reaches a device; -1 restores them
+    import paper_2109_05072_gb300 as ceed
+    assert ceed._lib.ceed_set_wait_limits(1 << 23, -1) == ceed.CEED_ERR_INVALID
+    assert ceed._lib.ceed_set_wait_limits(-1, 1 << 26) == ceed.CEED_ERR_INVALID
+    assert ceed._lib.ceed_set_wait_limits(-1, -1) == ceed.CEED_OK
+    assert ceed._lib.ceed_fma_throughput(3, None, None, None, None) == ceed.CEED_ERR_INVALID

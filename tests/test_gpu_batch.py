@@ -36,6 +36,10 @@ def _case(ceed, specs, qkind, op, prec, ncomp, nrhs):
 
 @pytest.mark.parametrize("specs,qkind,op,prec,ncomp,nrhs", [
     ([(3, (4, 3, 3)), (5, (3, 2, 2)), (7, (2, 2, 2))], "gauss", "diffusion", 0, 3, 2),
+    # the right-hand-side counts bench.py times: 3 components x 8 and x 16 (48 interleaved columns)
+    ([(3, (4, 3, 3)), (5, (3, 2, 2)), (7, (2, 2, 2))], "gauss", "diffusion", 0, 3, 8),
+    ([(3, (4, 3, 3)), (5, (3, 2, 2)), (7, (2, 2, 2))], "gauss", "diffusion", 0, 3, 16),
+    ([(3, (4, 3, 3)), (7, (2, 2, 2))], "gauss", "diffusion", 1, 3, 16),
     ([(2, (3, 3, 2)), (4, (2, 3, 2))], "gll", "diffusion", 0, 1, 4),
     ([(3, (3, 3, 3)), (5, (2, 2, 3))], "gauss", "mass", 0, 3, 1),
     ([(3, (4, 3, 3)), (7, (2, 2, 2))], "gauss", "diffusion", 1, 3, 1),

@@ -4,7 +4,7 @@
   sin (90,518,849 DOFs), the autotuned apply kernel variant, FP64 / double-float / FP32 / BF16
   quadrature data.
 * The batched mixed-order apply: p = 3, 5, 7 on 48^3, 40^3, 32^3 (Gauss q = p + 2), 3 components,
-  4 right-hand sides, one autotuned persistent launch.
+  4, 8 and 16 right-hand sides, one autotuned persistent launch.
 * The adjoint: p = 4 on 32^3 with a lognormal per-point coefficient, geometry stored and recomputed.
 
 The oracle cannot run whole actions at these sizes, so it computes sampled output entries one by
@@ -127,20 +127,33 @@ def test_headline_apply_sampled(ceed, headline, prec, tol):
     torch.cuda.empty_cache()
 
 
-def test_batched_mixed_order_sampled(ceed):
-    specs, ncomp, nrhs = [(3, 48), (5, 40), (7, 32)], 3, 4
-    ms, meshes, qds, xs_host, xs, ys = [], [], [], [], [], []
-    for k, (p, N) in enumerate(specs):
+@pytest.fixture(scope="module")
+def batched_meshes(ceed):
+    specs, ncomp = [(3, 48), (5, 40), (7, 32)], 3
+    ms, meshes, qds = [], [], []
+    for p, N in specs:
         m = synthetic.cube_mesh(N, p, seed=0)
         mesh = ceed.ceed_setup_mesh(m.n_elem, m.n_ldof, p, torch.from_numpy(m.elem_dofs).cuda(),
                                     torch.from_numpy(m.vertices).cuda(), None, q_rule=ceed.CEED_QRULE_GAUSS,
                                     ncomp=ncomp)
         qd = ceed.alloc_qdata(mesh, ceed.CEED_OP_DIFFUSION, ceed.CEED_F64)
         ceed.ceed_build_qdata(mesh, ceed.CEED_OP_DIFFUSION, ceed.CEED_COEFF_SINE, None, ceed.CEED_F64, qd)
-        xh = synthetic.uniform(m.n_ldof * ncomp * nrhs, seed=7 + k)
         ms.append(m)
         meshes.append(mesh)
         qds.append(qd)
+    yield specs, ncomp, ms, meshes, qds
+    for mesh in meshes:
+        mesh.close()
+
+
+@pytest.mark.parametrize("nrhs", [4, 8, 16])
+def test_batched_mixed_order_sampled(ceed, batched_meshes, nrhs):
+    """Every right-hand-side count bench.py times except 1 (covered by the single-mesh tests);
+    nrhs = 16 is 48 interleaved columns per node (x and y: 17 GB on the device)."""
+    specs, ncomp, ms, meshes, qds = batched_meshes
+    xs_host, xs, ys = [], [], []
+    for k, m in enumerate(ms):
+        xh = synthetic.uniform(m.n_ldof * ncomp * nrhs, seed=7 + k)
         xs_host.append(xh)
         xs.append(torch.from_numpy(xh).cuda())
         ys.append(torch.full_like(xs[-1], float("nan")))
@@ -149,16 +162,14 @@ def test_batched_mixed_order_sampled(ceed):
     ceed.ceed_batch_apply(batch)
     ceed.ceed_batch_status(batch)
     for k, ((p, N), m) in enumerate(zip(specs, ms)):
-        nodes = _sample_nodes(np.random.default_rng(200 + k), N, p, n_each=20)
+        nodes = _sample_nodes(np.random.default_rng(200 + k + nrhs), N, p, n_each=12)
         X = xs_host[k].reshape(m.n_ldof, ncomp * nrhs)   # [node][component][rhs], A acts on each column
         node_id, ref, counts = _sampled_action(m, N, p, nodes, X, _SineQdata(m, p, "gauss"))
         assert set(counts.tolist()) >= {1, 2, 8}
         got = ys[k].view(m.n_ldof, ncomp * nrhs)[torch.from_numpy(node_id).cuda()].cpu().numpy()
         _close(got, ref, 1e-12)
     batch.close()
-    for mesh in meshes:
-        mesh.close()
-    del qds, xs, ys
+    del xs, ys, xs_host
     torch.cuda.empty_cache()
 
 
