@@ -26,6 +26,7 @@
 #pragma once
 
 #include <cuda_bf16.h>
+#include <type_traits>
 #include <cuda_fp16.h>
 
 #include "convert.cuh"
@@ -81,6 +82,12 @@ __device__ __forceinline__ void tma_bulk_load(void *dst, const void *src, uint32
                : "memory");
 }
 
+// Asks the memory system to bring `bytes` (a multiple of 16, 16-byte aligned) at `src` into L2,
+// without waiting and without touching shared memory or registers.
+__device__ __forceinline__ void l2_prefetch_bulk(const void *src, uint32_t bytes) {
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(src), "r"(bytes) : "memory");
+}
+
 // Bounded wait on phase `parity`: returns false if the copy did not land within `limit` polls.
 __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, int limit = WAIT_COPY_DEFAULT) {
   const uint32_t a = smem_u32(bar);
@@ -132,6 +139,9 @@ __device__ __forceinline__ void eo_apply(const EOMat<T> &M, const T *v, T *out) 
 }
 
 constexpr int APPLY_MAX_THREADS = 256;
+#ifndef APPLY_DF_MAX_REGS
+#define APPLY_DF_MAX_REGS 128
+#endif
 constexpr int APPLY_MAX_NE = 32;
 
 // g1 a + g2 b + g3 c and a + b + c: plain FMAs for float/double, compensated for double-float
@@ -165,37 +175,42 @@ __device__ __forceinline__ DF add3<DF>(DF a, DF b, DF c) {
 }
 
 // Even-odd 1D operator in double-float: folds/unfolds by exact-sum additions, the two half-size
-// products by compensated dot products (same algebra as the float/double version below).
+// products by compensated dot products (same algebra as the float/double version above).  Row i's
+// two sums, A = sum_j E_ij e_j and B = sum_j O_ij o_j, are independent and take the same steps, so
+// they run side by side in the two lanes of packed FP32 instructions (lane 0 = A, lane 1 = B).
+// With an odd NI the middle input's term cmid_i v_mid ends A's sum; lane 1 adds 0 * 0 meanwhile,
+// which leaves B unchanged.
 template <int NO, int NI, int S>
 __device__ __forceinline__ void eo_apply(const EOMat<DF> &M, const DF *v, DF *out) {
   constexpr int HI = NI / 2, HO = NO / 2;
-  DF e[HI > 0 ? HI : 1], o[HI > 0 ? HI : 1];
+  float2 eoh[HI > 0 ? HI : 1], eol[HI > 0 ? HI : 1];  // (e_j, o_j): high words, low words
 #pragma unroll
   for (int j = 0; j < HI; ++j) {
-    e[j] = df_add(v[j], v[NI - 1 - j]);
-    o[j] = df_sub(v[j], v[NI - 1 - j]);
+    const DF e = df_add(v[j], v[NI - 1 - j]), o = df_sub(v[j], v[NI - 1 - j]);
+    eoh[j] = make_float2(e.hi, o.hi);
+    eol[j] = make_float2(e.lo, o.lo);
   }
 #pragma unroll
   for (int i = 0; i < HO; ++i) {
-    // each sum starts from its first exact product (the same terms in the same order as a sum
-    // started from zero, without the TwoSum against zero)
-    DFAcc A = (NI & 1) ? acc_first(M.cmid[i], v[HI]) : acc_first(M.E[i * EO_H], e[0]);
-    DFAcc B = acc_first(M.O[i * EO_H], o[0]);
-    if (NI & 1) acc_mac(A, M.E[i * EO_H], e[0]);
+    DFAcc2 AB = acc2_first(M.eo_hi[i * EO_H], M.eo_lo[i * EO_H], eoh[0], eol[0]);
 #pragma unroll
-    for (int j = 1; j < HI; ++j) {
-      acc_mac(A, M.E[i * EO_H + j], e[j]);
-      acc_mac(B, M.O[i * EO_H + j], o[j]);
-    }
-    const DF a = acc_get(A), b = acc_get(B);
+    for (int j = 1; j < HI; ++j) acc2_mac(AB, M.eo_hi[i * EO_H + j], M.eo_lo[i * EO_H + j], eoh[j], eol[j]);
+    if constexpr (NI & 1)
+      acc2_mac(AB, make_float2(M.cmid[i].hi, 0.f), make_float2(M.cmid[i].lo, 0.f), make_float2(v[HI].hi, 0.f),
+               make_float2(v[HI].lo, 0.f));
+    const DF a(AB.s.x, AB.c.x), b(AB.s.y, AB.c.y);
     out[i] = df_add(a, b);
     out[NO - 1 - i] = (S > 0) ? df_sub(a, b) : df_sub(b, a);
   }
   if constexpr (NO & 1) {
-    DFAcc C = (NI & 1) ? acc_first(M.cc, v[HI]) : acc_first(M.rmid[0], (S > 0) ? e[0] : o[0]);
-    if (NI & 1) acc_mac(C, M.rmid[0], (S > 0) ? e[0] : o[0]);
+    const DF e0(eoh[0].x, eol[0].x), o0(eoh[0].y, eol[0].y);
+    DFAcc C = (NI & 1) ? acc_first(M.cc, v[HI]) : acc_first(M.rmid[0], (S > 0) ? e0 : o0);
+    if (NI & 1) acc_mac(C, M.rmid[0], (S > 0) ? e0 : o0);
 #pragma unroll
-    for (int j = 1; j < HI; ++j) acc_mac(C, M.rmid[j], (S > 0) ? e[j] : o[j]);
+    for (int j = 1; j < HI; ++j) {
+      const DF ej(eoh[j].x, eol[j].x), oj(eoh[j].y, eol[j].y);
+      acc_mac(C, M.rmid[j], (S > 0) ? ej : oj);
+    }
     out[HO] = acc_get(C);
   }
 }
@@ -286,6 +301,11 @@ __device__ __forceinline__ void apply_block(const ApplyArgs &a, const OpTab<T> &
         tma_bulk_load((void *)sq, (const TQ *)a.qdata + e * a.estride, (uint32_t)(a.estride * sizeof(TQ)), &bar[el]);
     }
     __syncthreads();  // barrier initialised before any thread waits on it
+  } else {
+    // quadrature data read at the pointwise step: start moving the element's block towards L2 now,
+    // so that those loads wait for L2 rather than DRAM
+    if (ij == 0 && active)
+      l2_prefetch_bulk((const TQ *)a.qdata + e * a.estride, (uint32_t)(a.estride * sizeof(TQ)));
   }
 
   // ---- restriction of my node column (a = i, b = j, c = 0..P-1)
@@ -302,6 +322,9 @@ __device__ __forceinline__ void apply_block(const ApplyArgs &a, const OpTab<T> &
 
   for (int col = 0; col < a.ncol; ++col) {
     // ---- all global loads of the column up front: x at my nodes, old y where an earlier colour wrote
+    // (the double-float operator, whose element work is long and register-hungry, loads the old y
+    // only at the scatter: holding it across the element would cost 2P registers of occupancy)
+    constexpr bool EARLY_YOLD = !std::is_same<T, DF>::value;
     double xv[P], yold[P];
 #pragma unroll
     for (int c = 0; c < P; ++c) {
@@ -312,7 +335,7 @@ __device__ __forceinline__ void apply_block(const ApplyArgs &a, const OpTab<T> &
         const int64_t o = (int64_t)(v & DOF_MASK) * a.ncol + col;
         const bool dir = a.masked && (v & FLAG_DIR);
         if (!dir) xv[c] = __ldg(a.x + o);
-        if (!dir && !(v & FLAG_FIRST)) yold[c] = __ldcg(a.y + o);  // L2: written by an earlier colour
+        if (EARLY_YOLD && !dir && !(v & FLAG_FIRST)) yold[c] = __ldcg(a.y + o);  // L2: written by an earlier colour
       }
     }
     T u[P];
@@ -508,6 +531,16 @@ __device__ __forceinline__ void apply_block(const ApplyArgs &a, const OpTab<T> &
     }
 
     // ---- scatter-add (E -> L), atomic-free
+    if constexpr (!EARLY_YOLD) {
+      if (active && node_thread && q_ok) {
+#pragma unroll
+        for (int c = 0; c < P; ++c) {
+          const uint32_t v = idx[c];
+          const int64_t o = (int64_t)(v & DOF_MASK) * a.ncol + col;
+          if (!(a.masked && (v & FLAG_DIR)) && !(v & FLAG_FIRST)) yold[c] = __ldcg(a.y + o);
+        }
+      }
+    }
     if (!a.dot_part) {
       if (active && node_thread && q_ok) {
 #pragma unroll
@@ -576,11 +609,26 @@ apply_kernel(const ApplyArgs a, const OpTab<T> tab) {
   apply_block<P, Q, OP, T, TQ, STAGE>(a, tab, blockIdx.x, smem_raw, bar);
 }
 
+// The double-float instantiations under a register cap: that operator is bound by latency
+// (dependent compensated sums, quadrature-data loads), so it is given more resident warps to switch
+// between instead of registers to hoist loads into (128: the best of 96..255 measured at p = 7).
+// Blocks of at most APPLY_MAX_THREADS threads.
+template <int P, int Q, int OP, typename T, typename TQ, bool STAGE>
+__global__ void __maxnreg__(APPLY_DF_MAX_REGS) apply_kernel_capped(const ApplyArgs a, const OpTab<T> tab) {
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  __shared__ uint64_t bar[STAGE ? APPLY_MAX_NE : 1];
+  apply_block<P, Q, OP, T, TQ, STAGE>(a, tab, blockIdx.x, smem_raw, bar);
+}
+
 // Launch one kernel per colour for a fixed (P, Q, op, T, TQ) and variant (elements per block, staging).
 template <int P, int Q, int OP, typename T, typename TQ, bool STAGE>
 int launch_variant(ceed_mesh_t m, const OpTab<T> &tab, const ApplyReq &r, int ne, cudaStream_t s) {
   const size_t smem = (size_t)ne * apply_elem_smem<P, Q, OP, T, TQ, STAGE>();
-  if (int st = ensure_dynamic_smem((const void *)apply_kernel<P, Q, OP, T, TQ, STAGE>, smem)) return st;
+  constexpr bool CAPPED = std::is_same<T, DF>::value;
+  const void *kfn;
+  if constexpr (CAPPED) kfn = (const void *)apply_kernel_capped<P, Q, OP, T, TQ, STAGE>;
+  else kfn = (const void *)apply_kernel<P, Q, OP, T, TQ, STAGE>;
+  if (int st = ensure_dynamic_smem(kfn, smem)) return st;
   const dim3 block(Q * Q * ne);
   ApplyArgs a;
   a.emap = m->d_emap;
@@ -601,7 +649,8 @@ int launch_variant(ceed_mesh_t m, const OpTab<T> &tab, const ApplyReq &r, int ne
     if (n == 0) continue;
     a.e_count = n;
     const dim3 grid((unsigned)((n + ne - 1) / ne));
-    apply_kernel<P, Q, OP, T, TQ, STAGE><<<grid, block, smem, s>>>(a, tab);
+    if constexpr (CAPPED) apply_kernel_capped<P, Q, OP, T, TQ, STAGE><<<grid, block, smem, s>>>(a, tab);
+    else apply_kernel<P, Q, OP, T, TQ, STAGE><<<grid, block, smem, s>>>(a, tab);
     a.dot_base += grid.x;
   }
   if (r.dot_n) *r.dot_n = a.dot_part ? a.dot_base : 0;

@@ -55,8 +55,10 @@ struct DFAcc {
   float s, c;
 };
 
+// (products by __fmul_rn: the compiler may not contract them into a later addition, which would
+// break the error-free transformations)
 __device__ __forceinline__ void acc_mac(DFAcc &A, DF m, DF v) {
-  const float p = m.hi * v.hi;
+  const float p = __fmul_rn(m.hi, v.hi);
   float e = fmaf(m.hi, v.hi, -p);  // TwoProduct error, exact
   e = fmaf(m.hi, v.lo, e);
   e = fmaf(m.lo, v.hi, e);
@@ -70,7 +72,7 @@ __device__ __forceinline__ void acc_mac(DFAcc &A, DF m, DF v) {
 // TwoSum against an empty accumulator.  Bit-identical to acc_mac on {0, 0} (TwoSum(0, p) = (p, 0)
 // exactly), but the compiler cannot drop those additions itself (0 + x differs from x for x = -0).
 __device__ __forceinline__ DFAcc acc_first(DF m, DF v) {
-  const float p = m.hi * v.hi;
+  const float p = __fmul_rn(m.hi, v.hi);
   float e = fmaf(m.hi, v.hi, -p);
   e = fmaf(m.hi, v.lo, e);
   e = fmaf(m.lo, v.hi, e);
@@ -86,6 +88,41 @@ __device__ __forceinline__ DF df_dot(const DF *m, const DF *v) {
 #pragma unroll
   for (int j = 1; j < N; ++j) acc_mac(A, m[j], v[j]);
   return acc_get(A);
+}
+
+// ---------------------------------------------------------------- two sums side by side
+// The same Dot2 steps on two independent sums at once, one per lane of a float2, with the packed
+// two-lane FP32 instructions of sm_100 and later (fma.rn.f32x2 and friends): each lane is rounded
+// exactly as the scalar operation would be, and one instruction issues the work of two.
+__device__ __forceinline__ float2 neg2(float2 a) { return make_float2(-a.x, -a.y); }
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __fadd2_rn(a, neg2(b)); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+
+struct DFAcc2 {
+  float2 s, c;
+};
+
+// first term m v of both sums: (mh, ml) and (vh, vl) hold the two lanes' high and low words
+__device__ __forceinline__ DFAcc2 acc2_first(float2 mh, float2 ml, float2 vh, float2 vl) {
+  const float2 p = mul2(mh, vh);
+  float2 e = fma2(mh, vh, neg2(p));  // TwoProduct error, exact
+  e = fma2(mh, vl, e);
+  e = fma2(ml, vh, e);
+  return DFAcc2{p, e};
+}
+
+__device__ __forceinline__ void acc2_mac(DFAcc2 &A, float2 mh, float2 ml, float2 vh, float2 vl) {
+  const float2 p = mul2(mh, vh);
+  float2 e = fma2(mh, vh, neg2(p));
+  e = fma2(mh, vl, e);
+  e = fma2(ml, vh, e);
+  const float2 t = add2(A.s, p);       // TwoSum(A.s, p), lane by lane
+  const float2 z = sub2(t, A.s);
+  const float2 q = add2(sub2(A.s, sub2(t, z)), sub2(p, z));
+  A.s = t;
+  A.c = add2(A.c, add2(q, e));
 }
 
 // Host/device split of a double into the nearest float and the float nearest to the remainder.

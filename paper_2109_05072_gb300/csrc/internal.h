@@ -35,6 +35,19 @@ struct EOMat {
   T cc;
 };
 
+// Double-float form of the even-odd blocks, laid out for packed two-lane FP32 arithmetic: entry k
+// of the E block and entry k of the O block side by side (lane 0 = E, lane 1 = O), high words in
+// eo_hi and low words in eo_lo; same size as the generic layout.
+template <>
+struct EOMat<DF> {
+  float2 eo_hi[EO_H * EO_H];
+  float2 eo_lo[EO_H * EO_H];
+  DF cmid[EO_H];
+  DF rmid[EO_H];
+  DF cc;
+};
+static_assert(sizeof(EOMat<DF>) == sizeof(EOMat<double>), "double-float even-odd blocks: layout size");
+
 // 1D operators passed to kernels by value (kernel parameters live in the constant bank, so
 // compile-time indices become constant operands of the FMAs).
 template <typename T>

@@ -235,6 +235,21 @@ static void build_tables(ceed_mesh_s *m) {
   DF *dst = reinterpret_cast<DF *>(&m->tabdf);
   static_assert(sizeof(OpTab<double>) == sizeof(OpTab<DF>), "table layouts differ");
   for (size_t k = 0; k < sizeof(OpTab<double>) / sizeof(double); ++k) dst[k] = df_from_double(src[k]);
+  // the even-odd blocks of the double-float tables use their own (E, O)-interleaved layout
+  const EOMat<double> *e64[4] = {&m->tab64.eB, &m->tab64.eBT, &m->tab64.eD, &m->tab64.eDT};
+  EOMat<DF> *edf[4] = {&m->tabdf.eB, &m->tabdf.eBT, &m->tabdf.eD, &m->tabdf.eDT};
+  for (int t = 0; t < 4; ++t) {
+    for (int k = 0; k < EO_H * EO_H; ++k) {
+      const DF e = df_from_double(e64[t]->E[k]), o = df_from_double(e64[t]->O[k]);
+      edf[t]->eo_hi[k] = make_float2(e.hi, o.hi);
+      edf[t]->eo_lo[k] = make_float2(e.lo, o.lo);
+    }
+    for (int k = 0; k < EO_H; ++k) {
+      edf[t]->cmid[k] = df_from_double(e64[t]->cmid[k]);
+      edf[t]->rmid[k] = df_from_double(e64[t]->rmid[k]);
+    }
+    edf[t]->cc = df_from_double(e64[t]->cc);
+  }
 }
 
 int launch_apply(ceed_mesh_t m, const ApplyReq &r, cudaStream_t s);

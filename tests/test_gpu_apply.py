@@ -186,7 +186,9 @@ def test_setup_diagonal_and_rhs(ceed):
                                              (3, "gauss", "mass", 0), (5, "gauss", "diffusion", 2), (2, "gll", "diffusion", 1),
                                              (5, "gll", "diffusion", 1), (3, "gll", "diffusion", 2), (1, "gll", "diffusion", 1),
                                              (7, "gll", "diffusion", 4), (4, "gauss", "diffusion", 4),
-                                             (7, "gll", "diffusion", 5)])
+                                             (7, "gll", "diffusion", 5), (8, "gauss", "diffusion", 5),
+                                             (3, "gauss", "mass", 5), (2, "gll", "diffusion", 5),
+                                             (1, "gll", "mass", 5), (5, "gll", "mass", 5), (6, "gauss", "diffusion", 5)])
 def test_apply_variants_identical_and_autotune(ceed, p, qkind, op, prec):
     # every (elements per block, staging) variant runs the same arithmetic: bitwise-identical output
     m = synthetic.HexMesh(5, 3, 3, p, seed=13)
@@ -214,6 +216,8 @@ def test_apply_variants_identical_and_autotune(ceed, p, qkind, op, prec):
     assert torch.equal(y, outs[0])
     with pytest.raises(ceed.CeedError):
         ceed.ceed_set_apply_variant(mesh, cop, prec, ne_max + 1, 1)
+    with pytest.raises(ceed.CeedError):
+        ceed.ceed_set_apply_variant(mesh, cop, prec, 1, 2)
     if prec in (0, 5):
         sp_, qref = oracle_qdata(m, qkind, op, "sine")
         ref = fem.apply(sp_, m.elem_dofs, qref, x.cpu().numpy(), fem.DIFFUSION if op == "diffusion" else fem.MASS)
