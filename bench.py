@@ -484,6 +484,11 @@ def compact_summary(line):
         f = cg.get("fp64_to_1e-10", {})
         out["cg_fp64_s"] = r(f.get("seconds"))
         out["cg_fp64_iters"] = f.get("iterations")
+        out["cg_fp64_100_iters_fused_s"] = r(cg.get("fp64_100_iters_s"))
+        out["cg_fp64_100_iters_separate_s"] = r(cg.get("fp64_100_iters_separate_kernels_s"))
+        sep = cg.get("mixed_f32_reliable_separate_kernels_to_1e-10")
+        if sep:
+            out["cg_mixed_f32_reliable_separate_kernels_s"] = r(sep.get("seconds"))
         for key in ("mixed_f32", "mixed_f32_reliable", "mixed_f64df_reliable", "pmg_fp32_smoothers"):
             d = cg.get(f"{key}_to_1e-10")
             if d:
@@ -681,9 +686,14 @@ def main():
                                      op=ceed.CEED_OP_DIFFUSION)
         cg["fp64_100_iters_s"] = rep["seconds"]
         cg["fp64_100_iters_dof_iter_per_s"] = 100 * m.n_ldof / rep["seconds"]
+        cg["fp64_100_iters_fused"] = rep["fused"]
+        # the same 100 iterations with one kernel per step (apply, reductions, updates)
+        st, rep_sep = ceed.ceed_cg_solve(mesh, qd64, ceed.CEED_F64, b, xs, mode=ceed.CEED_CG_FP64, fixed_iters=100,
+                                         op=ceed.CEED_OP_DIFFUSION, separate_kernels=1)
+        cg["fp64_100_iters_separate_kernels_s"] = rep_sep["seconds"]
         st, rep64 = ceed.ceed_cg_solve(mesh, qd64, ceed.CEED_F64, b, xs, mode=ceed.CEED_CG_FP64, tol=1e-10,
                                        max_iter=20000, op=ceed.CEED_OP_DIFFUSION, raise_on_error=False)
-        cg["fp64_to_1e-10"] = dict(rep64, status=st)
+        cg["fp64_to_1e-10"] = dict(rep64, status=st, ms_per_iter=1e3 * rep64["seconds"] / max(1, rep64["iterations"]))
         # low-precision inner operators: iterative refinement (restarted inner PCG to 1e-4 per pass) and
         # reliable updates (one PCG run, true FP64 residual put in place at every 10x decrease)
         for name, prec, modes in (("f32", ceed.CEED_F32, ("", "reliable")), ("bf16", ceed.CEED_BF16, ("reliable",)),
@@ -697,9 +707,16 @@ def main():
                                               mode=ceed.CEED_CG_MIXED_RELIABLE if mode else ceed.CEED_CG_MIXED,
                                               tol=1e-10, max_iter=8000 if mode else 40000, op=ceed.CEED_OP_DIFFUSION, qdata_lo=qlo,
                                               prec_lo=prec, inner_tol=1e-4, raise_on_error=False)
-                cg[f"{key}_to_1e-10"] = dict(repm, status=st)
+                cg[f"{key}_to_1e-10"] = dict(repm, status=st, ms_per_iter=1e3 * repm["seconds"] / max(1, repm["iterations"]))
                 if rep64["seconds"] > 0 and repm["seconds"] > 0:
                     cg[f"{key}_speedup"] = rep64["seconds"] / repm["seconds"]
+                if name == "f32" and mode == "reliable":
+                    # the same solve with one kernel per step instead of the fused iteration
+                    st, reps = ceed.ceed_cg_solve(mesh, qd64, ceed.CEED_F64, b, xs, mode=ceed.CEED_CG_MIXED_RELIABLE,
+                                                  tol=1e-10, max_iter=8000, op=ceed.CEED_OP_DIFFUSION, qdata_lo=qlo,
+                                                  prec_lo=prec, raise_on_error=False, separate_kernels=1)
+                    cg[f"{key}_separate_kernels_to_1e-10"] = dict(
+                        reps, status=st, ms_per_iter=1e3 * reps["seconds"] / max(1, reps["iterations"]))
             del qlo
         # p-multigrid-preconditioned (flexible) CG: levels p = 7, 3, 1 on the same elements, Chebyshev-Jacobi
         # smoothing (degree 3) with FP64 or FP32-arithmetic level operators, Jacobi-PCG on the p = 1 level

@@ -219,6 +219,10 @@ typedef struct {
                              V-cycle per iteration instead of Jacobi */
   double reliable_delta;  /* MIXED_RELIABLE: replace the recurrence residual by the true FP64 residual
                              each time it has fallen by this factor; 0 -> 0.1, else in (0, 1) */
+  int32_t separate_kernels; /* 0: Jacobi-PCG iterations run as one persistent kernel per batch of
+                               check_every iterations where the (inner) operator allows it (diffusion,
+                               GLL collocated, F64 / F32 / BF16 / F32_GEO / F64_DF); nonzero: one kernel
+                               per step (apply, reductions, updates) */
 } ceed_cg_opts;
 
 typedef struct {
@@ -226,12 +230,19 @@ typedef struct {
   int32_t outer_iterations; /* MIXED: refinement steps; MIXED_RELIABLE: FP64 true-residual evaluations */
   double rel_residual;      /* ||b - A x|| / ||b|| with the FP64 operator at exit */
   double seconds;           /* wall time of the solve, measured with CUDA events */
+  int32_t fused;            /* 1 if the (inner) PCG iterations ran in the fused persistent kernel */
 } ceed_cg_report;
 
 /* Bytes of device workspace ceed_cg_solve needs for these options. */
 size_t ceed_cg_workspace_bytes(ceed_mesh_t mesh, const ceed_cg_opts *opts);
 
 /* Solve A x = b with Jacobi-preconditioned CG (Section 1) on the Dirichlet-masked operator.
+ * Fused iteration (default where supported): one cooperative persistent kernel runs check_every
+ * whole iterations -- the colour-ordered apply q = A p with p.q summed by each node's last writer,
+ * alpha, x and r updates with the r.z and r.r sums (z = D^{-1} r is not stored), beta, p update --
+ * separated by bounded grid barriers; reductions in a fixed order (results are reproducible run to
+ * run, and differ from the separate-kernel path only in rounding order).  A barrier that gives up
+ * returns CEED_ERR_TIMEOUT.
  * FP64 mode: all arithmetic FP64.  MIXED mode: iterative refinement, outer residual
  * r = b - A x with the FP64 operator (qdata, prec), inner PCG with the low-precision operator
  * (opts->qdata_lo, FP32 contractions, or the double-float operator of F64_DF) and FP64 vectors,

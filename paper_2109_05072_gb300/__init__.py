@@ -49,7 +49,7 @@ class _CgOpts(ctypes.Structure):
                 ("check_every", ctypes.c_int32), ("fixed_iters", ctypes.c_int32), ("op", ctypes.c_int32),
                 ("tol", ctypes.c_double), ("inner_tol", ctypes.c_double), ("qdata_lo", ctypes.c_void_p),
                 ("prec_lo", ctypes.c_int32), ("use_x0", ctypes.c_int32), ("pmg", ctypes.c_void_p),
-                ("reliable_delta", ctypes.c_double)]
+                ("reliable_delta", ctypes.c_double), ("separate_kernels", ctypes.c_int32)]
 
 
 class _PmgOpts(ctypes.Structure):
@@ -72,7 +72,7 @@ class _HpDesc(ctypes.Structure):
 
 class _CgReport(ctypes.Structure):
     _fields_ = [("iterations", ctypes.c_int32), ("outer_iterations", ctypes.c_int32),
-                ("rel_residual", ctypes.c_double), ("seconds", ctypes.c_double)]
+                ("rel_residual", ctypes.c_double), ("seconds", ctypes.c_double), ("fused", ctypes.c_int32)]
 
 
 def _load():
@@ -330,7 +330,7 @@ def ceed_cg_solve(mesh: Mesh, qdata, prec, b, x, work=None, stream=None, raise_o
     st = _lib.ceed_cg_solve(mesh.handle, _ptr(qdata), prec, _ptr(b), _ptr(x), ctypes.byref(o), ctypes.byref(rep),
                             _ptr(work), work.numel() * work.element_size(), _stream(stream))
     report = dict(iterations=rep.iterations, outer_iterations=rep.outer_iterations,
-                  rel_residual=rep.rel_residual, seconds=rep.seconds)
+                  rel_residual=rep.rel_residual, seconds=rep.seconds, fused=rep.fused)
     if raise_on_error and st not in (CEED_OK,):
         raise CeedError(st, _lib.ceed_last_error().decode())
     return st, report

@@ -265,12 +265,16 @@ struct ApplyArgs {
   int wait_limit;    // polls of the quadrature-data copy wait before it gives up (CEED_ERR_TIMEOUT)
   double *dot_part;  // optional: partial sums of x_i y_i over the nodes whose final y this block writes
   int64_t dot_base;  // index of this launch's first block in dot_part
+  double *dot_sh;    // optional, instead of dot_part: a shared-memory sum the block adds its partial to
+                     // (thread 0, in the order the block processes its work: a persistent block's sum)
 };
 
 // One thread block's share of a colour: elements e_begin + blk * ne + (0 .. ne-1).  Threads past
 // ne * Q^2 (a block shape that does not divide evenly) act as an inactive element; the caller
 // provides shared memory for ceil(blockDim / Q^2) elements and the mbarrier array.
-template <int P, int Q, int OP, typename T, typename TQ, bool STAGE>
+// XCG: x is read through L2 only (ld.global.cg) instead of the read-only path: required when x
+// changes during the kernel (the persistent CG iteration updates p between its applies).
+template <int P, int Q, int OP, typename T, typename TQ, bool STAGE, bool XCG = false>
 __device__ __forceinline__ void apply_block(const ApplyArgs &a, const OpTab<T> &tab, int64_t blk,
                                             unsigned char *smem_raw, uint64_t *bar) {
   constexpr int NPT = Q * Q;
@@ -334,7 +338,7 @@ __device__ __forceinline__ void apply_block(const ApplyArgs &a, const OpTab<T> &
         const uint32_t v = idx[c];
         const int64_t o = (int64_t)(v & DOF_MASK) * a.ncol + col;
         const bool dir = a.masked && (v & FLAG_DIR);
-        if (!dir) xv[c] = __ldg(a.x + o);
+        if (!dir) xv[c] = XCG ? __ldcg(a.x + o) : __ldg(a.x + o);
         if (EARLY_YOLD && !dir && !(v & FLAG_FIRST)) yold[c] = __ldcg(a.y + o);  // L2: written by an earlier colour
       }
     }
@@ -531,6 +535,7 @@ __device__ __forceinline__ void apply_block(const ApplyArgs &a, const OpTab<T> &
     }
 
     // ---- scatter-add (E -> L), atomic-free
+    const bool fused_dot = a.dot_part || a.dot_sh;
     if constexpr (!EARLY_YOLD) {
       if (active && node_thread && q_ok) {
 #pragma unroll
@@ -541,14 +546,14 @@ __device__ __forceinline__ void apply_block(const ApplyArgs &a, const OpTab<T> &
         }
       }
     }
-    if (!a.dot_part) {
+    if (!fused_dot) {
       if (active && node_thread && q_ok) {
 #pragma unroll
         for (int c = 0; c < P; ++c) {
           const uint32_t v = idx[c];
           const int64_t o = (int64_t)(v & DOF_MASK) * a.ncol + col;
           if (a.masked && (v & FLAG_DIR)) {
-            if (v & FLAG_FIRST) a.y[o] = a.x[o];
+            if (v & FLAG_FIRST) a.y[o] = XCG ? __ldcg(a.x + o) : a.x[o];
           } else if (v & FLAG_FIRST) {
             a.y[o] = LVec<T>::out(yv[c]);
           } else {
@@ -567,14 +572,14 @@ __device__ __forceinline__ void apply_block(const ApplyArgs &a, const OpTab<T> &
           const int64_t o = (int64_t)(v & DOF_MASK) * a.ncol + col;
           if (a.masked && (v & FLAG_DIR)) {
             if (v & FLAG_FIRST) {
-              const double out = a.x[o];
+              const double out = XCG ? __ldcg(a.x + o) : a.x[o];
               a.y[o] = out;
               dot += out * out;
             }
           } else {
             const double out = (v & FLAG_FIRST) ? LVec<T>::out(yv[c]) : LVec<T>::add(yold[c], yv[c]);
             a.y[o] = out;
-            if (v & FLAG_LAST) dot += __ldg(a.x + o) * out;  // reloaded (cache hit): keeps xv dead early
+            if (v & FLAG_LAST) dot += (XCG ? __ldcg(a.x + o) : __ldg(a.x + o)) * out;  // reloaded: keeps xv dead early
           }
         }
       }
@@ -587,7 +592,8 @@ __device__ __forceinline__ void apply_block(const ApplyArgs &a, const OpTab<T> &
       if (tid == 0) {
         double t = 0.0;
         for (int w = 0; w < (int)((blockDim.x + 31) >> 5); ++w) t += dsum[w];
-        a.dot_part[a.dot_base + blk] = t;
+        if (a.dot_sh) *a.dot_sh += t;
+        else a.dot_part[a.dot_base + blk] = t;
       }
     }
     if (col + 1 < a.ncol) __syncthreads();
@@ -643,6 +649,7 @@ int launch_variant(ceed_mesh_t m, const OpTab<T> &tab, const ApplyReq &r, int ne
   a.estride = qdata_estride(OP, sizeof(TQ), Q);
   a.dot_part = (r.ncol == 1) ? r.dot_part : nullptr;
   a.dot_base = 0;
+  a.dot_sh = nullptr;
   for (int c = 0; c < m->n_colors; ++c) {
     a.e_begin = m->color_start[c];
     const int64_t n = m->color_start[c + 1] - a.e_begin;

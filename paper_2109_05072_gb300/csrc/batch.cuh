@@ -172,6 +172,7 @@ int launch_batch(int n, ceed_mesh_t const *meshes, const ApplyReq *reqs, const O
     bm.a.estride = qdata_estride(OP, sizeof(TQ), m->Q);
     bm.a.dot_part = nullptr;
     bm.a.dot_base = 0;
+    bm.a.dot_sh = nullptr;
     b.tab[k] = *tabs[k];
     b.max_colors = std::max(b.max_colors, m->n_colors);
     const size_t sm = L.stage ? batch_smem_for<OP, T, TQ, true>(m->P, m->Q, L.threads)

@@ -13,6 +13,7 @@
 #include <new>
 #include <vector>
 
+#include "cg_fused.cuh"
 #include "internal.h"
 
 namespace ceedgb {
@@ -27,11 +28,7 @@ static int red_blocks(int64_t n) {
   return (int)b;
 }
 
-struct Scalars {
-  double rz, rz_new, pq, alpha, beta, rr, bb, tol2;
-  double rr_out, bb_out;
-  int done, iters, nonfinite, pad;
-};
+using Scalars = CgScalars;
 
 __device__ __forceinline__ double block_sum(double v, double *sh) {
   sh[threadIdx.x] = v;
@@ -234,6 +231,7 @@ __global__ void start_finalize_kernel(const double *__restrict__ part_rz, const 
     sc->rr = b;
     if (set_bb_from_rr) sc->bb = b;
     sc->iters = 0;
+    sc->timeout = 0;
     sc->nonfinite = (!finite(a) || !finite(b)) ? 1 : 0;
     sc->done = sc->nonfinite || (!fixed && b <= sc->tol2 * sc->bb) || b == 0.0;
   }
@@ -277,6 +275,8 @@ struct Work {
   double *r_out, *d, *r, *z, *p, *q, *dinv, *part1, *part2;
   double *r_old;    // flexible CG: residual of the previous iteration
   double *pq_part;  // per-block partial sums of p . q written by the fused apply
+  double *fpart;    // fused iteration: per-block partials [3][CGF_MAX_GRID]
+  unsigned *fsync;  // fused iteration: grid barrier state
   Scalars *sc;
 };
 
@@ -301,6 +301,8 @@ static size_t layout(int64_t n, int64_t n_elem, bool mixed, char *base, Work *w)
   t.pq_part = (double *)take((size_t)n_elem * sizeof(double));
   t.part1 = (double *)take(RED_MAX_BLOCKS * sizeof(double));
   t.part2 = (double *)take(RED_MAX_BLOCKS * sizeof(double));
+  t.fpart = (double *)take(3 * CGF_MAX_GRID * sizeof(double));
+  t.fsync = (unsigned *)take(4 * sizeof(unsigned));
   t.sc = (Scalars *)take(sizeof(Scalars));
   if (w) *w = t;
   return off;
@@ -347,10 +349,67 @@ static int pcg_iteration(ceed_mesh_t m, const ApplyReq &op, double *y, const Wor
   return CEED_OK;
 }
 
+// The fused iteration (cg_fused.cuh) covers the CG configuration of the paper's bake-off solves:
+// diffusion, GLL-collocated quadrature, one component, FP64 / FP32 / BF16 / on-the-fly-geometry /
+// double-float operators.  Other operators run the iteration as separate kernels (pcg_iteration).
+static bool fused_supported(ceed_mesh_t m, const ApplyReq &op) {
+  return op.op == CEED_OP_DIFFUSION && m->P == m->Q && op.ncol == 1 && m->n_colors <= CGF_MAX_COLORS &&
+         (op.prec == CEED_F64 || op.prec == CEED_F32 || op.prec == CEED_BF16 || op.prec == CEED_F32_GEO ||
+          op.prec == CEED_F64_DF);
+}
+
+// Up to `iters` PCG iterations in one fused launch (same device scalars and stopping rules as
+// pcg_iteration; fixed: no tolerance stop).
+static int fused_batch(ceed_mesh_t m, const ApplyReq &op, double *y, const Work &w, int64_t n, int iters, bool fixed,
+                       cudaStream_t s) {
+  CgFusedArgs g;
+  std::memset(&g, 0, sizeof(g));
+  const int qop = (op.prec == CEED_F32_GEO) ? OP_DIFF_GEO : CEED_OP_DIFFUSION;
+  g.a.emap = m->d_emap;
+  g.a.qdata = op.qdata;
+  g.a.x = w.p;
+  g.a.y = w.q;
+  g.a.ncol = 1;
+  g.a.masked = op.masked;
+  g.a.err = m->d_err + 1;
+  g.a.wait_limit = copy_wait_limit();
+  g.a.estride = qdata_estride(qop, prec_size(op.prec), m->Q);
+  for (int c = 0; c <= m->n_colors; ++c) g.cstart[c] = m->color_start[c];
+  g.ncolors = m->n_colors;
+  g.x = y;
+  g.r = w.r;
+  g.p = w.p;
+  g.q = w.q;
+  g.dinv = w.dinv;
+  g.n = n;
+  g.part = w.fpart;
+  g.sc = w.sc;
+  g.sync = w.fsync;
+  g.grid_wait = grid_wait_limit();
+  g.iters = iters;
+  g.fixed = fixed ? 1 : 0;
+  if (((uintptr_t)op.qdata & 15) != 0) return fail(CEED_ERR_INVALID, "qdata must be 16-byte aligned");
+  CEED_CUDA_CHECK(cudaMemsetAsync(w.fsync, 0, 4 * sizeof(unsigned), s));  // barrier state (a timeout leaves it dirty)
+  // elements per block: the apply variant chosen for this operator (autotuner or
+  // ceed_set_apply_variant), else blocks of about 128 threads
+  const int tuned = m->tuned[CEED_OP_DIFFUSION][op.prec].ne;
+  const int ne = tuned > 0 ? tuned : std::max(1, std::min(APPLY_MAX_NE, 128 / (m->Q * m->Q)));
+  unsigned grid = 0;
+  switch (op.prec) {
+    case CEED_F64: return launch_cg_fused_f64(m, g, ne, s, &grid);
+    case CEED_F64_DF: return launch_cg_fused_df(m, g, ne, s, &grid);
+    default: return launch_cg_fused_f32(m, op.prec, g, ne, s, &grid);
+  }
+}
+
 // Run PCG on A y = rhs (y starts at 0; rhs in w.r on entry), with the given operator.
 // Stops when ||r|| <= tol ||ref|| (ref = rhs), or after max_iter iterations, or exactly `fixed` iterations.
+// fused: whole iterations in the persistent kernel where the operator supports it.
 static int pcg_run(ceed_mesh_t m, const ApplyReq &op, double *y, const Work &w, int64_t n, double tol, int max_iter,
-                   int check_every, int fixed, cudaStream_t s, int *iters_out, int *nonfinite) {
+                   int check_every, int fixed, cudaStream_t s, int *iters_out, int *nonfinite, bool fused = true,
+                   int *fused_out = nullptr) {
+  fused = fused && fused_supported(m, op);
+  if (fused_out) *fused_out = fused ? 1 : 0;
   const int nb = red_blocks(n);
   Scalars h{};
   // tol2 and bb: bb comes from ||rhs||^2 (start_finalize with set_bb_from_rr)
@@ -364,11 +423,16 @@ static int pcg_run(ceed_mesh_t m, const ApplyReq &op, double *y, const Work &w, 
   int it = 0;
   while (it < cap) {
     const int batch = std::min(cap - it, fixed > 0 ? cap : check_every);
-    for (int b = 0; b < batch; ++b)
-      if (int st = pcg_iteration(m, op, y, w, n, fixed > 0, s)) return st;
+    if (fused) {
+      if (int st = fused_batch(m, op, y, w, n, batch, fixed > 0, s)) return st;
+    } else {
+      for (int b = 0; b < batch; ++b)
+        if (int st = pcg_iteration(m, op, y, w, n, fixed > 0, s)) return st;
+    }
     CEED_CUDA_CHECK(cudaGetLastError());
     it += batch;
     if (int st = read_scalars(&h, w.sc, s)) return st;
+    if (h.timeout) return fail(CEED_ERR_TIMEOUT, "a grid barrier of the fused CG iteration gave up");
     if (h.done) break;
   }
   if (fixed <= 0 || !h.done) {
@@ -406,7 +470,10 @@ static int residual(ceed_mesh_t m, const ApplyReq &op, const double *b, const do
 // iterations, true-residual evaluations.
 static int reliable_run(ceed_mesh_t m, const ApplyReq &hi, const ApplyReq &lo, const double *b, double *x,
                         const Work &w, int64_t n, double bb, double tol, double delta, int max_iter, int check_every,
-                        cudaStream_t s, int *iters_out, int *evals_out, double *rel_out, int *nonfinite) {
+                        cudaStream_t s, int *iters_out, int *evals_out, double *rel_out, int *nonfinite,
+                        bool fused = true, int *fused_out = nullptr) {
+  fused = fused && fused_supported(m, lo);
+  if (fused_out) *fused_out = fused ? 1 : 0;
   const int nb = red_blocks(n);
   *iters_out = 0;
   *evals_out = 1;
@@ -437,10 +504,15 @@ static int reliable_run(ceed_mesh_t m, const ApplyReq &hi, const ApplyReq &lo, c
   // bound only guards against a stuck state
   for (int batches = 0; it < max_iter && batches <= max_iter; ++batches) {
     const int batch = std::min(max_iter - it, check_every);
-    for (int k = 0; k < batch; ++k)
-      if (int st = pcg_iteration(m, lo, x, w, n, false, s)) return st;
+    if (fused) {
+      if (int st = fused_batch(m, lo, x, w, n, batch, false, s)) return st;
+    } else {
+      for (int k = 0; k < batch; ++k)
+        if (int st = pcg_iteration(m, lo, x, w, n, false, s)) return st;
+    }
     CEED_CUDA_CHECK(cudaGetLastError());
     if (int st = read_scalars(&h, w.sc, s)) return st;
+    if (h.timeout) return fail(CEED_ERR_TIMEOUT, "a grid barrier of the fused CG iteration gave up");
     it = h.iters;  // completed iterations since the start (replacements do not reset the count)
     if (h.nonfinite) {
       *nonfinite = 1;
@@ -834,12 +906,13 @@ extern "C" int ceed_cg_solve(ceed_mesh_t m, const void *qdata, int prec, const d
     oplo.prec = o.prec_lo;
     oplo.qdata = o.qdata_lo;
   }
+  const bool fused = (o.separate_kernels == 0);
   if (reliable && o.fixed_iters <= 0) {
     if (!o.use_x0) zero_kernel<<<stream_blocks(n), 256, 0, s>>>(x, n);
     int iters = 0, evals = 0, nonfin = 0;
     double rel = 0.0;
     if (int st = reliable_run(m, op64, oplo, b, x, w, n, bb, o.tol, o.reliable_delta, o.max_iter, o.check_every, s,
-                              &iters, &evals, &rel, &nonfin))
+                              &iters, &evals, &rel, &nonfin, fused, &report->fused))
       return st;
     report->iterations = iters;
     report->outer_iterations = evals;
@@ -850,7 +923,8 @@ extern "C" int ceed_cg_solve(ceed_mesh_t m, const void *qdata, int prec, const d
     // exactly fixed_iters PCG iterations from x0 = 0 with the FP64 operator (timing runs)
     copy_kernel<<<stream_blocks(n), 256, 0, s>>>(w.r, b, n);
     int iters = 0, nonfin = 0;
-    if (int st = pcg_run(m, op64, x, w, n, o.tol, o.max_iter, o.check_every, o.fixed_iters, s, &iters, &nonfin))
+    if (int st = pcg_run(m, op64, x, w, n, o.tol, o.max_iter, o.check_every, o.fixed_iters, s, &iters, &nonfin,
+                         fused, &report->fused))
       return st;
     report->iterations = iters;
     report->outer_iterations = 1;
@@ -886,7 +960,7 @@ extern "C" int ceed_cg_solve(ceed_mesh_t m, const void *qdata, int prec, const d
                              &nonfin))
           return st;
       } else if (int st = pcg_run(m, mixed ? oplo : op64, w.d, w, n, inner, o.max_iter - total, o.check_every, 0, s,
-                                  &iters, &nonfin)) {
+                                  &iters, &nonfin, fused, &report->fused)) {
         return st;
       }
       total += iters;

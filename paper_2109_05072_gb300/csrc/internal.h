@@ -79,6 +79,13 @@ constexpr long long WAIT_GRID_DEFAULT = 1LL << 25;
 int copy_wait_limit();
 long long grid_wait_limit();
 
+// Device-resident scalars of a CG run (the host reads them between batches of iterations).
+struct CgScalars {
+  double rz, rz_new, pq, alpha, beta, rr, bb, tol2;
+  double rr_out, bb_out;
+  int done, iters, nonfinite, timeout;  // timeout: a grid barrier of the fused iteration gave up
+};
+
 struct QRule {
   double x[MAX_Q];
   double w[MAX_Q];

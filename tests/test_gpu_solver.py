@@ -214,3 +214,57 @@ def test_adjoint_matches_oracle(ceed, p, stored):
     an = (kd.grad * v).sum().item()
     assert abs(fd - an) <= 1e-6 * abs(an)
     mesh.close()
+
+
+@pytest.mark.parametrize("mode,prec_lo", [(0, None), (1, 1), (2, 1), (2, 2), (2, 5)])
+def test_fused_iteration_matches_separate_kernels(ceed, mode, prec_lo):
+    """The fused persistent PCG iteration (one launch per batch of iterations) against the
+    separate-kernel iteration: same stopping rules, so the same iteration counts up to rounding-order
+    effects, both at 1e-10 on the true FP64 residual, solutions agreeing to the solve's accuracy."""
+    m, mesh, qd, b = _setup(ceed, 4, 4)
+    kw = dict(mode=mode, tol=1e-10, max_iter=4000, op=ceed.CEED_OP_DIFFUSION)
+    if prec_lo is not None:
+        ql = ceed.alloc_qdata(mesh, ceed.CEED_OP_DIFFUSION, prec_lo)
+        ceed.ceed_build_qdata(mesh, ceed.CEED_OP_DIFFUSION, ceed.CEED_COEFF_SINE, None, prec_lo, ql)
+        kw.update(qdata_lo=ql, prec_lo=prec_lo)
+    xf, xs = torch.empty_like(b), torch.empty_like(b)
+    st, rf = ceed.ceed_cg_solve(mesh, qd, ceed.CEED_F64, b, xf, **kw)
+    st, rs = ceed.ceed_cg_solve(mesh, qd, ceed.CEED_F64, b, xs, separate_kernels=1, **kw)
+    assert rf["fused"] == 1 and rs["fused"] == 0
+    assert rf["rel_residual"] <= 1e-10 and rs["rel_residual"] <= 1e-10
+    assert abs(rf["iterations"] - rs["iterations"]) <= max(2, rs["iterations"] // 50)
+    assert rel_err(xf.cpu().numpy(), xs.cpu().numpy()) <= 1e-8
+    # reproducible: the fused reductions have a fixed order
+    x2 = torch.empty_like(b)
+    st, r2 = ceed.ceed_cg_solve(mesh, qd, ceed.CEED_F64, b, x2, **kw)
+    assert torch.equal(x2, xf) and r2["iterations"] == rf["iterations"]
+    mesh.close()
+
+
+def test_fused_iteration_fixed_iterations(ceed):
+    # exactly 25 iterations, in batches of 10 launches (10, 10, 5), equal to the separate kernels'
+    # iterate up to rounding order
+    m, mesh, qd, b = _setup(ceed, 3, 5)
+    xf, xs = torch.empty_like(b), torch.empty_like(b)
+    _, rf = ceed.ceed_cg_solve(mesh, qd, ceed.CEED_F64, b, xf, mode=0, fixed_iters=25, op=ceed.CEED_OP_DIFFUSION)
+    _, rs = ceed.ceed_cg_solve(mesh, qd, ceed.CEED_F64, b, xs, mode=0, fixed_iters=25, op=ceed.CEED_OP_DIFFUSION,
+                               separate_kernels=1)
+    assert rf["iterations"] == rs["iterations"] == 25 and rf["fused"] == 1
+    assert rel_err(xf.cpu().numpy(), xs.cpu().numpy()) <= 1e-9
+    mesh.close()
+
+
+def test_fused_iteration_barrier_expiry(ceed):
+    # grid barriers of the fused iteration give up at once: TIMEOUT, no hang; then a normal solve
+    m, mesh, qd, b = _setup(ceed, 3, 3)
+    x = torch.empty_like(b)
+    ceed.ceed_set_wait_limits(-1, 0)
+    try:
+        st, rep = ceed.ceed_cg_solve(mesh, qd, ceed.CEED_F64, b, x, mode=0, tol=1e-10, op=ceed.CEED_OP_DIFFUSION,
+                                     raise_on_error=False)
+        assert st == ceed.CEED_ERR_TIMEOUT
+    finally:
+        ceed.ceed_set_wait_limits(-1, -1)
+    st, rep = ceed.ceed_cg_solve(mesh, qd, ceed.CEED_F64, b, x, mode=0, tol=1e-10, op=ceed.CEED_OP_DIFFUSION)
+    assert st == ceed.CEED_OK and rep["rel_residual"] <= 1e-10 and rep["fused"] == 1
+    mesh.close()
