@@ -54,6 +54,7 @@ WORKLOADS = {
     "c2a": dict(N=40, p=7),     # 22.19M DOFs: the DOF count quoted for the same workload
     "c4": dict(N=80, p=7),      # the mixed-precision CG workload
     "w48": dict(N=48, p=7),     # profiling size: one colour launch moves more than L2, a few GB on the device
+    "w32": dict(N=32, p=7),     # profiling size of the fused CG iteration (11.4M DOFs, about 2 GB on the device)
 }
 
 
@@ -235,6 +236,28 @@ def run_profile(args):
                       "colors": mesh.n_colors, "variant": args.variant}))
 
 
+def run_profile_cg(args):
+    """A short mixed-precision (FP32 operator, reliable updates) CG on the chosen workload: two fused
+    launches of 10 iterations each (for ncu captures of the fused PCG iteration kernel)."""
+    import torch
+    import paper_2109_05072_gb300 as ceed
+    wl = WORKLOADS[args.workload]
+    m = synthetic.cube_mesh(wl["N"], wl["p"], seed=0)
+    mesh = ceed.ceed_setup_mesh(m.n_elem, m.n_ldof, wl["p"], torch.from_numpy(m.elem_dofs).cuda(),
+                                torch.from_numpy(m.vertices).cuda(), torch.from_numpy(m.boundary).cuda())
+    q64 = ceed.alloc_qdata(mesh, ceed.CEED_OP_DIFFUSION, ceed.CEED_F64)
+    ceed.ceed_build_qdata(mesh, ceed.CEED_OP_DIFFUSION, ceed.CEED_COEFF_SINE, None, ceed.CEED_F64, q64)
+    q32 = ceed.alloc_qdata(mesh, ceed.CEED_OP_DIFFUSION, ceed.CEED_F32)
+    ceed.ceed_build_qdata(mesh, ceed.CEED_OP_DIFFUSION, ceed.CEED_COEFF_SINE, None, ceed.CEED_F32, q32)
+    b = torch.empty(m.n_ldof, dtype=torch.float64, device="cuda")
+    ceed.ceed_manufactured_rhs(mesh, ceed.CEED_COEFF_SINE, b, flags=ceed.CEED_APPLY_DIRICHLET)
+    x = torch.empty_like(b)
+    st, rep = ceed.ceed_cg_solve(mesh, q64, ceed.CEED_F64, b, x, mode=ceed.CEED_CG_MIXED_RELIABLE, tol=1e-10,
+                                 max_iter=20, op=ceed.CEED_OP_DIFFUSION, qdata_lo=q32, prec_lo=ceed.CEED_F32,
+                                 separate_kernels=args.cg_separate, raise_on_error=False)
+    print(json.dumps({"profile": "cg", "workload": args.workload, "n_ldof": m.n_ldof, "status": st, **rep}))
+
+
 def _time_cuda(fn, steps, warmup):
     import torch
     for _ in range(warmup):
@@ -256,7 +279,7 @@ def batched_model_flops(p, N):
     return N ** 3 * (24 * P ** 4 + 15 * Q ** 3)
 
 
-def run_batched(ceed, dev, args, peaks=None):
+def run_batched(ceed, dev, args, peaks=None, nrhs_list=(1, 4, 8, 16), steps=5):
     """Three independent meshes of order 3, 5, 7 (Gauss q = p+2: 5, 7, 9 points) on 48^3, 40^3, 32^3
     elements, 3-component diffusion, FP64, applied by one persistent launch replayed from a CUDA graph."""
     import torch
@@ -275,13 +298,13 @@ def run_batched(ceed, dev, args, peaks=None):
            "ncomp": 3, "dtype": "f64", "runs": [],
            "model": "per element and column 24 P^4 + 15 Q^3 flops (Section 2 model, contraction term doubled "
                     "for q = p + 2); fp64_frac against the measured FP64 FMA rate"}
-    for nrhs in (1, 4, 8, 16):
+    for nrhs in nrhs_list:
         xs = [torch.from_numpy(synthetic.uniform(n * 3 * nrhs, seed=7 + k)).to(dev) for k, n in enumerate(nodes)]
         ys = [torch.empty_like(x) for x in xs]
         batch = ceed.ceed_batch_create(meshes, qds, ceed.CEED_F64, ceed.CEED_OP_DIFFUSION, xs, ys, nrhs=nrhs)
         ceed.ceed_batch_autotune(batch)
         threads, stage, grid = ceed.ceed_batch_info(batch)
-        ms = _time_cuda(lambda: ceed.ceed_batch_apply(batch), 5, 3)
+        ms = _time_cuda(lambda: ceed.ceed_batch_apply(batch), steps, 3)
         ceed.ceed_batch_status(batch)
         dofs = sum(nodes) * 3 * nrhs
         flops = sum(batched_model_flops(p, N) for p, N in specs) * 3 * nrhs
@@ -517,8 +540,10 @@ def main():
     ap.add_argument("--cg-workload", default="c2", choices=sorted(WORKLOADS))
     ap.add_argument("--cpu-sample", type=int, default=40000, help="elements in the timed oracle sample")
     ap.add_argument("--ref-sample", type=int, default=1000, help="elements per reference-arm step")
-    ap.add_argument("--profile", default=None, choices=["f64", "f32", "bf16", "f64df"],
-                    help="profiling case: set up the workload, run three applies in this precision, exit")
+    ap.add_argument("--profile", default=None, choices=["f64", "f32", "bf16", "f64df", "cg", "batched"],
+                    help="profiling case: set up the workload, run three applies in this precision (or, with "
+                         "cg, 20 mixed-precision CG iterations), exit")
+    ap.add_argument("--cg-separate", type=int, default=0, help="--profile cg: one kernel per CG step (1) or fused (0)")
     ap.add_argument("--variant", default=None, help="ne,stage for --profile (default: autotune)")
     ap.add_argument("--autotune", type=int, default=1, help="autotune the apply kernel before timing")
     ap.add_argument("--batched", type=int, default=1, help="measure the batched mixed-order apply")
@@ -533,6 +558,14 @@ def main():
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.profile == "cg":
+        return run_profile_cg(args)
+    if args.profile == "batched":   # the persistent mixed-order launch, nrhs = 1 (for ncu captures)
+        import torch
+        import paper_2109_05072_gb300 as ceed
+        out = run_batched(ceed, torch.device("cuda", 0), args, nrhs_list=(1,), steps=1)
+        print(json.dumps({"profile": "batched", "runs": out["runs"]}))
+        return
     if args.profile:
         return run_profile(args)
     if args.nt_profile:

@@ -53,7 +53,10 @@ typedef enum {
  * F64_DF (mass and diffusion, either rule) -> an FP64-accurate operator computed on the FP32 pipe:
  * values and quadrature data carried as double-float pairs (hi + lo, about 48 bits) and every
  * contraction summed with a compensated dot product; agrees with the FP64 operator to ~1e-14
- * relative on well-conditioned inputs (FP64 L-vectors in and out, qdata 8 bytes per value). */
+ * relative on well-conditioned inputs (FP64 L-vectors in and out, qdata 8 bytes per value).  Each
+ * word must stay in the FP32 normal range: with the quadrature data of unit-cube meshes the 1e-12
+ * agreement holds for inputs of magnitude 1e-20 .. 1e30 (tested; at 1e-30 it fails); beyond that
+ * range the low words underflow (accuracy falls towards FP32) or the high words overflow (Inf). */
 typedef enum { CEED_F64 = 0, CEED_F32 = 1, CEED_BF16 = 2, CEED_F16 = 3, CEED_F32_GEO = 4, CEED_F64_DF = 5 } ceed_prec;
 
 /* Quadrature: GLL = collocated on the p+1 Gauss-Lobatto nodes (BP5 style, Q = p+1);
@@ -496,12 +499,13 @@ int ceed_dot_noalloc(const double *x, const double *y, int64_t n, double *out, v
  * (elements whose wait gave up write nothing).  CEED_OK otherwise. */
 int ceed_mesh_status(ceed_mesh_t mesh, void *stream);
 
-/* Iteration limits of the bounded device-side waits (not an operation of the paper; failure
- * handling): copy_polls bounds each apply kernel's wait for its quadrature-data copy, barrier_polls
- * the persistent batched launch's grid barrier between colours.  A wait that runs out records
- * CEED_ERR_TIMEOUT (read by ceed_mesh_status / ceed_batch_status) and the kernel finishes without
- * hanging.  A negative value restores the default (2^22 and 2^25 polls); 0 makes the wait give up
- * at once (a test uses this to drive the timeout path); values above the defaults are INVALID.
+/* Limits of the bounded device-side waits (not an operation of the paper; failure handling):
+ * copy_polls governs each apply kernel's wait for its quadrature-data copy (negative: the default
+ * bound of 2^22 polls; 0: give up at once; the kernels keep that bound a compile-time constant, so
+ * other values are INVALID), barrier_polls the grid barriers of the persistent batched launch and of
+ * the fused CG iteration (negative: the default 2^25 polls; 0 .. 2^25: that many polls).  A wait
+ * that runs out records CEED_ERR_TIMEOUT (read by ceed_mesh_status / ceed_batch_status, returned by
+ * ceed_cg_solve) and the kernel finishes without hanging; tests use 0 to drive these paths.
  * Process-wide; applies to launches issued afterwards (a batch's CUDA graph keeps the limits it was
  * captured with: re-create the batch or re-run ceed_batch_autotune to pick up new ones). */
 int ceed_set_wait_limits(int64_t copy_polls, int64_t barrier_polls);

@@ -474,8 +474,8 @@ extern "C" int ceed_mesh_info(ceed_mesh_t m, int32_t *n_colors, int32_t *Q, int3
 }
 
 extern "C" int ceed_set_wait_limits(int64_t copy_polls, int64_t barrier_polls) {
-  if (copy_polls > WAIT_COPY_DEFAULT || barrier_polls > WAIT_GRID_DEFAULT)
-    return fail(CEED_ERR_INVALID, "wait limits above the defaults are not accepted");
+  if (copy_polls > 0 || barrier_polls > WAIT_GRID_DEFAULT)
+    return fail(CEED_ERR_INVALID, "copy_polls must be negative (default) or 0; barrier_polls at most the default");
   g_copy_wait.store(copy_polls < 0 ? WAIT_COPY_DEFAULT : (int)copy_polls, std::memory_order_relaxed);
   g_grid_wait.store(barrier_polls < 0 ? WAIT_GRID_DEFAULT : (long long)barrier_polls, std::memory_order_relaxed);
   return CEED_OK;

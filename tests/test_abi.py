@@ -123,6 +123,7 @@ def test_wait_limits_validated_on_the_host():
     # limits above the defaults are refused before anything reaches a device; -1 restores them
     import paper_2109_05072_gb300 as ceed
     assert ceed._lib.ceed_set_wait_limits(1 << 23, -1) == ceed.CEED_ERR_INVALID
+    assert ceed._lib.ceed_set_wait_limits(5, -1) == ceed.CEED_ERR_INVALID
     assert ceed._lib.ceed_set_wait_limits(-1, 1 << 26) == ceed.CEED_ERR_INVALID
     assert ceed._lib.ceed_set_wait_limits(-1, -1) == ceed.CEED_OK
     assert ceed._lib.ceed_fma_throughput(3, None, None, None, None) == ceed.CEED_ERR_INVALID

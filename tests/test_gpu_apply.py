@@ -282,3 +282,22 @@ def test_host_buffer_apply(ceed, pinned):
         ceed.ceed_apply_host(mesh, ceed.CEED_OP_DIFFUSION, qd, ceed.CEED_F64, xh, yh, xd, xd, nrhs=nrhs)
     mesh.close()
 
+
+
+@pytest.mark.parametrize("scale", [1e-20, 1e-10, 1.0, 1e20, 1e30])
+def test_double_float_input_range(ceed, scale):
+    """The double-float operator carries each value as two FP32 words, so it holds the 1e-12 bar only
+    while every word stays in the FP32 normal range: inputs from 1e-20 to 1e30 with the quadrature data
+    of these meshes (the header states the range; at 1e-30 the low words of the products reach the
+    FP32 subnormals and the bar fails on the GB300).  The operator is linear: A (s x) = s (A x)."""
+    p = 5
+    m = synthetic.HexMesh(3, 3, 2, p, seed=81)
+    mesh = gpu_mesh(ceed, m, "gll")
+    qd = _qdata(ceed, mesh, "diffusion", ceed.CEED_F64_DF)
+    sp_, qref = oracle_qdata(m, "gll", "diffusion", "sine")
+    x = synthetic.uniform(m.n_ldof, seed=82)
+    ref = scale * fem.apply(sp_, m.elem_dofs, qref, x, fem.DIFFUSION)
+    y = _apply(ceed, mesh, "diffusion", qd, ceed.CEED_F64_DF, scale * x)
+    assert rel_err(y, ref) <= 1e-12
+    assert np.abs(y - ref).max() <= 1e-12 * np.abs(ref).max()
+    mesh.close()
