@@ -45,6 +45,8 @@ PROFILED_TRAFFIC_PER_LAUNCH = {
     "apply_kernel<8,8,DIFFUSION,double,double,stage=0>[ne=1]": 570.09e6 * 32768 / 13824,
     # same file: 503.84 MB read + 67.13 MB written per 13,824-element launch
     "apply_kernel<8,8,DIFFUSION,double,double,stage=0>[ne=2]": 570.97e6 * 32768 / 13824,
+    # profiles/df_apply_kernel_p7_48cube_ncu.md: 504.33 MB read + 68.59 MB written per 13,824-element launch
+    "apply_kernel<8,8,DIFFUSION,DF,DF,stage=0>[ne=4]": 572.92e6 * 32768 / 13824,
 }
 # DRAM bytes (read + write) of one launch of the tensor-core tetrahedral kernel on the 48^3 x 6
 # degree-4 workload (profiles/nt_tc_kernel_p4_tet48_ncu.md): 2143.84 MB read + 90.39 MB written
@@ -840,6 +842,9 @@ def main():
                          "peak_kind": "measured in this run: FP64 FMA chains on every SM (ceed_fma_throughput), "
                                       f"{peaks['f64']['sm_mhz']:.0f} MHz; nominal {FP64_NOMINAL_TFLOPS}",
                          "peak_nominal": FP64_NOMINAL_TFLOPS,
+                         "note": "achieved counts the paper's cost model (12 P^4 + 15 P^3 per element); the even-odd "
+                                 "1D operators execute about 0.8 of those flops, so frac reads above 1 while ncu "
+                                 "shows the FP64 pipe 85% busy",
                          "flops_per_launch": flops_launch, "ms_per_launch": ms_launch,
                          "hbm_gbs": bytes64 / (ms64 * 1e-3) / 1e9, "hbm_peak": hbm_peak, "hbm_peak_kind": hbm_kind,
                          "hbm_frac": bytes64 / (ms64 * 1e-3) / 1e9 / hbm_peak},
