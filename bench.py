@@ -281,29 +281,30 @@ def batched_model_flops(p, N):
     return N ** 3 * (24 * P ** 4 + 15 * Q ** 3)
 
 
-def run_batched(ceed, dev, args, peaks=None, nrhs_list=(1, 4, 8, 16), steps=5):
+def run_batched(ceed, dev, args, peaks=None, nrhs_list=(1, 4, 8, 16), steps=5, prec=None):
     """Three independent meshes of order 3, 5, 7 (Gauss q = p+2: 5, 7, 9 points) on 48^3, 40^3, 32^3
     elements, 3-component diffusion, FP64, applied by one persistent launch replayed from a CUDA graph."""
     import torch
+    prec = ceed.CEED_F64 if prec is None else prec
     specs = [(3, 48), (5, 40), (7, 32)]
     meshes, qds, nodes = [], [], []
     for p, N in specs:
         m = synthetic.cube_mesh(N, p, seed=0)
         mesh = ceed.ceed_setup_mesh(m.n_elem, m.n_ldof, p, torch.from_numpy(m.elem_dofs).to(dev),
                                     torch.from_numpy(m.vertices).to(dev), None, q_rule=ceed.CEED_QRULE_GAUSS, ncomp=3)
-        qd = ceed.alloc_qdata(mesh, ceed.CEED_OP_DIFFUSION, ceed.CEED_F64, dev)
-        ceed.ceed_build_qdata(mesh, ceed.CEED_OP_DIFFUSION, ceed.CEED_COEFF_SINE, None, ceed.CEED_F64, qd)
+        qd = ceed.alloc_qdata(mesh, ceed.CEED_OP_DIFFUSION, prec, dev)
+        ceed.ceed_build_qdata(mesh, ceed.CEED_OP_DIFFUSION, ceed.CEED_COEFF_SINE, None, prec, qd)
         meshes.append(mesh)
         qds.append(qd)
         nodes.append(m.n_ldof)
     out = {"meshes": [f"p={p}, {N}^3, Gauss q={p + 2}, n_ldof={n}" for (p, N), n in zip(specs, nodes)],
-           "ncomp": 3, "dtype": "f64", "runs": [],
+           "ncomp": 3, "dtype": "f64" if prec == ceed.CEED_F64 else "f32x2 (double-float, FP64-accurate)", "runs": [],
            "model": "per element and column 24 P^4 + 15 Q^3 flops (Section 2 model, contraction term doubled "
                     "for q = p + 2); fp64_frac against the measured FP64 FMA rate"}
     for nrhs in nrhs_list:
         xs = [torch.from_numpy(synthetic.uniform(n * 3 * nrhs, seed=7 + k)).to(dev) for k, n in enumerate(nodes)]
         ys = [torch.empty_like(x) for x in xs]
-        batch = ceed.ceed_batch_create(meshes, qds, ceed.CEED_F64, ceed.CEED_OP_DIFFUSION, xs, ys, nrhs=nrhs)
+        batch = ceed.ceed_batch_create(meshes, qds, prec, ceed.CEED_OP_DIFFUSION, xs, ys, nrhs=nrhs)
         ceed.ceed_batch_autotune(batch)
         threads, stage, grid = ceed.ceed_batch_info(batch)
         ms = _time_cuda(lambda: ceed.ceed_batch_apply(batch), steps, 3)
@@ -312,7 +313,7 @@ def run_batched(ceed, dev, args, peaks=None, nrhs_list=(1, 4, 8, 16), steps=5):
         flops = sum(batched_model_flops(p, N) for p, N in specs) * 3 * nrhs
         row = {"nrhs": nrhs, "ms_per_apply": ms, "gdofs": dofs / ms / 1e6, "threads": threads,
                "tma_staging": stage, "grid": grid, "launches_per_apply": 1, "model_tflops": flops / ms / 1e9}
-        if peaks and peaks.get("f64"):
+        if peaks and peaks.get("f64") and prec == ceed.CEED_F64:
             row["fp64_frac"] = row["model_tflops"] / peaks["f64"]["tflops"]
         out["runs"].append(row)
         batch.close()
@@ -526,6 +527,8 @@ def compact_summary(line):
     if b:
         out["batched_gdofs_by_nrhs"] = {str(x["nrhs"]): r(x["gdofs"]) for x in b["runs"]}
         out["batched_fp64_frac_by_nrhs"] = {str(x["nrhs"]): r(x.get("fp64_frac")) for x in b["runs"]}
+        if b.get("fp64_accurate_fp32_pipe"):
+            out["batched_df_gdofs_by_nrhs"] = {str(x["nrhs"]): r(x["gdofs"]) for x in b["fp64_accurate_fp32_pipe"]}
     pk = line.get("peaks_measured") or {}
     out["peak_tflops"] = {k: r(v["tflops"]) for k, v in pk.items()}
     return out
@@ -794,6 +797,9 @@ def main():
     batched = None
     if args.batched:
         batched = run_batched(ceed, dev, args, peaks)
+        # the same batches with the FP64-accurate double-float operator
+        batched["fp64_accurate_fp32_pipe"] = run_batched(ceed, dev, args, peaks, nrhs_list=(1, 4, 16),
+                                                         prec=ceed.CEED_F64_DF)["runs"]
 
     # ---------------- adjoint: L = 0.5 ||A(k) x - b||^2, p = 4 and 8 on 32^3, geometry stored vs recomputed
     adjoint = None

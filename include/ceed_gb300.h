@@ -182,7 +182,8 @@ int ceed_manufactured_rhs(ceed_mesh_t mesh, int coeff_kind, double *b, unsigned 
  * atomic-free scatter needs colours in sequence).  The launch is captured once into a CUDA graph and
  * replayed by ceed_batch_apply.  Buffers are fixed at creation: qdata[k] (built for meshes[k] in
  * `prec`), x[k], y[k] (FP64, [n_ldof * ncomp * nrhs] of mesh k).  All meshes must use the same
- * quadrature rule kind (GLL or Gauss).  Supported: F64 mass/diffusion, F32 diffusion.  The batch must
+ * quadrature rule kind (GLL or Gauss).  Supported: F64 and F64_DF (the FP64-accurate double-float
+ * operator) mass/diffusion, F32 diffusion.  The batch must
  * not run concurrently with other kernels on the device (the persistent grid assumes it has the GPU);
  * if a barrier wait times out, ceed_batch_status returns CEED_ERR_TIMEOUT. */
 typedef struct ceed_batch_s *ceed_batch_t;

@@ -10,6 +10,8 @@ int launch_batch_f64(int op, int n, ceed_mesh_t const *meshes, const ApplyReq *r
                      const BatchLaunch &L, cudaStream_t s, unsigned *grid);
 int launch_batch_f32(int op, int n, ceed_mesh_t const *meshes, const ApplyReq *reqs, unsigned *sync, int *err,
                      const BatchLaunch &L, cudaStream_t s, unsigned *grid);
+int launch_batch_df(int op, int n, ceed_mesh_t const *meshes, const ApplyReq *reqs, unsigned *sync, int *err,
+                    const BatchLaunch &L, cudaStream_t s, unsigned *grid);
 }  // namespace ceedgb
 
 using namespace ceedgb;
@@ -28,6 +30,8 @@ struct ceed_batch_s {
 
 static int batch_launch_direct(ceed_batch_s *b, cudaStream_t s) {
   if (b->prec == CEED_F64) return launch_batch_f64(b->op, b->n, b->meshes, b->reqs, b->d_sync, b->d_err, b->L, s, &b->grid);
+  if (b->prec == CEED_F64_DF)
+    return launch_batch_df(b->op, b->n, b->meshes, b->reqs, b->d_sync, b->d_err, b->L, s, &b->grid);
   return launch_batch_f32(b->op, b->n, b->meshes, b->reqs, b->d_sync, b->d_err, b->L, s, &b->grid);
 }
 
@@ -70,8 +74,8 @@ extern "C" int ceed_batch_create(int n, const ceed_mesh_t *meshes, const void *c
   if (n < 1 || n > 4) return fail(CEED_ERR_INVALID, "a batch holds 1..4 meshes");
   if (nrhs < 1) return fail(CEED_ERR_INVALID, "nrhs must be >= 1");
   if (op != CEED_OP_MASS && op != CEED_OP_DIFFUSION) return fail(CEED_ERR_INVALID, "unknown operator");
-  if (prec != CEED_F64 && !(prec == CEED_F32 && op == CEED_OP_DIFFUSION))
-    return fail(CEED_ERR_UNSUPPORTED, "batches support FP64 mass/diffusion and FP32 diffusion");
+  if (prec != CEED_F64 && prec != CEED_F64_DF && !(prec == CEED_F32 && op == CEED_OP_DIFFUSION))
+    return fail(CEED_ERR_UNSUPPORTED, "batches support FP64 and double-float mass/diffusion, and FP32 diffusion");
   ceed_batch_s *b = new (std::nothrow) ceed_batch_s();
   if (!b) return fail(CEED_ERR_OOM, "host allocation");
   b->n = n;

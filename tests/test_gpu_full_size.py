@@ -146,23 +146,30 @@ def batched_meshes(ceed):
         mesh.close()
 
 
-@pytest.mark.parametrize("nrhs", [4, 8, 16])
-def test_batched_mixed_order_sampled(ceed, batched_meshes, nrhs):
+@pytest.mark.parametrize("nrhs,prec", [(4, 0), (8, 0), (16, 0), (4, 5)])
+def test_batched_mixed_order_sampled(ceed, batched_meshes, nrhs, prec):
     """Every right-hand-side count bench.py times except 1 (covered by the single-mesh tests);
-    nrhs = 16 is 48 interleaved columns per node (x and y: 17 GB on the device)."""
+    nrhs = 16 is 48 interleaved columns per node (x and y: 17 GB on the device); prec 5 is the
+    double-float FP64-accurate operator in the same persistent launch."""
     specs, ncomp, ms, meshes, qds = batched_meshes
+    if prec != 0:
+        qds = []
+        for mesh in meshes:
+            qd = ceed.alloc_qdata(mesh, ceed.CEED_OP_DIFFUSION, prec)
+            ceed.ceed_build_qdata(mesh, ceed.CEED_OP_DIFFUSION, ceed.CEED_COEFF_SINE, None, prec, qd)
+            qds.append(qd)
     xs_host, xs, ys = [], [], []
     for k, m in enumerate(ms):
         xh = synthetic.uniform(m.n_ldof * ncomp * nrhs, seed=7 + k)
         xs_host.append(xh)
         xs.append(torch.from_numpy(xh).cuda())
         ys.append(torch.full_like(xs[-1], float("nan")))
-    batch = ceed.ceed_batch_create(meshes, qds, ceed.CEED_F64, ceed.CEED_OP_DIFFUSION, xs, ys, nrhs=nrhs)
+    batch = ceed.ceed_batch_create(meshes, qds, prec, ceed.CEED_OP_DIFFUSION, xs, ys, nrhs=nrhs)
     ceed.ceed_batch_autotune(batch)                      # the launch shape bench.py times
     ceed.ceed_batch_apply(batch)
     ceed.ceed_batch_status(batch)
     for k, ((p, N), m) in enumerate(zip(specs, ms)):
-        nodes = _sample_nodes(np.random.default_rng(200 + k + nrhs), N, p, n_each=12)
+        nodes = _sample_nodes(np.random.default_rng(200 + k + nrhs + prec), N, p, n_each=12)
         X = xs_host[k].reshape(m.n_ldof, ncomp * nrhs)   # [node][component][rhs], A acts on each column
         node_id, ref, counts = _sampled_action(m, N, p, nodes, X, _SineQdata(m, p, "gauss"))
         assert set(counts.tolist()) >= {1, 2, 8}
