@@ -465,6 +465,48 @@ __device__ __forceinline__ void apply_block(const ApplyArgs &a, const OpTab<T> &
           c3[c] = a3 + a5 * xr + a6 * xs + a7 * xr * xs;
         }
       }
+      // double-float with an even number of points per column: points k and k + 1 share the two
+      // lanes of the packed instructions (the same steps as dot3<DF>, lane by lane: bit-identical)
+      constexpr bool PAIRED = std::is_same<T, DF>::value && OP == CEED_OP_DIFFUSION && (Q % 2 == 0);
+      if constexpr (PAIRED) {
+#pragma unroll
+        for (int k = 0; k < Q; k += 2) {
+          const int q0 = (k * Q + j) * Q + i, q1 = q0 + Q * Q;
+          DF g0[6], g1[6];
+#pragma unroll
+          for (int c = 0; c < 6; ++c) {
+            g0[c] = q_to(sq[c * NQ + q0], T());
+            g1[c] = q_to(sq[c * NQ + q1], T());
+          }
+          const DF ur0 = sb[tix<Q>(k, j, i)], ur1 = sb[tix<Q>(k + 1, j, i)];
+          const DF us0 = sc[tix<Q>(k, j, i)], us1 = sc[tix<Q>(k + 1, j, i)];
+          const float2 urh = make_float2(ur0.hi, ur1.hi), url = make_float2(ur0.lo, ur1.lo);
+          const float2 ush = make_float2(us0.hi, us1.hi), usl = make_float2(us0.lo, us1.lo);
+          const float2 uth = make_float2(ut[k].hi, ut[k + 1].hi), utl = make_float2(ut[k].lo, ut[k + 1].lo);
+          float2 gh[6], gl[6];
+#pragma unroll
+          for (int c = 0; c < 6; ++c) {
+            gh[c] = make_float2(g0[c].hi, g1[c].hi);
+            gl[c] = make_float2(g0[c].lo, g1[c].lo);
+          }
+          // components rr 0, rs 1, rt 2, ss 3, st 4, tt 5
+          DFAcc2 A = acc2_first(gh[0], gl[0], urh, url);
+          acc2_mac(A, gh[1], gl[1], ush, usl);
+          acc2_mac(A, gh[2], gl[2], uth, utl);
+          DFAcc2 B = acc2_first(gh[1], gl[1], urh, url);
+          acc2_mac(B, gh[3], gl[3], ush, usl);
+          acc2_mac(B, gh[4], gl[4], uth, utl);
+          DFAcc2 C = acc2_first(gh[2], gl[2], urh, url);
+          acc2_mac(C, gh[4], gl[4], ush, usl);
+          acc2_mac(C, gh[5], gl[5], uth, utl);
+          sb[tix<Q>(k, j, i)] = DF(A.s.x, A.c.x);
+          sb[tix<Q>(k + 1, j, i)] = DF(A.s.y, A.c.y);
+          sc[tix<Q>(k, j, i)] = DF(B.s.x, B.c.x);
+          sc[tix<Q>(k + 1, j, i)] = DF(B.s.y, B.c.y);
+          vt[k] = DF(C.s.x, C.c.x);
+          vt[k + 1] = DF(C.s.y, C.c.y);
+        }
+      } else {
 #pragma unroll
       for (int k = 0; k < Q; ++k) {
         const int q = (k * Q + j) * Q + i;
@@ -501,6 +543,7 @@ __device__ __forceinline__ void apply_block(const ApplyArgs &a, const OpTab<T> &
         sc[tix<Q>(k, j, i)] = dot3(grs, ur, gss, us, gst, ut[k]);
         vt[k] = dot3(grt, ur, gst, us, gtt, ut[k]);
       }
+      }  // PAIRED
       __syncthreads();
       {  // r transposed: owners (s = i, t = j)
         T v[Q], g[Q];
@@ -521,8 +564,22 @@ __device__ __forceinline__ void apply_block(const ApplyArgs &a, const OpTab<T> &
       T yt[Q];
       eo_apply<Q, Q, -1>(tab.eDT, vt, yt);
       __syncthreads();
+      if constexpr (PAIRED) {
 #pragma unroll
-      for (int k = 0; k < Q; ++k) w[k] = add3(yt[k], sa[tix<Q>(k, j, i)], sc[tix<Q>(k, j, i)]);
+        for (int k = 0; k < Q; k += 2) {  // add3 on points k and k + 1 together
+          const DF a0 = sa[tix<Q>(k, j, i)], a1 = sa[tix<Q>(k + 1, j, i)];
+          const DF c0 = sc[tix<Q>(k, j, i)], c1 = sc[tix<Q>(k + 1, j, i)];
+          float2 h, l;
+          df2_add(make_float2(yt[k].hi, yt[k + 1].hi), make_float2(yt[k].lo, yt[k + 1].lo),
+                  make_float2(a0.hi, a1.hi), make_float2(a0.lo, a1.lo), h, l);
+          df2_add(h, l, make_float2(c0.hi, c1.hi), make_float2(c0.lo, c1.lo), h, l);
+          w[k] = DF(h.x, l.x);
+          w[k + 1] = DF(h.y, l.y);
+        }
+      } else {
+#pragma unroll
+        for (int k = 0; k < Q; ++k) w[k] = add3(yt[k], sa[tix<Q>(k, j, i)], sc[tix<Q>(k, j, i)]);
+      }
     }
 
     // ---- transposed interpolation back to the nodes

@@ -869,9 +869,17 @@ extern "C" int ceed_cg_solve(ceed_mesh_t m, const void *qdata, int prec, const d
   cudaStream_t s = (cudaStream_t)stream;
   std::memset(report, 0, sizeof(*report));
 
-  cudaEvent_t ev0, ev1;
-  CEED_CUDA_CHECK(cudaEventCreate(&ev0));
-  CEED_CUDA_CHECK(cudaEventCreate(&ev1));
+  // the two timing events are released on every return path
+  struct Events {
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    ~Events() {
+      if (e0) cudaEventDestroy(e0);
+      if (e1) cudaEventDestroy(e1);
+    }
+  } ev;
+  CEED_CUDA_CHECK(cudaEventCreate(&ev.e0));
+  CEED_CUDA_CHECK(cudaEventCreate(&ev.e1));
+  cudaEvent_t ev0 = ev.e0, ev1 = ev.e1;
   CEED_CUDA_CHECK(cudaEventRecord(ev0, s));
 
   ApplyReq op64{};
@@ -979,8 +987,6 @@ extern "C" int ceed_cg_solve(ceed_mesh_t m, const void *qdata, int prec, const d
   float ms = 0.f;
   cudaEventElapsedTime(&ms, ev0, ev1);
   report->seconds = ms * 1e-3;
-  cudaEventDestroy(ev0);
-  cudaEventDestroy(ev1);
   return status;
 }
 

@@ -125,6 +125,15 @@ __device__ __forceinline__ void acc2_mac(DFAcc2 &A, float2 mh, float2 ml, float2
   A.c = add2(A.c, add2(q, e));
 }
 
+// df_add on two values at once: (ah, al) and (bh, bl) hold the lanes' high and low words.
+__device__ __forceinline__ void df2_add(float2 ah, float2 al, float2 bh, float2 bl, float2 &sh, float2 &sl) {
+  const float2 s = add2(ah, bh);  // TwoSum(ah, bh), lane by lane
+  const float2 z = sub2(s, ah);
+  const float2 e = add2(sub2(ah, sub2(s, z)), sub2(bh, z));
+  sh = s;
+  sl = add2(e, add2(al, bl));
+}
+
 // Host/device split of a double into the nearest float and the float nearest to the remainder.
 __host__ __device__ inline DF df_from_double(double v) {
   const float h = (float)v;

@@ -216,7 +216,7 @@ def test_adjoint_matches_oracle(ceed, p, stored):
     mesh.close()
 
 
-@pytest.mark.parametrize("mode,prec_lo", [(0, None), (1, 1), (2, 1), (2, 2), (2, 5)])
+@pytest.mark.parametrize("mode,prec_lo", [(0, None), (1, 1), (2, 1), (2, 2), (2, 4), (2, 5)])
 def test_fused_iteration_matches_separate_kernels(ceed, mode, prec_lo):
     """The fused persistent PCG iteration (one launch per batch of iterations) against the
     separate-kernel iteration: same stopping rules, so the same iteration counts up to rounding-order
