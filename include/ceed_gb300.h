@@ -113,6 +113,14 @@ int ceed_destroy_mesh(ceed_mesh_t mesh);
 /* Mesh facts: number of colours, points per direction Q, nodes per direction P. */
 int ceed_mesh_info(ceed_mesh_t mesh, int32_t *n_colors, int32_t *Q, int32_t *P);
 
+/* Bricks found at setup (Section 2's gather and scatter grouped over neighbouring elements): the
+ * number of 2 x 2 x 1 element groups of a structured lattice -- node numbering x fastest, every
+ * element's nodes at base + a + b sy + c sz with common strides, even element counts per direction
+ * -- or 0 when the mesh is not such a lattice.  On a brick mesh the FP32-pipe operators (F32, BF16,
+ * F16, F32_GEO) with one column may run the brick kernel (apply variant stages 2 and 3), which reads
+ * every node of a brick once instead of once per element that contains it. */
+int ceed_mesh_bricks(ceed_mesh_t mesh, int64_t *n_bricks);
+
 /* Bytes of quadrature data for (op, prec): mass 1 value per point, diffusion 6 (the
  * symmetric G_rr, G_rs, G_rt, G_ss, G_st, G_tt of Section 2).  Layout is internal:
  * [colour-sorted element][component][Q^3]. */
@@ -150,15 +158,22 @@ int ceed_apply_host(ceed_mesh_t mesh, int op, const void *qdata, int prec, const
 /* Autotuner (the batched-apply design calls for tile shape and elements per block chosen by
  * measurement): runs every variant of the fused apply kernel -- elements per thread block
  * (1, 2, 4, ... up to 256 threads and 32 elements) x quadrature-data staging (TMA bulk copy into shared memory,
- * or direct loads) -- on the caller's qdata, x and y (y is overwritten), times each with CUDA
+ * or direct loads), and the brick kernel with and without staging where the mesh and precision
+ * allow it (ceed_set_apply_variant) -- on the caller's qdata, x and y (y is overwritten), times each with CUDA
  * events on `stream`, and keeps the fastest in the handle for (op, prec); later applies use it.
  * Returns the choice and its time per application.  Synchronizes `stream`. */
 int ceed_autotune_apply(ceed_mesh_t mesh, int op, const void *qdata, int prec, const double *x, double *y,
                         int nrhs, int32_t *best_ne, int32_t *best_stage, float *best_ms, void *stream);
 
 /* Fix the apply variant for (op, prec) by hand: ne elements per thread block (0 restores the
- * default), stage = 1 for TMA staging of quadrature data, 0 for direct loads.  INVALID if ne
- * exceeds min(32, 256 / Q^2).  Results do not depend on the variant (same arithmetic order). */
+ * default), stage = 1 for TMA staging of quadrature data, 0 for direct loads; stage = 2 (direct
+ * loads) or 3 (staging) selects the brick kernel, one 2 x 2 x 1 element group per thread block (ne
+ * is then ignored), for the FP32-pipe precisions on meshes with bricks (ceed_mesh_bricks).  INVALID
+ * if ne exceeds min(32, 256 / Q^2), or for a brick stage the mesh or precision cannot use.  The
+ * element variants (stages 0, 1) give bitwise-identical results; the brick variants add the
+ * contributions to a shared node in another order (the brick's elements first), so they agree
+ * with them to FP32 rounding, deterministically.  A brick choice applies to single-column applies;
+ * several columns run the default element variant. */
 int ceed_set_apply_variant(ceed_mesh_t mesh, int op, int prec, int ne, int stage);
 
 /* Jacobi diagonal of the operator (the cheap preconditioner for CG, Section 1), FP64

@@ -85,6 +85,7 @@ def _load():
         "ceed_destroy_mesh": (ctypes.c_int, [vp]),
         "ceed_mesh_node_coords": (ctypes.c_int, [vp, vp, vp]),
         "ceed_mesh_info": (ctypes.c_int, [vp, ctypes.POINTER(i32), ctypes.POINTER(i32), ctypes.POINTER(i32)]),
+        "ceed_mesh_bricks": (ctypes.c_int, [vp, ctypes.POINTER(i64)]),
         "ceed_qdata_bytes": (sz, [vp, ctypes.c_int, ctypes.c_int]),
         "ceed_build_qdata": (ctypes.c_int, [vp, ctypes.c_int, ctypes.c_int, vp, ctypes.c_int, vp, vp]),
         "ceed_apply_mass": (ctypes.c_int, [vp, vp, ctypes.c_int, vp, vp, ctypes.c_int, u32, vp]),
@@ -234,6 +235,13 @@ def ceed_mesh_info(mesh: Mesh):
     nc, Q, P = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
     _check(_lib.ceed_mesh_info(mesh.handle, ctypes.byref(nc), ctypes.byref(Q), ctypes.byref(P)))
     return nc.value, Q.value, P.value
+
+
+def ceed_mesh_bricks(mesh: Mesh) -> int:
+    """Number of 2 x 2 x 2 element bricks found at setup (0: the mesh is not a brick lattice)."""
+    n = ctypes.c_int64()
+    _check(_lib.ceed_mesh_bricks(mesh.handle, ctypes.byref(n)))
+    return n.value
 
 
 def ceed_mesh_node_coords(mesh: Mesh, coords: torch.Tensor, stream=None):

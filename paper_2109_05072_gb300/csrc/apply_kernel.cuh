@@ -274,6 +274,257 @@ __device__ __forceinline__ int tix(int t, int s, int r) {
   return (t * Q + s) * (Q + 1) + r;
 }
 
+// The element's operator from its node values u (one column of P nodes per node thread) to its
+// node results yv, through the quadrature points: interpolation (Gauss) or identity (collocated),
+// the derivative passes, the pointwise quadrature operator, the transposed passes.  Every thread of
+// the element takes part (the passes use block barriers); wait_q() runs before the first read of the
+// quadrature data sq.  Shared with the one-element-per-block-share kernel below and with the brick
+// kernel (brick.cuh).
+template <int P, int Q, int OP, typename T, typename TQ, typename WaitQ>
+__device__ __forceinline__ void element_op(const OpTab<T> &tab, const T (&u)[P], T (&yv)[P], const TQ *sq, T *sa,
+                                           T *sb, T *sc, int i, int j, bool node_thread, bool active,
+                                           WaitQ &wait_q) {
+  constexpr bool COLLOC = (P == Q);
+  constexpr int NQ = Q * Q * Q;
+  // ---- interpolate to the quadrature points (identity when collocated)
+  T uq[Q];
+  if constexpr (COLLOC) {
+#pragma unroll
+    for (int k = 0; k < Q; ++k) uq[k] = u[k];
+  } else {
+    if (node_thread) {  // t: column owners (r = i, s = j) hold the line in registers
+      T w[Q];
+      eo_apply<Q, P, 1>(tab.eB, u, w);
+#pragma unroll
+      for (int k = 0; k < Q; ++k) sa[tix<Q>(k, j, i)] = w[k];
+    }
+    __syncthreads();
+    if (i < P) {        // s: owners (r = i, t = j)
+      T v[P], w[Q];
+#pragma unroll
+      for (int m = 0; m < P; ++m) v[m] = sa[tix<Q>(j, m, i)];
+      eo_apply<Q, P, 1>(tab.eB, v, w);
+#pragma unroll
+      for (int n = 0; n < Q; ++n) sb[tix<Q>(j, n, i)] = w[n];
+    }
+    __syncthreads();
+    {                   // r: owners (s = i, t = j)
+      T v[P], w[Q];
+#pragma unroll
+      for (int m = 0; m < P; ++m) v[m] = sb[tix<Q>(j, i, m)];
+      eo_apply<Q, P, 1>(tab.eB, v, w);
+#pragma unroll
+      for (int n = 0; n < Q; ++n) sa[tix<Q>(j, i, n)] = w[n];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < Q; ++k) uq[k] = sa[tix<Q>(k, j, i)];
+  }
+
+  // ---- quadrature-point operator
+  T w[Q];
+  wait_q();  // quadrature data in place (staged copies: bounded wait)
+  if constexpr (OP == CEED_OP_MASS) {
+#pragma unroll
+    for (int k = 0; k < Q; ++k) w[k] = active ? qmul(q_to(sq[(k * Q + j) * Q + i], T()), uq[k]) : (T)0;
+  } else {
+    T ut[Q];
+    eo_apply<Q, Q, -1>(tab.eD, uq, ut);
+    if constexpr (COLLOC) {
+#pragma unroll
+      for (int k = 0; k < Q; ++k) sa[tix<Q>(k, j, i)] = uq[k];
+      __syncthreads();
+    }  // non-collocated: sa already holds uq at these positions
+    {  // r: owners (s = i, t = j)
+      T v[Q], g[Q];
+#pragma unroll
+      for (int m = 0; m < Q; ++m) v[m] = sa[tix<Q>(j, i, m)];
+      eo_apply<Q, Q, -1>(tab.eD, v, g);
+#pragma unroll
+      for (int n = 0; n < Q; ++n) sb[tix<Q>(j, i, n)] = g[n];
+    }
+    {  // s: owners (r = i, t = j)
+      T v[Q], g[Q];
+#pragma unroll
+      for (int m = 0; m < Q; ++m) v[m] = sa[tix<Q>(j, m, i)];
+      eo_apply<Q, Q, -1>(tab.eD, v, g);
+#pragma unroll
+      for (int n = 0; n < Q; ++n) sc[tix<Q>(j, n, i)] = g[n];
+    }
+    __syncthreads();
+    // pointwise v = G grad u at my column, in place
+    T vt[Q];
+    // on-the-fly geometry: the trilinear map x = a0 + a1 r + a2 s + a3 t + a4 rs + a5 rt + a6 st + a7 rst
+    // gives dx/dr = (a1 + a4 s) + (a5 + a7 s) t, dx/ds = (a2 + a4 r) + (a6 + a7 r) t and
+    // dx/dt = a3 + a5 r + a6 s + a7 rs, so along my column only t varies: 6 FMAs per point for J
+    T c1[3], c1t[3], c2[3], c2t[3], c3[3];
+    if constexpr (OP == OP_DIFF_GEO) {
+      const T xr = tab.qx[i], xs = tab.qx[j];
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        const T a1 = q_to(sq[c], T()), a2 = q_to(sq[3 + c], T()), a3 = q_to(sq[6 + c], T());
+        const T a4 = q_to(sq[9 + c], T()), a5 = q_to(sq[12 + c], T()), a6 = q_to(sq[15 + c], T());
+        const T a7 = q_to(sq[18 + c], T());
+        c1[c] = a1 + a4 * xs;
+        c1t[c] = a5 + a7 * xs;
+        c2[c] = a2 + a4 * xr;
+        c2t[c] = a6 + a7 * xr;
+        c3[c] = a3 + a5 * xr + a6 * xs + a7 * xr * xs;
+      }
+    }
+    // double-float with an even number of points per column: points k and k + 1 share the two
+    // lanes of the packed instructions (the same steps as dot3<DF>, lane by lane: bit-identical)
+    constexpr bool PAIRED = std::is_same<T, DF>::value && OP == CEED_OP_DIFFUSION && (Q % 2 == 0);
+    if constexpr (PAIRED) {
+#pragma unroll
+      for (int k = 0; k < Q; k += 2) {
+        const int q0 = (k * Q + j) * Q + i, q1 = q0 + Q * Q;
+        DF g0[6], g1[6];
+#pragma unroll
+        for (int c = 0; c < 6; ++c) {
+          g0[c] = q_to(sq[c * NQ + q0], T());
+          g1[c] = q_to(sq[c * NQ + q1], T());
+        }
+        const DF ur0 = sb[tix<Q>(k, j, i)], ur1 = sb[tix<Q>(k + 1, j, i)];
+        const DF us0 = sc[tix<Q>(k, j, i)], us1 = sc[tix<Q>(k + 1, j, i)];
+        const float2 urh = make_float2(ur0.hi, ur1.hi), url = make_float2(ur0.lo, ur1.lo);
+        const float2 ush = make_float2(us0.hi, us1.hi), usl = make_float2(us0.lo, us1.lo);
+        const float2 uth = make_float2(ut[k].hi, ut[k + 1].hi), utl = make_float2(ut[k].lo, ut[k + 1].lo);
+        float2 gh[6], gl[6];
+#pragma unroll
+        for (int c = 0; c < 6; ++c) {
+          gh[c] = make_float2(g0[c].hi, g1[c].hi);
+          gl[c] = make_float2(g0[c].lo, g1[c].lo);
+        }
+        // components rr 0, rs 1, rt 2, ss 3, st 4, tt 5
+        DFAcc2 A = acc2_first(gh[0], gl[0], urh, url);
+        acc2_mac(A, gh[1], gl[1], ush, usl);
+        acc2_mac(A, gh[2], gl[2], uth, utl);
+        DFAcc2 B = acc2_first(gh[1], gl[1], urh, url);
+        acc2_mac(B, gh[3], gl[3], ush, usl);
+        acc2_mac(B, gh[4], gl[4], uth, utl);
+        DFAcc2 C = acc2_first(gh[2], gl[2], urh, url);
+        acc2_mac(C, gh[4], gl[4], ush, usl);
+        acc2_mac(C, gh[5], gl[5], uth, utl);
+        sb[tix<Q>(k, j, i)] = DF(A.s.x, A.c.x);
+        sb[tix<Q>(k + 1, j, i)] = DF(A.s.y, A.c.y);
+        sc[tix<Q>(k, j, i)] = DF(B.s.x, B.c.x);
+        sc[tix<Q>(k + 1, j, i)] = DF(B.s.y, B.c.y);
+        vt[k] = DF(C.s.x, C.c.x);
+        vt[k + 1] = DF(C.s.y, C.c.y);
+      }
+    } else {
+#pragma unroll
+    for (int k = 0; k < Q; ++k) {
+      const int q = (k * Q + j) * Q + i;
+      T grr, grs, grt, gss, gst, gtt;
+      if constexpr (OP == OP_DIFF_GEO) {
+        const T xt = tab.qx[k];
+        T J[3][3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          J[c][0] = c1[c] + c1t[c] * xt;
+          J[c][1] = c2[c] + c2t[c] * xt;
+          J[c][2] = c3[c];
+        }
+        // adjugate rows A_a (A J = det I) and G = (w k / det) A A^T
+        const T A00 = J[1][1] * J[2][2] - J[1][2] * J[2][1], A01 = J[0][2] * J[2][1] - J[0][1] * J[2][2];
+        const T A02 = J[0][1] * J[1][2] - J[0][2] * J[1][1], A10 = J[1][2] * J[2][0] - J[1][0] * J[2][2];
+        const T A11 = J[0][0] * J[2][2] - J[0][2] * J[2][0], A12 = J[0][2] * J[1][0] - J[0][0] * J[1][2];
+        const T A20 = J[1][0] * J[2][1] - J[1][1] * J[2][0], A21 = J[0][1] * J[2][0] - J[0][0] * J[2][1];
+        const T A22 = J[0][0] * J[1][1] - J[0][1] * J[1][0];
+        const T det = J[0][0] * A00 + J[0][1] * A10 + J[0][2] * A20;
+        const T f = active ? q_to(sq[GEO_COEFFS + q], T()) / det : (T)0;
+        grr = f * (A00 * A00 + A01 * A01 + A02 * A02);
+        grs = f * (A00 * A10 + A01 * A11 + A02 * A12);
+        grt = f * (A00 * A20 + A01 * A21 + A02 * A22);
+        gss = f * (A10 * A10 + A11 * A11 + A12 * A12);
+        gst = f * (A10 * A20 + A11 * A21 + A12 * A22);
+        gtt = f * (A20 * A20 + A21 * A21 + A22 * A22);
+      } else {
+        grr = q_to(sq[q], T()), grs = q_to(sq[NQ + q], T()), grt = q_to(sq[2 * NQ + q], T());
+        gss = q_to(sq[3 * NQ + q], T()), gst = q_to(sq[4 * NQ + q], T()), gtt = q_to(sq[5 * NQ + q], T());
+      }
+      const T ur = sb[tix<Q>(k, j, i)], us = sc[tix<Q>(k, j, i)];
+      sb[tix<Q>(k, j, i)] = dot3(grr, ur, grs, us, grt, ut[k]);
+      sc[tix<Q>(k, j, i)] = dot3(grs, ur, gss, us, gst, ut[k]);
+      vt[k] = dot3(grt, ur, gst, us, gtt, ut[k]);
+    }
+    }  // PAIRED
+    __syncthreads();
+    {  // r transposed: owners (s = i, t = j)
+      T v[Q], g[Q];
+#pragma unroll
+      for (int m = 0; m < Q; ++m) v[m] = sb[tix<Q>(j, i, m)];
+      eo_apply<Q, Q, -1>(tab.eDT, v, g);
+#pragma unroll
+      for (int n = 0; n < Q; ++n) sa[tix<Q>(j, i, n)] = g[n];
+    }
+    {  // s transposed: owners (r = i, t = j), in place on their own line
+      T v[Q], g[Q];
+#pragma unroll
+      for (int m = 0; m < Q; ++m) v[m] = sc[tix<Q>(j, m, i)];
+      eo_apply<Q, Q, -1>(tab.eDT, v, g);
+#pragma unroll
+      for (int n = 0; n < Q; ++n) sc[tix<Q>(j, n, i)] = g[n];
+    }
+    T yt[Q];
+    eo_apply<Q, Q, -1>(tab.eDT, vt, yt);
+    __syncthreads();
+    if constexpr (PAIRED) {
+#pragma unroll
+      for (int k = 0; k < Q; k += 2) {  // add3 on points k and k + 1 together
+        const DF a0 = sa[tix<Q>(k, j, i)], a1 = sa[tix<Q>(k + 1, j, i)];
+        const DF c0 = sc[tix<Q>(k, j, i)], c1 = sc[tix<Q>(k + 1, j, i)];
+        float2 h, l;
+        df2_add(make_float2(yt[k].hi, yt[k + 1].hi), make_float2(yt[k].lo, yt[k + 1].lo),
+                make_float2(a0.hi, a1.hi), make_float2(a0.lo, a1.lo), h, l);
+        df2_add(h, l, make_float2(c0.hi, c1.hi), make_float2(c0.lo, c1.lo), h, l);
+        w[k] = DF(h.x, l.x);
+        w[k + 1] = DF(h.y, l.y);
+      }
+    } else {
+#pragma unroll
+      for (int k = 0; k < Q; ++k) w[k] = add3(yt[k], sa[tix<Q>(k, j, i)], sc[tix<Q>(k, j, i)]);
+    }
+  }
+
+  // ---- transposed interpolation back to the nodes
+  if constexpr (COLLOC) {
+#pragma unroll
+    for (int c = 0; c < P; ++c) yv[c] = w[c];
+  } else {
+    {  // t: column owners, registers
+      T z[P];
+      eo_apply<P, Q, 1>(tab.eBT, w, z);
+      if constexpr (OP == CEED_OP_MASS) __syncthreads();  // sa was last read as the uq column
+#pragma unroll
+      for (int c = 0; c < P; ++c) sa[tix<Q>(c, j, i)] = z[c];
+    }
+    __syncthreads();
+    if (j < P) {  // s: owners (r = i, t = j)
+      T v[Q], z[P];
+#pragma unroll
+      for (int m = 0; m < Q; ++m) v[m] = sa[tix<Q>(j, m, i)];
+      eo_apply<P, Q, 1>(tab.eBT, v, z);
+#pragma unroll
+      for (int n = 0; n < P; ++n) sb[tix<Q>(j, n, i)] = z[n];
+    }
+    __syncthreads();
+    if (node_thread) {  // r: owners (s = i, t = j)
+      T v[Q], z[P];
+#pragma unroll
+      for (int m = 0; m < Q; ++m) v[m] = sb[tix<Q>(j, i, m)];
+      eo_apply<P, Q, 1>(tab.eBT, v, z);
+#pragma unroll
+      for (int n = 0; n < P; ++n) sa[tix<Q>(j, i, n)] = z[n];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int c = 0; c < P; ++c) yv[c] = node_thread ? sa[tix<Q>(c, j, i)] : (T)0;
+  }
+}
+
 struct ApplyArgs {
   const uint32_t *emap;
   const void *qdata;
@@ -301,9 +552,7 @@ template <int P, int Q, int OP, typename T, typename TQ, bool STAGE, bool XCG = 
 __device__ __forceinline__ void apply_block(const ApplyArgs &a, const OpTab<T> &tab, int64_t blk,
                                             unsigned char *smem_raw, uint64_t *bar) {
   constexpr int NPT = Q * Q;
-  constexpr bool COLLOC = (P == Q);
   constexpr int ND = P * P * P;
-  constexpr int NQ = Q * Q * Q;
   constexpr size_t QB = STAGE ? ((qblock_bytes<Q, OP, TQ>() + 127) & ~(size_t)127) : 0;
   constexpr size_t EB = apply_elem_smem<P, Q, OP, T, TQ, STAGE>();
 
@@ -346,6 +595,19 @@ __device__ __forceinline__ void apply_block(const ApplyArgs &a, const OpTab<T> &
   }
   bool have_q = false;
   bool q_ok = true;  // false once this thread's copy wait gave up: the element then writes nothing
+  auto wait_q = [&]() {
+    if (STAGE && !have_q) {  // elements past the end issued no copy and do not wait
+      bool landed = true;
+      if (active)
+        landed = std::is_same<T, double>::value ? mbar_wait_n(&bar[el], 0, a.wait_limit)
+                                                : mbar_wait(&bar[el], 0, a.wait_limit == 0);
+      if (!landed) {
+        q_ok = false;
+        if (ij == 0) *a.err = CEED_ERR_TIMEOUT;
+      }
+      have_q = true;
+    }
+  };
 
   for (int col = 0; col < a.ncol; ++col) {
     // ---- all global loads of the column up front: x at my nodes, old y where an earlier colour wrote
@@ -369,254 +631,8 @@ __device__ __forceinline__ void apply_block(const ApplyArgs &a, const OpTab<T> &
 #pragma unroll
     for (int c = 0; c < P; ++c) u[c] = LVec<T>::in(xv[c]);
 
-    // ---- interpolate to the quadrature points (identity when collocated)
-    T uq[Q];
-    if constexpr (COLLOC) {
-#pragma unroll
-      for (int k = 0; k < Q; ++k) uq[k] = u[k];
-    } else {
-      if (node_thread) {  // t: column owners (r = i, s = j) hold the line in registers
-        T w[Q];
-        eo_apply<Q, P, 1>(tab.eB, u, w);
-#pragma unroll
-        for (int k = 0; k < Q; ++k) sa[tix<Q>(k, j, i)] = w[k];
-      }
-      __syncthreads();
-      if (i < P) {        // s: owners (r = i, t = j)
-        T v[P], w[Q];
-#pragma unroll
-        for (int m = 0; m < P; ++m) v[m] = sa[tix<Q>(j, m, i)];
-        eo_apply<Q, P, 1>(tab.eB, v, w);
-#pragma unroll
-        for (int n = 0; n < Q; ++n) sb[tix<Q>(j, n, i)] = w[n];
-      }
-      __syncthreads();
-      {                   // r: owners (s = i, t = j)
-        T v[P], w[Q];
-#pragma unroll
-        for (int m = 0; m < P; ++m) v[m] = sb[tix<Q>(j, i, m)];
-        eo_apply<Q, P, 1>(tab.eB, v, w);
-#pragma unroll
-        for (int n = 0; n < Q; ++n) sa[tix<Q>(j, i, n)] = w[n];
-      }
-      __syncthreads();
-#pragma unroll
-      for (int k = 0; k < Q; ++k) uq[k] = sa[tix<Q>(k, j, i)];
-    }
-
-    // ---- quadrature-point operator
-    T w[Q];
-    if (STAGE && !have_q) {  // elements past the end issued no copy and do not wait
-      bool landed = true;  // inactive elements issued no copy and must not wait
-      if (active)
-        landed = std::is_same<T, double>::value ? mbar_wait_n(&bar[el], 0, a.wait_limit)
-                                                : mbar_wait(&bar[el], 0, a.wait_limit == 0);
-      if (!landed) {
-        q_ok = false;
-        if (ij == 0) *a.err = CEED_ERR_TIMEOUT;
-      }
-      have_q = true;
-    }
-    if constexpr (OP == CEED_OP_MASS) {
-#pragma unroll
-      for (int k = 0; k < Q; ++k) w[k] = active ? qmul(q_to(sq[(k * Q + j) * Q + i], T()), uq[k]) : (T)0;
-    } else {
-      T ut[Q];
-      eo_apply<Q, Q, -1>(tab.eD, uq, ut);
-      if constexpr (COLLOC) {
-#pragma unroll
-        for (int k = 0; k < Q; ++k) sa[tix<Q>(k, j, i)] = uq[k];
-        __syncthreads();
-      }  // non-collocated: sa already holds uq at these positions
-      {  // r: owners (s = i, t = j)
-        T v[Q], g[Q];
-#pragma unroll
-        for (int m = 0; m < Q; ++m) v[m] = sa[tix<Q>(j, i, m)];
-        eo_apply<Q, Q, -1>(tab.eD, v, g);
-#pragma unroll
-        for (int n = 0; n < Q; ++n) sb[tix<Q>(j, i, n)] = g[n];
-      }
-      {  // s: owners (r = i, t = j)
-        T v[Q], g[Q];
-#pragma unroll
-        for (int m = 0; m < Q; ++m) v[m] = sa[tix<Q>(j, m, i)];
-        eo_apply<Q, Q, -1>(tab.eD, v, g);
-#pragma unroll
-        for (int n = 0; n < Q; ++n) sc[tix<Q>(j, n, i)] = g[n];
-      }
-      __syncthreads();
-      // pointwise v = G grad u at my column, in place
-      T vt[Q];
-      // on-the-fly geometry: the trilinear map x = a0 + a1 r + a2 s + a3 t + a4 rs + a5 rt + a6 st + a7 rst
-      // gives dx/dr = (a1 + a4 s) + (a5 + a7 s) t, dx/ds = (a2 + a4 r) + (a6 + a7 r) t and
-      // dx/dt = a3 + a5 r + a6 s + a7 rs, so along my column only t varies: 6 FMAs per point for J
-      T c1[3], c1t[3], c2[3], c2t[3], c3[3];
-      if constexpr (OP == OP_DIFF_GEO) {
-        const T xr = tab.qx[i], xs = tab.qx[j];
-#pragma unroll
-        for (int c = 0; c < 3; ++c) {
-          const T a1 = q_to(sq[c], T()), a2 = q_to(sq[3 + c], T()), a3 = q_to(sq[6 + c], T());
-          const T a4 = q_to(sq[9 + c], T()), a5 = q_to(sq[12 + c], T()), a6 = q_to(sq[15 + c], T());
-          const T a7 = q_to(sq[18 + c], T());
-          c1[c] = a1 + a4 * xs;
-          c1t[c] = a5 + a7 * xs;
-          c2[c] = a2 + a4 * xr;
-          c2t[c] = a6 + a7 * xr;
-          c3[c] = a3 + a5 * xr + a6 * xs + a7 * xr * xs;
-        }
-      }
-      // double-float with an even number of points per column: points k and k + 1 share the two
-      // lanes of the packed instructions (the same steps as dot3<DF>, lane by lane: bit-identical)
-      constexpr bool PAIRED = std::is_same<T, DF>::value && OP == CEED_OP_DIFFUSION && (Q % 2 == 0);
-      if constexpr (PAIRED) {
-#pragma unroll
-        for (int k = 0; k < Q; k += 2) {
-          const int q0 = (k * Q + j) * Q + i, q1 = q0 + Q * Q;
-          DF g0[6], g1[6];
-#pragma unroll
-          for (int c = 0; c < 6; ++c) {
-            g0[c] = q_to(sq[c * NQ + q0], T());
-            g1[c] = q_to(sq[c * NQ + q1], T());
-          }
-          const DF ur0 = sb[tix<Q>(k, j, i)], ur1 = sb[tix<Q>(k + 1, j, i)];
-          const DF us0 = sc[tix<Q>(k, j, i)], us1 = sc[tix<Q>(k + 1, j, i)];
-          const float2 urh = make_float2(ur0.hi, ur1.hi), url = make_float2(ur0.lo, ur1.lo);
-          const float2 ush = make_float2(us0.hi, us1.hi), usl = make_float2(us0.lo, us1.lo);
-          const float2 uth = make_float2(ut[k].hi, ut[k + 1].hi), utl = make_float2(ut[k].lo, ut[k + 1].lo);
-          float2 gh[6], gl[6];
-#pragma unroll
-          for (int c = 0; c < 6; ++c) {
-            gh[c] = make_float2(g0[c].hi, g1[c].hi);
-            gl[c] = make_float2(g0[c].lo, g1[c].lo);
-          }
-          // components rr 0, rs 1, rt 2, ss 3, st 4, tt 5
-          DFAcc2 A = acc2_first(gh[0], gl[0], urh, url);
-          acc2_mac(A, gh[1], gl[1], ush, usl);
-          acc2_mac(A, gh[2], gl[2], uth, utl);
-          DFAcc2 B = acc2_first(gh[1], gl[1], urh, url);
-          acc2_mac(B, gh[3], gl[3], ush, usl);
-          acc2_mac(B, gh[4], gl[4], uth, utl);
-          DFAcc2 C = acc2_first(gh[2], gl[2], urh, url);
-          acc2_mac(C, gh[4], gl[4], ush, usl);
-          acc2_mac(C, gh[5], gl[5], uth, utl);
-          sb[tix<Q>(k, j, i)] = DF(A.s.x, A.c.x);
-          sb[tix<Q>(k + 1, j, i)] = DF(A.s.y, A.c.y);
-          sc[tix<Q>(k, j, i)] = DF(B.s.x, B.c.x);
-          sc[tix<Q>(k + 1, j, i)] = DF(B.s.y, B.c.y);
-          vt[k] = DF(C.s.x, C.c.x);
-          vt[k + 1] = DF(C.s.y, C.c.y);
-        }
-      } else {
-#pragma unroll
-      for (int k = 0; k < Q; ++k) {
-        const int q = (k * Q + j) * Q + i;
-        T grr, grs, grt, gss, gst, gtt;
-        if constexpr (OP == OP_DIFF_GEO) {
-          const T xt = tab.qx[k];
-          T J[3][3];
-#pragma unroll
-          for (int c = 0; c < 3; ++c) {
-            J[c][0] = c1[c] + c1t[c] * xt;
-            J[c][1] = c2[c] + c2t[c] * xt;
-            J[c][2] = c3[c];
-          }
-          // adjugate rows A_a (A J = det I) and G = (w k / det) A A^T
-          const T A00 = J[1][1] * J[2][2] - J[1][2] * J[2][1], A01 = J[0][2] * J[2][1] - J[0][1] * J[2][2];
-          const T A02 = J[0][1] * J[1][2] - J[0][2] * J[1][1], A10 = J[1][2] * J[2][0] - J[1][0] * J[2][2];
-          const T A11 = J[0][0] * J[2][2] - J[0][2] * J[2][0], A12 = J[0][2] * J[1][0] - J[0][0] * J[1][2];
-          const T A20 = J[1][0] * J[2][1] - J[1][1] * J[2][0], A21 = J[0][1] * J[2][0] - J[0][0] * J[2][1];
-          const T A22 = J[0][0] * J[1][1] - J[0][1] * J[1][0];
-          const T det = J[0][0] * A00 + J[0][1] * A10 + J[0][2] * A20;
-          const T f = active ? q_to(sq[GEO_COEFFS + q], T()) / det : (T)0;
-          grr = f * (A00 * A00 + A01 * A01 + A02 * A02);
-          grs = f * (A00 * A10 + A01 * A11 + A02 * A12);
-          grt = f * (A00 * A20 + A01 * A21 + A02 * A22);
-          gss = f * (A10 * A10 + A11 * A11 + A12 * A12);
-          gst = f * (A10 * A20 + A11 * A21 + A12 * A22);
-          gtt = f * (A20 * A20 + A21 * A21 + A22 * A22);
-        } else {
-          grr = q_to(sq[q], T()), grs = q_to(sq[NQ + q], T()), grt = q_to(sq[2 * NQ + q], T());
-          gss = q_to(sq[3 * NQ + q], T()), gst = q_to(sq[4 * NQ + q], T()), gtt = q_to(sq[5 * NQ + q], T());
-        }
-        const T ur = sb[tix<Q>(k, j, i)], us = sc[tix<Q>(k, j, i)];
-        sb[tix<Q>(k, j, i)] = dot3(grr, ur, grs, us, grt, ut[k]);
-        sc[tix<Q>(k, j, i)] = dot3(grs, ur, gss, us, gst, ut[k]);
-        vt[k] = dot3(grt, ur, gst, us, gtt, ut[k]);
-      }
-      }  // PAIRED
-      __syncthreads();
-      {  // r transposed: owners (s = i, t = j)
-        T v[Q], g[Q];
-#pragma unroll
-        for (int m = 0; m < Q; ++m) v[m] = sb[tix<Q>(j, i, m)];
-        eo_apply<Q, Q, -1>(tab.eDT, v, g);
-#pragma unroll
-        for (int n = 0; n < Q; ++n) sa[tix<Q>(j, i, n)] = g[n];
-      }
-      {  // s transposed: owners (r = i, t = j), in place on their own line
-        T v[Q], g[Q];
-#pragma unroll
-        for (int m = 0; m < Q; ++m) v[m] = sc[tix<Q>(j, m, i)];
-        eo_apply<Q, Q, -1>(tab.eDT, v, g);
-#pragma unroll
-        for (int n = 0; n < Q; ++n) sc[tix<Q>(j, n, i)] = g[n];
-      }
-      T yt[Q];
-      eo_apply<Q, Q, -1>(tab.eDT, vt, yt);
-      __syncthreads();
-      if constexpr (PAIRED) {
-#pragma unroll
-        for (int k = 0; k < Q; k += 2) {  // add3 on points k and k + 1 together
-          const DF a0 = sa[tix<Q>(k, j, i)], a1 = sa[tix<Q>(k + 1, j, i)];
-          const DF c0 = sc[tix<Q>(k, j, i)], c1 = sc[tix<Q>(k + 1, j, i)];
-          float2 h, l;
-          df2_add(make_float2(yt[k].hi, yt[k + 1].hi), make_float2(yt[k].lo, yt[k + 1].lo),
-                  make_float2(a0.hi, a1.hi), make_float2(a0.lo, a1.lo), h, l);
-          df2_add(h, l, make_float2(c0.hi, c1.hi), make_float2(c0.lo, c1.lo), h, l);
-          w[k] = DF(h.x, l.x);
-          w[k + 1] = DF(h.y, l.y);
-        }
-      } else {
-#pragma unroll
-        for (int k = 0; k < Q; ++k) w[k] = add3(yt[k], sa[tix<Q>(k, j, i)], sc[tix<Q>(k, j, i)]);
-      }
-    }
-
-    // ---- transposed interpolation back to the nodes
     T yv[P];
-    if constexpr (COLLOC) {
-#pragma unroll
-      for (int c = 0; c < P; ++c) yv[c] = w[c];
-    } else {
-      {  // t: column owners, registers
-        T z[P];
-        eo_apply<P, Q, 1>(tab.eBT, w, z);
-        if constexpr (OP == CEED_OP_MASS) __syncthreads();  // sa was last read as the uq column
-#pragma unroll
-        for (int c = 0; c < P; ++c) sa[tix<Q>(c, j, i)] = z[c];
-      }
-      __syncthreads();
-      if (j < P) {  // s: owners (r = i, t = j)
-        T v[Q], z[P];
-#pragma unroll
-        for (int m = 0; m < Q; ++m) v[m] = sa[tix<Q>(j, m, i)];
-        eo_apply<P, Q, 1>(tab.eBT, v, z);
-#pragma unroll
-        for (int n = 0; n < P; ++n) sb[tix<Q>(j, n, i)] = z[n];
-      }
-      __syncthreads();
-      if (node_thread) {  // r: owners (s = i, t = j)
-        T v[Q], z[P];
-#pragma unroll
-        for (int m = 0; m < Q; ++m) v[m] = sb[tix<Q>(j, i, m)];
-        eo_apply<P, Q, 1>(tab.eBT, v, z);
-#pragma unroll
-        for (int n = 0; n < P; ++n) sa[tix<Q>(j, i, n)] = z[n];
-      }
-      __syncthreads();
-#pragma unroll
-      for (int c = 0; c < P; ++c) yv[c] = node_thread ? sa[tix<Q>(c, j, i)] : (T)0;
-    }
+    element_op<P, Q, OP, T, TQ>(tab, u, yv, sq, sa, sb, sc, i, j, node_thread, active, wait_q);
 
     // ---- scatter-add (E -> L), atomic-free
     const bool fused_dot = a.dot_part || a.dot_sh;
@@ -710,6 +726,12 @@ __global__ void __maxnreg__(APPLY_DF_MAX_REGS) apply_kernel_capped(const ApplyAr
   apply_block<P, Q, OP, T, TQ, STAGE>(a, tab, blockIdx.x, smem_raw, bar);
 }
 
+}  // namespace ceedgb
+
+#include "brick.cuh"
+
+namespace ceedgb {
+
 // Launch one kernel per colour for a fixed (P, Q, op, T, TQ) and variant (elements per block, staging).
 template <int P, int Q, int OP, typename T, typename TQ, bool STAGE>
 int launch_variant(ceed_mesh_t m, const OpTab<T> &tab, const ApplyReq &r, int ne, cudaStream_t s) {
@@ -756,6 +778,17 @@ int launch_colours(ceed_mesh_t m, const OpTab<T> &tab, const ApplyReq &r, cudaSt
     const ApplyChoice &ch = m->tuned[r.op][r.prec];
     ne = ch.ne > 0 ? ch.ne : default_elems_per_block<Q>();
     stage = ch.ne > 0 ? ch.stage : 1;
+  }
+  if (stage >= 2) {  // brick kernel: FP32-pipe operators on a brick lattice, one column
+    if constexpr (std::is_same<T, float>::value) {
+      if (m->n_bricks > 0 && r.ncol == 1) {
+        if (stage == 3) return launch_bricks<P, Q, OP, T, TQ, true>(m, tab, r, s);
+        return launch_bricks<P, Q, OP, T, TQ, false>(m, tab, r, s);
+      }
+    }
+    if (r.ne > 0) return fail(CEED_ERR_UNSUPPORTED, "brick kernel: needs a brick lattice, one column, an FP32-pipe operator");
+    ne = default_elems_per_block<Q>();  // a tuned brick choice on a request the bricks cannot serve
+    stage = 1;
   }
   if (ne > max_elems_per_block<Q>() || ne > APPLY_MAX_NE) return fail(CEED_ERR_INVALID, "elements per block too large");
   if (stage) return launch_variant<P, Q, OP, T, TQ, true>(m, tab, r, ne, s);

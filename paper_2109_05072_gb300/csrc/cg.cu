@@ -392,7 +392,8 @@ static int fused_batch(ceed_mesh_t m, const ApplyReq &op, double *y, const Work 
   CEED_CUDA_CHECK(cudaMemsetAsync(w.fsync, 0, 4 * sizeof(unsigned), s));  // barrier state (a timeout leaves it dirty)
   // elements per block: the apply variant chosen for this operator (autotuner or
   // ceed_set_apply_variant), else blocks of about 128 threads
-  const int tuned = m->tuned[CEED_OP_DIFFUSION][op.prec].ne;
+  const ApplyChoice &tc = m->tuned[CEED_OP_DIFFUSION][op.prec];
+  const int tuned = tc.stage < 2 ? tc.ne : 0;  // a tuned brick variant says nothing about element blocks
   const int ne = tuned > 0 ? tuned : std::max(1, std::min(APPLY_MAX_NE, 128 / (m->Q * m->Q)));
   unsigned grid = 0;
   switch (op.prec) {

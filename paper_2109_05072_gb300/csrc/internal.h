@@ -22,6 +22,14 @@ constexpr uint32_t FLAG_DIR = 1u << 30;
 constexpr uint32_t FLAG_LAST = 1u << 29;
 constexpr uint32_t DOF_MASK = (1u << 29) - 1u;
 
+// Brick flags (brick.cuh): bits 0-2 parity of the brick's lattice coordinates (x, y, z); bits 3-8 set
+// when the brick's face at -x, +x, -y, +y, -z, +z touches another brick.
+constexpr uint32_t BRICK_MX = 1u << 3, BRICK_PX = 1u << 4, BRICK_MY = 1u << 5, BRICK_PY = 1u << 6;
+constexpr uint32_t BRICK_MZ = 1u << 7, BRICK_PZ = 1u << 8;
+// Elements of a brick along z (2 x 2 x BRICK_KZ elements per brick).  One layer: 2 x 2 x 2 bricks
+// read about 6% fewer nodes but fit half as many blocks per SM, and measured slower.
+constexpr int BRICK_KZ = 1;
+
 // Even-odd split of a centro-(anti)symmetric NO x NI matrix M (M[NO-1-i][NI-1-j] = +-M[i][j]):
 // E/O are the (NO/2) x (NI/2) blocks acting on folded inputs, cmid the middle input column
 // (odd NI), rmid the middle output row (odd NO), cc the centre entry.
@@ -92,7 +100,8 @@ struct QRule {
 };
 
 // Apply-kernel variant: elements per thread block, and whether quadrature data is staged in
-// shared memory by a TMA bulk copy (1) or read from global memory at the pointwise step (0).
+// shared memory by a TMA bulk copy (1) or read from global memory at the pointwise step (0); stage 2
+// and 3 select the brick kernel (2 x 2 x BRICK_KZ elements per block) without and with staging.
 struct ApplyChoice {
   int ne = 0;      // 0: not tuned (use the default)
   int stage = 1;
@@ -128,6 +137,15 @@ struct ceed_mesh_s {
   ceedgb::QRule rule;                   // quadrature rule of the mesh
   double gll_x[ceedgb::MAX_P];          // GLL nodes of the basis
   ceedgb::ApplyChoice tuned[3][6];      // [op][prec] autotuned apply variant
+  // 2 x 2 x BRICK_KZ element bricks of a structured lattice (brick.cuh), found at setup; n_bricks = 0
+  // if the mesh is not such a lattice
+  int64_t n_bricks = 0;
+  std::vector<int64_t> brick_start;     // brick ranges of the 8 brick colours, size 9
+  int64_t brick_sy = 0, brick_sz = 0;   // node-lattice strides
+  int32_t *d_gbase = nullptr;           // [brick] corner node
+  int32_t *d_gelem = nullptr;           // [brick][4 BRICK_KZ] colour-sorted elements
+  uint32_t *d_gflags = nullptr;         // [brick] parity and neighbour bits
+  uint32_t *d_dirbits = nullptr;        // Dirichlet bit per node (meshes with a Dirichlet mask)
 };
 
 namespace ceedgb {

@@ -34,7 +34,21 @@ int ensure_dynamic_smem(const void *func, size_t bytes) {
   std::lock_guard<std::mutex> lock(mu);
   size_t &cur = raised[{func, dev}];
   if (bytes > cur) {
-    CEED_CUDA_CHECK(cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+    // refuse a size the device cannot give before asking for it: a failed request would leave an
+    // error for the next cudaGetLastError of an unrelated call
+    int optin = 0;
+    CEED_CUDA_CHECK(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+    cudaFuncAttributes fa;
+    CEED_CUDA_CHECK(cudaFuncGetAttributes(&fa, func));
+    if (bytes + fa.sharedSizeBytes > (size_t)optin)
+      return fail(CEED_ERR_UNSUPPORTED, "kernel variant needs " + std::to_string(bytes + fa.sharedSizeBytes) +
+                                            " bytes of shared memory per block; the device allows " +
+                                            std::to_string(optin));
+    const cudaError_t e = cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e != cudaSuccess) {
+      cudaGetLastError();  // not sticky: clear it
+      return cuda_fail(e, "cudaFuncSetAttribute(MaxDynamicSharedMemorySize)");
+    }
     cur = bytes;
   }
   return CEED_OK;
@@ -291,10 +305,106 @@ struct HostFree {
     cudaFree(m->d_vertices);
     cudaFree(m->d_coords);
     cudaFree(m->d_err);
+    cudaFree(m->d_gbase);
+    cudaFree(m->d_gelem);
+    cudaFree(m->d_gflags);
+    cudaFree(m->d_dirbits);
     delete m;
   }
 };
 }  // namespace
+
+// Bricks of a structured lattice (brick.cuh).  The mesh qualifies when the node numbering is a
+// lexicographic lattice (x fastest) and every element's nodes are base + a + b sy + c sz with
+// common strides sy, sz, the element lattice dimensions are multiples of the brick's (2, 2,
+// BRICK_KZ) and every lattice cell holds one element.  Bricks are sorted by colour (parity of their
+// coordinates: bit 0 x, bit 1 y, bit 2 z) and then lexicographically.  Leaves n_bricks = 0 (the
+// element kernel serves the mesh) when the mesh does not qualify.
+static int detect_bricks(ceed_mesh_s *m, const std::vector<uint32_t> &map, const std::vector<int32_t> &perm,
+                         const std::vector<uint8_t> &dir, cudaStream_t s) {
+  const int P = m->P, p = m->p;
+  const int64_t E = m->E, nd = (int64_t)P * P * P, nL = m->n_ldof;
+  if (p < 1 || E < 8) return CEED_OK;
+  const int64_t n00 = map[0];
+  const int64_t sy = (int64_t)map[P] - n00, sz = (int64_t)map[(int64_t)P * P] - n00;
+  if ((int64_t)map[1] - n00 != 1 || sy < P || sz < sy * P || sz % sy != 0 || nL % sz != 0) return CEED_OK;
+  const int64_t nxn = sy, nyn = sz / sy, nzn = nL / sz;
+  if ((nxn - 1) % p || (nyn - 1) % p || (nzn - 1) % p) return CEED_OK;
+  const int64_t Nx = (nxn - 1) / p, Ny = (nyn - 1) / p, Nz = (nzn - 1) / p;
+  if (Nx * Ny * Nz != E || Nx % 2 || Ny % 2 || Nz % BRICK_KZ) return CEED_OK;
+  std::vector<int32_t> elem_at;
+  try {
+    elem_at.assign(E, -1);
+  } catch (...) {
+    return fail(CEED_ERR_OOM, "host allocation");
+  }
+  for (int64_t e = 0; e < E; ++e) {
+    const uint32_t *row = &map[e * nd];
+    const int64_t b0 = row[0];
+    const int64_t X = b0 % sy, Y = (b0 / sy) % nyn, Z = b0 / sz;
+    if (X % p || Y % p || Z % p || X / p >= Nx || Y / p >= Ny || Z / p >= Nz) return CEED_OK;
+    for (int c = 0, n = 0; c < P; ++c)
+      for (int b = 0; b < P; ++b)
+        for (int a = 0; a < P; ++a, ++n)
+          if ((int64_t)row[n] != b0 + a + b * sy + c * sz) return CEED_OK;
+    const int64_t cell = X / p + Nx * (Y / p + Ny * (Z / p));
+    if (elem_at[cell] >= 0) return CEED_OK;
+    elem_at[cell] = (int32_t)e;
+  }
+  std::vector<int32_t> spos(E);
+  for (int64_t i = 0; i < E; ++i) spos[perm[i]] = (int32_t)i;
+  const int64_t Gx = Nx / 2, Gy = Ny / 2, Gz = Nz / BRICK_KZ, G = Gx * Gy * Gz;
+  constexpr int NEL = 4 * BRICK_KZ;
+  std::vector<int32_t> gbase, gelem;
+  std::vector<uint32_t> gflags;
+  std::vector<int64_t> start(9, 0);
+  gbase.reserve(G);
+  gelem.reserve(NEL * G);
+  gflags.reserve(G);
+  for (int c = 0; c < 8; ++c) {
+    start[c] = (int64_t)gbase.size();
+    for (int64_t gz = (c >> 2) & 1; gz < Gz; gz += 2)
+      for (int64_t gy = (c >> 1) & 1; gy < Gy; gy += 2)
+        for (int64_t gx = c & 1; gx < Gx; gx += 2) {
+          gbase.push_back((int32_t)(2 * gx * p + 2 * gy * p * sy + BRICK_KZ * gz * p * sz));
+          for (int k = 0; k < NEL; ++k) {
+            const int64_t ex = 2 * gx + (k & 1), ey = 2 * gy + ((k >> 1) & 1), ez = BRICK_KZ * gz + (k >> 2);
+            gelem.push_back(spos[elem_at[ex + Nx * (ey + Ny * ez)]]);
+          }
+          uint32_t f = (uint32_t)((gx & 1) | ((gy & 1) << 1) | ((gz & 1) << 2));
+          if (gx > 0) f |= BRICK_MX;
+          if (gx + 1 < Gx) f |= BRICK_PX;
+          if (gy > 0) f |= BRICK_MY;
+          if (gy + 1 < Gy) f |= BRICK_PY;
+          if (gz > 0) f |= BRICK_MZ;
+          if (gz + 1 < Gz) f |= BRICK_PZ;
+          gflags.push_back(f);
+        }
+  }
+  start[8] = (int64_t)gbase.size();
+  std::vector<uint32_t> bits;
+  if (!dir.empty()) {
+    bits.assign((nL + 31) / 32, 0u);
+    for (int64_t v = 0; v < nL; ++v)
+      if (dir[v]) bits[v >> 5] |= 1u << (v & 31);
+  }
+  CEED_CUDA_CHECK(cudaMalloc(&m->d_gbase, G * sizeof(int32_t)));
+  CEED_CUDA_CHECK(cudaMalloc(&m->d_gelem, NEL * G * sizeof(int32_t)));
+  CEED_CUDA_CHECK(cudaMalloc(&m->d_gflags, G * sizeof(uint32_t)));
+  CEED_CUDA_CHECK(cudaMemcpyAsync(m->d_gbase, gbase.data(), G * sizeof(int32_t), cudaMemcpyHostToDevice, s));
+  CEED_CUDA_CHECK(cudaMemcpyAsync(m->d_gelem, gelem.data(), NEL * G * sizeof(int32_t), cudaMemcpyHostToDevice, s));
+  CEED_CUDA_CHECK(cudaMemcpyAsync(m->d_gflags, gflags.data(), G * sizeof(uint32_t), cudaMemcpyHostToDevice, s));
+  if (!bits.empty()) {
+    CEED_CUDA_CHECK(cudaMalloc(&m->d_dirbits, bits.size() * sizeof(uint32_t)));
+    CEED_CUDA_CHECK(cudaMemcpyAsync(m->d_dirbits, bits.data(), bits.size() * sizeof(uint32_t), cudaMemcpyHostToDevice, s));
+  }
+  CEED_CUDA_CHECK(cudaStreamSynchronize(s));  // the host vectors go out of scope
+  m->brick_start = start;
+  m->brick_sy = sy;
+  m->brick_sz = sz;
+  m->n_bricks = G;
+  return CEED_OK;
+}
 
 extern "C" int ceed_setup_mesh(const ceed_mesh_desc *desc, ceed_mesh_t *out, void *stream) {
   if (!desc || !out) return fail(CEED_ERR_INVALID, "null descriptor or output");
@@ -441,6 +551,7 @@ extern "C" int ceed_setup_mesh(const ceed_mesh_desc *desc, ceed_mesh_t *out, voi
     }
   }
 
+  if (int st = detect_bricks(m.get(), map, perm, dir, s)) return st;
   CEED_CUDA_CHECK(cudaMalloc(&m->d_emap, E * nd * 4));
   CEED_CUDA_CHECK(cudaMalloc(&m->d_perm, E * 4));
   CEED_CUDA_CHECK(cudaMalloc(&m->d_vertices, E * 24 * 8));
@@ -470,6 +581,13 @@ extern "C" int ceed_mesh_info(ceed_mesh_t m, int32_t *n_colors, int32_t *Q, int3
   if (n_colors) *n_colors = m->n_colors;
   if (Q) *Q = m->Q;
   if (P) *P = m->P;
+  return CEED_OK;
+}
+
+extern "C" int ceed_mesh_bricks(ceed_mesh_t m, int64_t *n_bricks) {
+  if (int st = check_mesh(m)) return st;
+  if (!n_bricks) return fail(CEED_ERR_INVALID, "null output");
+  *n_bricks = m->n_bricks;
   return CEED_OK;
 }
 
@@ -562,6 +680,13 @@ extern "C" int ceed_apply_host(ceed_mesh_t m, int op, const void *qdata, int pre
   return CEED_OK;
 }
 
+// The brick kernel serves FP32-pipe operators (FP32 arithmetic on FP32, BF16, FP16 or on-the-fly
+// geometry data) with one column, on meshes whose setup found a brick lattice.
+static bool brick_ok(ceed_mesh_t m, int prec, int ncol) {
+  return m->n_bricks > 0 && ncol == 1 &&
+         (prec == CEED_F32 || prec == CEED_BF16 || prec == CEED_F16 || prec == CEED_F32_GEO);
+}
+
 // ---------------------------------------------------------------------------------------------
 // Autotuner for the apply kernel: times every (elements per block, staging) variant on the
 // caller's mesh, quadrature data and vectors, and keeps the fastest for (op, prec) in the handle.
@@ -587,8 +712,9 @@ extern "C" int ceed_autotune_apply(ceed_mesh_t m, int op, const void *qdata, int
   ApplyChoice best;
   best.ms = 1e30f;
   const int reps = 3;
-  for (int stage = 0; stage <= 1; ++stage) {
-    for (int ne = 1; ne <= ne_max; ne *= 2) {
+  const bool bricks = brick_ok(m, prec, r.ncol);
+  for (int stage = 0; stage <= (bricks ? 3 : 1); ++stage) {
+    for (int ne = 1; ne <= (stage >= 2 ? 1 : ne_max); ne *= 2) {  // the brick kernel has one shape
       r.ne = ne;
       r.stage = stage;
       if (launch_apply(m, r, s) != CEED_OK) continue;  // e.g. shared memory beyond the limit
@@ -621,8 +747,11 @@ extern "C" int ceed_set_apply_variant(ceed_mesh_t m, int op, int prec, int ne, i
   if (int st = check_mesh(m)) return st;
   if (op != CEED_OP_MASS && op != CEED_OP_DIFFUSION) return fail(CEED_ERR_INVALID, "unknown operator");
   if (prec < CEED_F64 || prec > CEED_F64_DF) return fail(CEED_ERR_INVALID, "unknown precision");
-  if (ne < 0 || ne > std::min(32, std::max(1, 256 / (m->Q * m->Q))) || (stage != 0 && stage != 1))
-    return fail(CEED_ERR_INVALID, "elements per block must be 0 (default) .. min(32, 256 / Q^2), stage 0 or 1");
+  if (ne < 0 || ne > std::min(32, std::max(1, 256 / (m->Q * m->Q))) || stage < 0 || stage > 3)
+    return fail(CEED_ERR_INVALID, "elements per block must be 0 (default) .. min(32, 256 / Q^2), stage 0 .. 3");
+  if (stage >= 2 && !brick_ok(m, prec, 1))
+    return fail(CEED_ERR_INVALID, "stage 2 and 3 (brick kernel) need a brick lattice and an FP32-pipe precision");
+  if (stage >= 2 && ne == 0) ne = 1;  // the brick kernel has one shape (ne = 0 would restore the default)
   m->tuned[op][prec].ne = ne;
   m->tuned[op][prec].stage = stage;
   m->tuned[op][prec].ms = 0.f;
