@@ -152,6 +152,7 @@ __device__ __forceinline__ void brick_block(const BrickArgs &a, const OpTab<T> &
   const int A = tid % RL;
   const int rbase = tid / RL;
   const bool a_ok = (A < NB) && (tid < RPASS * RL);
+  const bool mask = a.masked && (gf & BRICK_DIR);  // only bricks holding a Dirichlet node test the mask
 
   if constexpr (STAGE) {
     if (ij == 0) {
@@ -167,12 +168,27 @@ __device__ __forceinline__ void brick_block(const BrickArgs &a, const OpTab<T> &
   {
     double xv[NPASS];
     BrickRows<NB, RPASS> it(rbase, base + A, a.sy, a.sz);
+    if (mask) {  // mask bits and values loaded side by side, then the Dirichlet nodes zeroed
+      bool dz[NPASS];
 #pragma unroll
-    for (int r = 0; r < NPASS; ++r, it.next()) {
-      const int row = rbase + r * RPASS;
-      xv[r] = 0.0;
-      if (a_ok && row < ROWS && !(a.masked && brick_dir(a.dirbits, it.v)))
-        xv[r] = XCG ? __ldcg(a.x + it.v) : __ldg(a.x + it.v);
+      for (int r = 0; r < NPASS; ++r, it.next()) {
+        const int row = rbase + r * RPASS;
+        xv[r] = 0.0;
+        dz[r] = false;
+        if (a_ok && row < ROWS) {
+          xv[r] = XCG ? __ldcg(a.x + it.v) : __ldg(a.x + it.v);
+          dz[r] = brick_dir(a.dirbits, it.v);
+        }
+      }
+#pragma unroll
+      for (int r = 0; r < NPASS; ++r) xv[r] = dz[r] ? 0.0 : xv[r];
+    } else {
+#pragma unroll
+      for (int r = 0; r < NPASS; ++r, it.next()) {
+        const int row = rbase + r * RPASS;
+        xv[r] = 0.0;
+        if (a_ok && row < ROWS) xv[r] = XCG ? __ldcg(a.x + it.v) : __ldg(a.x + it.v);
+      }
     }
 #pragma unroll
     for (int r = 0; r < NPASS; ++r) {
@@ -241,7 +257,7 @@ __device__ __forceinline__ void brick_block(const BrickArgs &a, const OpTab<T> &
         const bool sz_ = (it.C == 0 && (gf & BRICK_MZ)) || (it.C == NBZ - 1 && (gf & BRICK_PZ));
         const bool first = !(sx && px) && !(sy_ && py) && !(sz_ && pz);
         const bool last = !(sx && !px) && !(sy_ && !py) && !(sz_ && !pz);
-        const bool dir = a.masked && brick_dir(a.dirbits, it.v);
+        const bool dir = mask && brick_dir(a.dirbits, it.v);
         fl[r] = (first ? 1u : 0u) | (last ? 2u : 0u) | (dir ? 4u : 0u) | 8u;
         if (!first && !dir) yold[r] = __ldcg(a.y + it.v);
       }

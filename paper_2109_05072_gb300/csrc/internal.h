@@ -26,6 +26,7 @@ constexpr uint32_t DOF_MASK = (1u << 29) - 1u;
 // when the brick's face at -x, +x, -y, +y, -z, +z touches another brick.
 constexpr uint32_t BRICK_MX = 1u << 3, BRICK_PX = 1u << 4, BRICK_MY = 1u << 5, BRICK_PY = 1u << 6;
 constexpr uint32_t BRICK_MZ = 1u << 7, BRICK_PZ = 1u << 8;
+constexpr uint32_t BRICK_DIR = 1u << 9;  // some node of the brick is a Dirichlet node
 // Elements of a brick along z (2 x 2 x BRICK_KZ elements per brick).  One layer: 2 x 2 x 2 bricks
 // read about 6% fewer nodes but fit half as many blocks per SM, and measured slower.
 constexpr int BRICK_KZ = 1;

@@ -378,6 +378,18 @@ static int detect_bricks(ceed_mesh_s *m, const std::vector<uint32_t> &map, const
           if (gy + 1 < Gy) f |= BRICK_PY;
           if (gz > 0) f |= BRICK_MZ;
           if (gz + 1 < Gz) f |= BRICK_PZ;
+          if (!dir.empty()) {  // does the brick hold a Dirichlet node?
+            const int64_t b0 = 2 * gx * p + 2 * gy * p * sy + BRICK_KZ * gz * p * sz;
+            bool any = false;
+            for (int64_t c = 0; c <= BRICK_KZ * p && !any; ++c)
+              for (int64_t b = 0; b <= 2 * p && !any; ++b)
+                for (int64_t a = 0; a <= 2 * p; ++a)
+                  if (dir[b0 + a + b * sy + c * sz]) {
+                    any = true;
+                    break;
+                  }
+            if (any) f |= BRICK_DIR;
+          }
           gflags.push_back(f);
         }
   }
