@@ -47,6 +47,10 @@ PROFILED_TRAFFIC_PER_LAUNCH = {
     "apply_kernel<8,8,DIFFUSION,double,double,stage=0>[ne=2]": 570.97e6 * 32768 / 13824,
     # profiles/df_apply_kernel_p7_48cube_ncu.md: 504.33 MB read + 68.59 MB written per 13,824-element launch
     "apply_kernel<8,8,DIFFUSION,DF,DF,stage=0>[ne=4]": 572.92e6 * 32768 / 13824,
+    # profiles/brick_kernel_p7_48cube_ncu.md: 279.28 MB read + 43.38 MB written per 3,456-brick launch
+    "brick_kernel<8,8,DIFFUSION,float,float,stage=0>": 322.66e6 * 32768 / 13824,
+    # same file, BF16 quadrature data: 193.56 MB read + 38.23 MB written
+    "brick_kernel<8,8,DIFFUSION,float,bf16,stage=0>": 231.79e6 * 32768 / 13824,
 }
 # DRAM bytes (read + write) of one launch of the tensor-core tetrahedral kernel on the 48^3 x 6
 # degree-4 workload (profiles/nt_tc_kernel_p4_tet48_ncu.md): 2143.84 MB read + 90.39 MB written
@@ -502,9 +506,15 @@ def compact_summary(line):
         out["df_gdofs"] = r(df["gdofs"])
         out["df_hbm_frac"] = r(df["roofline"]["frac"])
         out["df_rel_l2_vs_fp64"] = df["rel_l2_vs_fp64"]
+        if df.get("fp32_pipe_ceiling"):
+            out["df_ceiling_gdofs_dot2_16warps"] = r(df["fp32_pipe_ceiling"]["gdofs_at_dot2_rate_16warps"])
     for k, v in (line.get("mixed_apply") or {}).items():
         out[f"{k}_gdofs"] = r(v["gdofs"])
         out[f"{k}_hbm_frac"] = r(v["hbm_frac"])
+        if v.get("roofline"):
+            out[f"{k}_kernel"] = v["roofline"]["kernel"].split("<")[0]
+        if v.get("element_kernel_ms"):
+            out[f"{k}_element_kernel_gdofs"] = r(v["gdofs"] * v["ms"] / v["element_kernel_ms"])
     cg = line.get("cg") or {}
     if cg:
         f = cg.get("fp64_to_1e-10", {})
@@ -627,6 +637,11 @@ def main():
     for name, kind in (("f64", 0), ("f32", 1), ("f32x2", 2)):
         tf, per_clk, mhz = ceed.ceed_fma_throughput(kind)
         peaks[name] = {"tflops": tf, "fma_per_clk_per_sm": per_clk, "sm_mhz": mhz}
+    # the double-float operator's packed compensated sums (Dot2 steps) alone, at its occupancy (16
+    # warps per SM) and at 64: FP32 lane operations per clock per SM (the FMA pipe's peak is ~128)
+    for name, kind in (("dot2_16warps", 3), ("dot2_64warps", 4)):
+        tops, per_clk, mhz = ceed.ceed_fma_throughput(kind)
+        peaks[name] = {"tflops": tops, "lane_ops_per_clk_per_sm": per_clk, "sm_mhz": mhz}
 
     # ---------------- headline: FP64 apply (variant chosen by the library's autotuner first)
     variants = {}
@@ -676,6 +691,19 @@ def main():
                               "kernel": kid_df, "alg_bytes_per_launch": bytes64 / launches_per_apply,
                               "ms_per_launch": ms_df / launches_per_apply, "peak_kind": f"{hbm_kind} copy bandwidth",
                               "fp32_peak_tflops_measured": peaks["f32"]["tflops"]}}
+        # FP32-pipe ceiling: lane operations per element of the compensated passes (6 passes x P^2
+        # lines x 448 at P = 8, and 100 per point) at the rate measured for the bare Dot2 chains
+        if p == 7:
+            lane_ops_el = 6 * 64 * 448 + 512 * 100
+            dofs_el = m.n_ldof / m.n_elem
+            f64df["fp32_pipe_ceiling"] = {
+                "lane_ops_per_element": lane_ops_el,
+                "gdofs_at_fma_peak": peaks["f32"]["tflops"] * 1e12 / lane_ops_el * dofs_el / 1e9,
+                "gdofs_at_dot2_rate_16warps": peaks["dot2_16warps"]["tflops"] * 1e12 / lane_ops_el * dofs_el / 1e9,
+                "gdofs_at_dot2_rate_64warps": peaks["dot2_64warps"]["tflops"] * 1e12 / lane_ops_el * dofs_el / 1e9,
+                "note": "the operator's compensated arithmetic alone, at the measured rates of the FMA pipe and "
+                        "of bare packed Dot2 chains; HBM bound at 93 B/DOF for comparison: "
+                        f"{hbm_peak / 93.1:.1f} GDOF/s"}
         del qdf, ydf
         torch.cuda.empty_cache()
 
@@ -691,6 +719,22 @@ def main():
         by = algorithmic_bytes(m, qb, geo=(prec == ceed.CEED_F32_GEO))
         mixed[name] = {"gdofs": whole_job_rate(m.n_ldof, ws, ms), "ms": ms, "alg_bytes": by,
                        "hbm_gbs": by / (ms * 1e-3) / 1e9, "hbm_frac": by / (ms * 1e-3) / 1e9 / hbm_peak}
+        v = variants.get(name, {"elems_per_block": 0, "tma_staging": 1})
+        tq = {"f32": "float", "bf16": "bf16", "f32geo": "float,geo"}[name]
+        if v["tma_staging"] >= 2:   # the brick kernel (2 x 2 x 1 elements per block)
+            kid = f"brick_kernel<8,8,DIFFUSION,float,{tq},stage={v['tma_staging'] - 2}>"
+            # the element kernel on the same buffers, for comparison
+            ceed.ceed_set_apply_variant(mesh, ceed.CEED_OP_DIFFUSION, prec, 2, 1)
+            mixed[name]["element_kernel_ms"] = timed(lambda: ceed.ceed_apply_diffusion(mesh, qlo, prec, x, y),
+                                                     args.steps, args.warmup)
+            ceed.ceed_set_apply_variant(mesh, ceed.CEED_OP_DIFFUSION, prec, 1, v["tma_staging"])
+        else:
+            kid = f"apply_kernel<8,8,DIFFUSION,float,{tq},stage={v['tma_staging']}>[ne={v['elems_per_block']}]"
+        mixed[name]["roofline"] = {"bound": "hbm", "achieved": by / (ms * 1e-3) / 1e9, "peak": hbm_peak, "unit": "GB/s",
+                                   "frac": by / (ms * 1e-3) / 1e9 / hbm_peak,
+                                   "traffic": PROFILED_TRAFFIC_PER_LAUNCH.get(kid) if N == 64 else None,
+                                   "kernel": kid, "alg_bytes_per_launch": by / launches_per_apply,
+                                   "ms_per_launch": ms / launches_per_apply, "peak_kind": f"{hbm_kind} copy bandwidth"}
         del qlo
     torch.cuda.empty_cache()
 

@@ -530,7 +530,11 @@ int ceed_set_wait_limits(int64_t copy_polls, int64_t barrier_polls);
  * roofline denominators): kind 0 = FP64 FMA, 1 = FP32 FMA, 2 = packed two-lane FP32 FMA
  * (fma.rn.f32x2).  Runs independent FMA chains on every SM (64 warps per SM, about 50-100 ms per
  * run, best of three) on `stream` and returns TFLOP/s (2 flops per FMA), FMAs per clock per SM and
- * the SM clock in MHz seen by one block during the run (either pointer may be NULL).  Synchronizes
+ * the SM clock in MHz seen by one block during the run (either pointer may be NULL).  Kinds 3 and
+ * 4 run the double-float operator's packed compensated sums instead (4 independent Dot2
+ * accumulators per thread, each step a TwoProduct with cross terms and a TwoSum in two-lane form)
+ * at 16 warps per SM (that operator's occupancy) and 64; they return FP32 lane operations per second
+ * / 1e12 in *tflops and lane operations per clock per SM in *fma_per_clk_sm.  Synchronizes
  * `stream`.  Errors: INVALID, CUDA. */
 int ceed_fma_throughput(int kind, double *tflops, double *fma_per_clk_sm, double *sm_mhz, void *stream);
 

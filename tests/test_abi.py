@@ -126,4 +126,5 @@ def test_wait_limits_validated_on_the_host():
     assert ceed._lib.ceed_set_wait_limits(5, -1) == ceed.CEED_ERR_INVALID
     assert ceed._lib.ceed_set_wait_limits(-1, 1 << 26) == ceed.CEED_ERR_INVALID
     assert ceed._lib.ceed_set_wait_limits(-1, -1) == ceed.CEED_OK
-    assert ceed._lib.ceed_fma_throughput(3, None, None, None, None) == ceed.CEED_ERR_INVALID
+    assert ceed._lib.ceed_fma_throughput(5, None, None, None, None) == ceed.CEED_ERR_INVALID
+    assert ceed._lib.ceed_fma_throughput(-1, None, None, None, None) == ceed.CEED_ERR_INVALID

@@ -147,3 +147,8 @@ def test_fma_throughput_is_plausible(ceed):
     assert f32 > 10 * f64
     assert 300 < mhz64 < 3500 and 300 < mhz32 < 3500
     assert 0.5 < f32_clk <= 130 and 0.1 < f64_clk < 70
+    # the double-float operator's compensated sums: FP32 lane operations, at most the FMA pipe's rate
+    d16, d16_clk, _ = ceed.ceed_fma_throughput(3)
+    d64, d64_clk, _ = ceed.ceed_fma_throughput(4)
+    assert 1 < d16 <= 1.05 * 2 * f32x2 and 1 < d64 <= 1.05 * 2 * f32x2
+    assert 1 < d16_clk <= 1.05 * 2 * f32x2_clk and d16_clk <= 1.05 * d64_clk
