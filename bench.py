@@ -698,7 +698,7 @@ def main():
             dofs_el = m.n_ldof / m.n_elem
             f64df["fp32_pipe_ceiling"] = {
                 "lane_ops_per_element": lane_ops_el,
-                "gdofs_at_fma_peak": peaks["f32"]["tflops"] * 1e12 / lane_ops_el * dofs_el / 1e9,
+                "gdofs_at_fma_peak": peaks["f32"]["tflops"] * 1e12 / 2 / lane_ops_el * dofs_el / 1e9,
                 "gdofs_at_dot2_rate_16warps": peaks["dot2_16warps"]["tflops"] * 1e12 / lane_ops_el * dofs_el / 1e9,
                 "gdofs_at_dot2_rate_64warps": peaks["dot2_64warps"]["tflops"] * 1e12 / lane_ops_el * dofs_el / 1e9,
                 "note": "the operator's compensated arithmetic alone, at the measured rates of the FMA pipe and "

@@ -380,6 +380,7 @@ static int fused_batch(ceed_mesh_t m, const ApplyReq &op, double *y, const Work 
   g.r = w.r;
   g.p = w.p;
   g.q = w.q;
+  g.z = w.z;
   g.dinv = w.dinv;
   g.n = n;
   g.part = w.fpart;

@@ -9,8 +9,8 @@
 // scatter and the phases of the iteration.  Every reduction has a fixed order: each block adds its
 // share in a fixed sequence, and every block then sums the blocks' partials in block order itself,
 // so all blocks hold the same alpha and beta and take the same stopping decision without another
-// barrier.  Block 0 publishes the scalars for the host.  z = D^{-1} r is never stored: the p update
-// recomputes it from r and the Jacobi diagonal.
+// barrier.  Block 0 publishes the scalars for the host.  The update stores z = D^{-1} r for the p
+// update (as many bytes as reading r and D^{-1} there, one FP64 product less per entry).
 #pragma once
 
 #include "batch.cuh"
@@ -23,6 +23,7 @@ struct CgFusedArgs {
   int64_t cstart[CGF_MAX_COLORS + 1];        // colour-sorted element ranges
   int ncolors;
   double *x, *r, *p, *q;
+  double *z;                                 // z = D^{-1} r of the current iteration (written, read once)
   const double *dinv;
   int64_t n;
   double *part;                              // [3][gridDim]: p.q, r.z, r.r partials per block
@@ -121,7 +122,9 @@ __device__ __forceinline__ void cg_fused_body(const CgFusedArgs &g, const OpTab<
           g.x[kk] = xk[u] + alpha * pk[u];
           const double rn = rk[u] - alpha * qk[u];
           g.r[kk] = rn;
-          arz[u] += rn * (dk[u] * rn);
+          const double zn = dk[u] * rn;
+          g.z[kk] = zn;
+          arz[u] += rn * zn;
           arr[u] += rn * rn;
         }
       }
@@ -130,7 +133,9 @@ __device__ __forceinline__ void cg_fused_body(const CgFusedArgs &g, const OpTab<
         g.x[k] = __ldcg(g.x + k) + alpha * pk;
         const double rn = __ldcg(g.r + k) - alpha * __ldcg(g.q + k);
         g.r[k] = rn;
-        arz[0] += rn * (__ldg(g.dinv + k) * rn);
+        const double zn = __ldg(g.dinv + k) * rn;
+        g.z[k] = zn;
+        arz[0] += rn * zn;
         arr[0] += rn * rn;
       }
     }
@@ -162,21 +167,22 @@ __device__ __forceinline__ void cg_fused_body(const CgFusedArgs &g, const OpTab<
       sc->beta = beta;
       sc->rz = rz;
     }
-    // ---- p = D^{-1} r + beta p
+    // ---- p = z + beta p (z = D^{-1} r stored by the update: one FP64 FMA here instead of a product
+    // and an FMA, at the same traffic -- z is written once and read once instead of reading r and
+    // D^{-1}; GB300's FP64 pipe, not only HBM, bounds these streaming phases)
     {
       int64_t k = (int64_t)blockIdx.x * blockDim.x + tid;
       for (; k + 3 * stride < g.n; k += 4 * stride) {
-        double rk[4], pk[4], dk[4];
+        double zk[4], pk[4];
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
-          rk[u] = __ldcg(g.r + k + u * stride);
+          zk[u] = __ldcg(g.z + k + u * stride);
           pk[u] = __ldcg(g.p + k + u * stride);
-          dk[u] = __ldg(g.dinv + k + u * stride);
         }
 #pragma unroll
-        for (int u = 0; u < 4; ++u) g.p[k + u * stride] = dk[u] * rk[u] + beta * pk[u];
+        for (int u = 0; u < 4; ++u) g.p[k + u * stride] = fma(beta, pk[u], zk[u]);
       }
-      for (; k < g.n; k += stride) g.p[k] = __ldg(g.dinv + k) * __ldcg(g.r + k) + beta * __ldcg(g.p + k);
+      for (; k < g.n; k += stride) g.p[k] = fma(beta, __ldcg(g.p + k), __ldcg(g.z + k));
     }
     if (!grid_barrier(g.sync, &sc->timeout, g.grid_wait, &ok_sh)) return;
   }
