@@ -41,11 +41,17 @@ FP64_NOMINAL_TFLOPS = 1.25      # GB300 dense FP64 (nominal table), reported bes
 # current kernel on the 48^3 mesh (13,824 elements per colour launch), scaled by elements to a 64^3
 # colour launch (32,768 elements); keyed by variant, empty until a capture of the current kernel.
 PROFILED_TRAFFIC_PER_LAUNCH = {
-    # profiles/apply_kernel_p7_48cube_ncu.md: 503.70 MB read + 66.40 MB written per 13,824-element launch
-    "apply_kernel<8,8,DIFFUSION,double,double,stage=0>[ne=1]": 570.09e6 * 32768 / 13824,
-    # same file: 503.84 MB read + 67.13 MB written per 13,824-element launch
-    "apply_kernel<8,8,DIFFUSION,double,double,stage=0>[ne=2]": 570.97e6 * 32768 / 13824,
-    # profiles/df_apply_kernel_p7_48cube_ncu.md: 504.33 MB read + 68.59 MB written per 13,824-element launch
+    # DRAM bytes (read + write) of one colour launch at 48^3 (13,824 elements), scaled by elements to
+    # a 64^3 launch (32,768): profiles/apply_kernel_variants_traffic_p7_48cube.md
+    "apply_kernel<8,8,DIFFUSION,double,double,stage=0>[ne=1]": 622.10e6 * 32768 / 13824,
+    "apply_kernel<8,8,DIFFUSION,double,double,stage=0>[ne=2]": 618.94e6 * 32768 / 13824,
+    "apply_kernel<8,8,DIFFUSION,double,double,stage=0>[ne=4]": 614.67e6 * 32768 / 13824,
+    "apply_kernel<8,8,DIFFUSION,double,double,stage=1>[ne=1]": 570.23e6 * 32768 / 13824,
+    "apply_kernel<8,8,DIFFUSION,double,double,stage=1>[ne=2]": 570.97e6 * 32768 / 13824,
+    "apply_kernel<8,8,DIFFUSION,double,double,stage=1>[ne=4]": 571.53e6 * 32768 / 13824,
+    "apply_kernel<8,8,DIFFUSION,DF,DF,stage=0>[ne=1]": 570.61e6 * 32768 / 13824,
+    "apply_kernel<8,8,DIFFUSION,DF,DF,stage=0>[ne=2]": 570.52e6 * 32768 / 13824,
+    # profiles/df_apply_kernel_p7_48cube_ncu.md: 504.33 MB read + 68.59 MB written
     "apply_kernel<8,8,DIFFUSION,DF,DF,stage=0>[ne=4]": 572.92e6 * 32768 / 13824,
     # profiles/brick_kernel_p7_48cube_ncu.md: 279.28 MB read + 43.38 MB written per 3,456-brick launch
     "brick_kernel<8,8,DIFFUSION,float,float,stage=0>": 322.66e6 * 32768 / 13824,
