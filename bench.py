@@ -37,9 +37,9 @@ import synthetic  # noqa: E402
 
 METRIC = "diffusion apply GDOF/s at p=7 (FP64 vs mixed), % HBM roofline, CG time-to-1e-10"
 FP64_NOMINAL_TFLOPS = 1.25      # GB300 dense FP64 (nominal table), reported beside the measured peak
-# DRAM bytes (read + write) per launch of the FP64 apply kernel variant, from one ncu capture of the
-# current kernel on the 48^3 mesh (13,824 elements per colour launch), scaled by elements to a 64^3
-# colour launch (32,768 elements); keyed by variant, empty until a capture of the current kernel.
+# DRAM bytes (read + write) per launch of each apply kernel variant, from ncu captures of the current
+# kernels on the 48^3 mesh, scaled by elements to a 64^3 colour launch; keyed by kernel and variant
+# (a variant without a capture reports null).
 PROFILED_TRAFFIC_PER_LAUNCH = {
     # DRAM bytes (read + write) of one colour launch at 48^3 (13,824 elements), scaled by elements to
     # a 64^3 launch (32,768): profiles/apply_kernel_variants_traffic_p7_48cube.md
