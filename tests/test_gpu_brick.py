@@ -184,3 +184,30 @@ def test_brick_cg_separate_kernels(ceed):
         xs.append(x.cpu().numpy())
     assert rel_err(xs[0], xs[1]) <= 1e-8
     mesh.close()
+
+
+def test_brick_copy_wait_expiry_then_recovery(ceed):
+    # the staged brick variant waits (bounded) for its quadrature-data copies: with the wait limit at
+    # zero it gives up at once, writes nothing, reports CEED_ERR_TIMEOUT and leaves no hung GPU;
+    # the next apply with the default limit is correct
+    m = synthetic.HexMesh(4, 2, 3, 3, seed=60)
+    mesh = gpu_mesh(ceed, m, "gll")
+    qd = _qdata(ceed, mesh, ceed.CEED_OP_DIFFUSION, ceed.CEED_F32)
+    x = torch.from_numpy(synthetic.uniform(m.n_ldof, seed=61)).cuda()
+    _variant(ceed, mesh, ceed.CEED_OP_DIFFUSION, ceed.CEED_F32, 3)
+    y = torch.zeros_like(x)
+    ceed.ceed_set_wait_limits(0, -1)
+    try:
+        ceed.ceed_apply_diffusion(mesh, qd, ceed.CEED_F32, x, y)
+        with pytest.raises(ceed.CeedError) as ei:
+            ceed.ceed_mesh_status(mesh)
+        assert ei.value.status == ceed.CEED_ERR_TIMEOUT
+    finally:
+        ceed.ceed_set_wait_limits(-1, -1)
+    ceed.ceed_mesh_status(mesh)
+    y = _run(ceed, mesh, ceed.CEED_OP_DIFFUSION, qd, ceed.CEED_F32, x)
+    ceed.ceed_mesh_status(mesh)
+    sp_, qref = oracle_qdata(m, "gll", "diffusion", "sine")
+    ref = fem.apply(sp_, m.elem_dofs, qref, x.cpu().numpy(), fem.DIFFUSION)
+    assert rel_err(y.cpu().numpy(), ref) <= 64 * 4 * EPS32
+    mesh.close()
