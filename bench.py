@@ -492,7 +492,7 @@ def run_hp(ceed, dev, args):
     y = torch.empty_like(x)
     out = {"workload": f"orders 3/5/7 in x-slabs of {nx}x{ny}x{nz} hexahedra, Gauss q=p+2, conforming (minimum rule)",
            "n_true": h.n_true, "n_elem_nodes": h.n_rows, "setup_s": setup_s, "runs": []}
-    for name, prec in (("f64", ceed.CEED_F64), ("f32", ceed.CEED_F32)):
+    for name, prec in (("f64", ceed.CEED_F64), ("f64df", ceed.CEED_F64_DF), ("f32", ceed.CEED_F32)):
         ceed.ceed_hp_build_qdata(h, ceed.CEED_OP_DIFFUSION, ceed.CEED_COEFF_SINE, prec=prec)
         ms = _time_cuda(lambda: ceed.ceed_hp_apply(h, ceed.CEED_OP_DIFFUSION, prec, x, y,
                                                    flags=ceed.CEED_APPLY_DIRICHLET), 5, 3)

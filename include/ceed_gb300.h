@@ -472,8 +472,9 @@ int ceed_hp_setup(const ceed_hp_desc *desc, ceed_hp_t *out, void *stream);
 int ceed_hp_destroy(ceed_hp_t h);
 /* Number of true dofs, of element-node rows, of order groups. */
 int ceed_hp_info(ceed_hp_t h, int64_t *n_true, int64_t *n_rows, int32_t *n_groups);
-/* Quadrature data of every order group (handle-owned) for (op, prec F64 or F32); coefficients ONE,
- * CONST or SINE.  Synchronizes `stream`. */
+/* Quadrature data of every order group (handle-owned) for (op, prec F64, F32 or F64_DF: the
+ * FP64-accurate double-float element kernels); coefficients ONE, CONST or SINE.  Synchronizes
+ * `stream`. */
 int ceed_hp_build_qdata(ceed_hp_t h, int op, int coeff_kind, const double *coeff, int prec, void *stream);
 /* Element vectors u_elem = P x (device FP64 [n_rows]); asynchronous. */
 int ceed_hp_prolong(ceed_hp_t h, const double *x, double *u_elem, void *stream);

@@ -38,7 +38,7 @@ struct ceed_hp_s {
     int p = 0;
     int64_t n_elem = 0, row0 = 0;     // element count, first E-vector row
     ceed_mesh_t mesh = nullptr;       // identity restriction over the group's element vectors
-    void *qdata[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};   // [op][prec: F64, F32]
+    void *qdata[2][3] = {{nullptr, nullptr, nullptr}, {nullptr, nullptr, nullptr}};  // [op][prec: F64, F32, F64_DF]
   };
   std::vector<Group> groups;
   int64_t *d_prow = nullptr;     // CSR of P: [n_rows + 1]
@@ -327,7 +327,7 @@ struct HpFree {
     for (auto &g : h->groups) {
       if (g.mesh) ceed_destroy_mesh(g.mesh);
       for (int a = 0; a < 2; ++a)
-        for (int b = 0; b < 2; ++b) cudaFree(g.qdata[a][b]);
+        for (int b = 0; b < 3; ++b) cudaFree(g.qdata[a][b]);
     }
     cudaFree(h->d_prow);
     cudaFree(h->d_pcol);
@@ -560,15 +560,19 @@ extern "C" int ceed_hp_info(ceed_hp_t h, int64_t *n_true, int64_t *n_rows, int32
 static int hp_check(ceed_hp_t h, int op, int prec) {
   if (!h) return fail(CEED_ERR_INVALID, "null hp handle");
   if (op != CEED_OP_MASS && op != CEED_OP_DIFFUSION) return fail(CEED_ERR_INVALID, "op must be MASS or DIFFUSION");
-  if (prec != CEED_F64 && prec != CEED_F32) return fail(CEED_ERR_UNSUPPORTED, "hp operator: prec F64 or F32");
+  if (prec != CEED_F64 && prec != CEED_F32 && prec != CEED_F64_DF)
+    return fail(CEED_ERR_UNSUPPORTED, "hp operator: prec F64, F32 or F64_DF");
   return CEED_OK;
 }
+
+// index of a precision in the groups' quadrature-data slots
+static int hp_slot(int prec) { return prec == CEED_F64 ? 0 : prec == CEED_F32 ? 1 : 2; }
 
 extern "C" int ceed_hp_build_qdata(ceed_hp_t h, int op, int coeff_kind, const double *coeff, int prec, void *stream) {
   int st = hp_check(h, op, prec);
   if (st != CEED_OK) return st;
   if (coeff_kind == CEED_COEFF_PER_QPT) return fail(CEED_ERR_UNSUPPORTED, "hp operator: per-point coefficients");
-  const int pi = prec == CEED_F64 ? 0 : 1;
+  const int pi = hp_slot(prec);
   for (auto &g : h->groups) {
     if (!g.qdata[op][pi]) {
       const size_t bytes = ceed_qdata_bytes(g.mesh, op, prec);
@@ -592,7 +596,7 @@ extern "C" int ceed_hp_apply(ceed_hp_t h, int op, int prec, const double *x, dou
   int st = hp_check(h, op, prec);
   if (st != CEED_OK) return st;
   if (!x || !y || x == y) return fail(CEED_ERR_INVALID, "null or overlapping x, y");
-  const int pi = prec == CEED_F64 ? 0 : 1;
+  const int pi = hp_slot(prec);
   for (auto &g : h->groups)
     if (!g.qdata[op][pi]) return fail(CEED_ERR_INVALID, "hp operator: quadrature data not built for this op/prec");
   const int masked = (flags & CEED_APPLY_DIRICHLET) && h->dirichlet;

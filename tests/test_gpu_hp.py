@@ -60,19 +60,22 @@ def test_prolongation_matches_oracle(ceed, seed):
 CASES = [("diffusion", "gll", True), ("diffusion", "gauss", False), ("mass", "gauss", False), ("mass", "gll", True)]
 
 
+@pytest.mark.parametrize("prec", ["f64", "f64df"])
 @pytest.mark.parametrize("op,qkind,masked", CASES)
-def test_apply_matches_oracle(ceed, op, qkind, masked):
+def test_apply_matches_oracle(ceed, op, qkind, masked, prec):
+    # FP64 and the FP64-accurate double-float element kernels: both within 1e-12 of the oracle
     nx, ny, nz = 3, 2, 2
     orders = np.random.default_rng(7).choice([2, 3, 4, 5, 6], size=nx * ny * nz)
     m = synthetic.HexMesh(nx, ny, nz, 1, seed=2)
     h = hpo.HpSpace(nx, ny, nz, orders)
     g = _gpu_hp(ceed, nx, ny, nz, orders, m.vertices, qkind)
     cop = ceed.CEED_OP_DIFFUSION if op == "diffusion" else ceed.CEED_OP_MASS
-    ceed.ceed_hp_build_qdata(g, cop, ceed.CEED_COEFF_SINE, prec=ceed.CEED_F64)
+    cprec = ceed.CEED_F64 if prec == "f64" else ceed.CEED_F64_DF
+    ceed.ceed_hp_build_qdata(g, cop, ceed.CEED_COEFF_SINE, prec=cprec)
     x = synthetic.uniform(h.n_true, seed=11)
     xd = torch.from_numpy(x).cuda()
     yd = torch.empty_like(xd)
-    ceed.ceed_hp_apply(g, cop, ceed.CEED_F64, xd, yd, flags=ceed.CEED_APPLY_DIRICHLET if masked else 0)
+    ceed.ceed_hp_apply(g, cop, cprec, xd, yd, flags=ceed.CEED_APPLY_DIRICHLET if masked else 0)
     torch.cuda.synchronize()
     f = hpo.operator(h, m.vertices, qkind, fem.DIFFUSION if op == "diffusion" else fem.MASS, "sine")
     ref = fem.masked(f, h.boundary_mask())(x) if masked else f(x)
@@ -90,7 +93,7 @@ def test_orders_357_slabs_and_fp32(ceed):
     x = synthetic.uniform(h.n_true, seed=12)
     xd = torch.from_numpy(x).cuda()
     ref = fem.masked(hpo.operator(h, m.vertices, "gauss", fem.DIFFUSION, "sine"), h.boundary_mask())(x)
-    for prec, tol in ((ceed.CEED_F64, 1e-12), (ceed.CEED_F32, 2e-5)):
+    for prec, tol in ((ceed.CEED_F64, 1e-12), (ceed.CEED_F64_DF, 1e-12), (ceed.CEED_F32, 2e-5)):
         ceed.ceed_hp_build_qdata(g, ceed.CEED_OP_DIFFUSION, ceed.CEED_COEFF_SINE, prec=prec)
         yd = torch.empty_like(xd)
         ceed.ceed_hp_apply(g, ceed.CEED_OP_DIFFUSION, prec, xd, yd, flags=ceed.CEED_APPLY_DIRICHLET)
