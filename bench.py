@@ -443,13 +443,15 @@ def run_nontensor(ceed, dev, args):
                        f"conical rule q={q}", "n_elem": E, "n_ldof": m.n_ldof, "P": P, "Q": Q,
            "flops_per_apply": flops, "runs": []}
     hbm_peak, _ = load_peaks()
-    for prec, name, tb in ((ceed.CEED_F64, "f64", 8), (ceed.CEED_F32, "f32", 4)):
+    for prec, name, tb in ((ceed.CEED_F64, "f64", 8), (ceed.CEED_F64_DF, "f64df", 8), (ceed.CEED_F32, "f32", 4)):
         qd = ceed.alloc_nt_qdata(nt, ceed.CEED_OP_DIFFUSION, prec, dev)
         ceed.ceed_nt_build_qdata(nt, ceed.CEED_OP_DIFFUSION, ceed.CEED_COEFF_SINE, None, prec, qd)
         # algorithmic bytes: x and y once per node, the quadrature data, the int32 restriction
         by = 16 * m.n_ldof + 6 * Q * E * tb + 4 * P * E
         modes = [("fused", ceed.CEED_NT_FUSED, 0, 0), ("gemm_native", ceed.CEED_NT_GEMM, 0, 0),
                  ("gemm_emulated", ceed.CEED_NT_GEMM, 0, 1)]
+        if prec == ceed.CEED_F64_DF:   # FP64 accuracy on the FP32 pipe: the fused algorithm only
+            modes = modes[:1]
         if prec == ceed.CEED_F32:
             modes.append(("gemm_tf32", ceed.CEED_NT_GEMM, 0, 2))
             modes.append(("tensor_core_3xtf32", ceed.CEED_NT_TC, 0, 0))

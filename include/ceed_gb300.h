@@ -376,6 +376,8 @@ int ceed_apply_diffusion_adjoint(ceed_mesh_t mesh, const double *k, const void *
  *                  the tensor cores (tcgen05): tiles of 128 elements, both basis actions as TF32 matrix
  *                  products with FP32-level accuracy from the three-product split
  *                  a b ~ a_hi b_hi + a_hi b_lo + a_lo b_hi, the pointwise D on the CUDA cores between them.
+ * Precisions: F64, F32 and F64_DF (FP64-accurate on the FP32 pipe: values, tables and quadrature
+ * data as double-float pairs, every sum a compensated dot product; FUSED only).
  * All finish with a deterministic transposed restriction (every node sums its element entries in
  * a fixed order).  The handle owns its tables, an element-vector buffer [P][E] and, once the GEMM
  * algorithm has been selected or tuned, two GEMM work arrays ([P][E] and [3 Q][E] doubles). */
@@ -410,7 +412,7 @@ int ceed_simplex_basis(int p, int q, double *interp, double *grad, double *qweig
  * Synchronizes `stream`.  Errors: INVALID, OOM, CUDA. */
 int ceed_nt_setup(const ceed_nt_desc *desc, ceed_nt_t *out, void *stream);
 int ceed_nt_destroy(ceed_nt_t h);
-/* Quadrature-data bytes for (op, prec F64 or F32); layout [ncomp][Q][E] (element fastest). */
+/* Quadrature-data bytes for (op, prec F64, F32 or F64_DF); layout [ncomp][Q][E] (element fastest). */
 size_t ceed_nt_qdata_bytes(ceed_nt_t h, int op, int prec);
 /* Quadrature data of the affine simplices (coefficients as for ceed_build_qdata; PER_QPT is
  * [E][Q]).  Synchronizes; BAD_GEOMETRY if det J <= 0 in some element. */

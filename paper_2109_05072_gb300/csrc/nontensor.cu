@@ -166,6 +166,12 @@ template <>
 __device__ __forceinline__ double nt_cvt<double>(double v) { return v; }
 template <>
 __device__ __forceinline__ float nt_cvt<float>(double v) { return (float)v; }
+template <>
+__device__ __forceinline__ DF nt_cvt<DF>(double v) { return df_from_double(v); }
+
+__device__ __forceinline__ double nt_to_double(double v) { return v; }
+__device__ __forceinline__ double nt_to_double(float v) { return (double)v; }
+__device__ __forceinline__ double nt_to_double(DF v) { return (double)v.hi + (double)v.lo; }
 
 // Quadrature data of the affine simplex map x = v0 + J xi (J columns v1-v0, v2-v0, v3-v0): mass
 // w |det J| rho, diffusion w k adj(J) adj(J)^T / det J.  One thread per (point, element).
@@ -359,8 +365,115 @@ __global__ void nt_assemble_kernel(int64_t n, const int64_t *__restrict__ off, c
     return;
   }
   double acc = 0.0;
-  for (int64_t k = off[i]; k < off[i + 1]; ++k) acc += (double)Ye[pos[k]];
+  for (int64_t k = off[i]; k < off[i + 1]; ++k) acc += nt_to_double(Ye[pos[k]]);
   y[i] = acc;
+}
+
+// The fused kernel with FP64 accuracy on the FP32 pipe: values and tables as double-float pairs, every
+// contraction and the pointwise products as compensated dot products (Dot2, df.cuh), the same data
+// flow as nt_fused_kernel.  The forward sums run as two Dot2 chains (even and odd basis functions)
+// joined by a double-float addition; the transposed sums accumulate in one Dot2 chain per node.
+template <int D>
+__global__ void __launch_bounds__(NT_NE * NT_WARPS)
+    nt_fused_df_kernel(int64_t E, int64_t Es, int P, int Q, const uint32_t *__restrict__ rmap,
+                       const double *__restrict__ x, const DF *__restrict__ tab, const DF *__restrict__ qd,
+                       DF *__restrict__ Ye, int masked) {
+  extern __shared__ __align__(16) unsigned char nt_smem[];
+  DF *Us = reinterpret_cast<DF *>(nt_smem);  // [P][NT_NE]
+  DF *Gc = Us + P * NT_NE;                     // [D][NT_QC][P]
+  DF *Sv = Gc + D * NT_QC * P;                 // [D NT_QC][NT_NE + 1]
+  constexpr int LD = NT_NE + 1;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int64_t e = (int64_t)blockIdx.x * NT_NE + lane;
+  const bool valid = e < E;
+  for (int n = warp; n < P; n += NT_WARPS) {
+    DF v(0.f, 0.f);
+    if (valid) {
+      const uint32_t m = rmap[(int64_t)n * E + e];
+      if (!(masked && (m & FLAG_DIR))) v = nt_cvt<DF>(x[m & DOF_MASK]);
+    }
+    Us[n * NT_NE + lane] = v;
+  }
+  DFAcc yr[NT_YR];
+#pragma unroll
+  for (int j = 0; j < NT_YR; ++j) yr[j] = DFAcc{0.f, 0.f};
+  const int64_t cs = (int64_t)Q * Es;
+  for (int q0 = 0; q0 < Q; q0 += NT_QC) {
+    const int qc = min(NT_QC, Q - q0);
+    __syncthreads();
+    for (int i = threadIdx.x; i < D * qc * P; i += NT_NE * NT_WARPS) {
+      const int d = i / (qc * P), r = i - d * qc * P;
+      Gc[d * NT_QC * P + r] = tab[((int64_t)d * Q + q0) * P + r];
+    }
+    __syncthreads();
+    for (int r = warp; r < D * NT_QC; r += NT_WARPS) {
+      if (r % NT_QC >= qc) continue;
+      const DF *g = Gc + r * P;
+      DFAcc a0 = acc_first(g[0], Us[lane]);
+      DFAcc a1{0.f, 0.f};
+      int n = 1;
+      if (P > 1) {
+        a1 = acc_first(g[1], Us[NT_NE + lane]);
+        for (n = 2; n + 1 < P; n += 2) {
+          acc_mac(a0, g[n], Us[n * NT_NE + lane]);
+          acc_mac(a1, g[n + 1], Us[(n + 1) * NT_NE + lane]);
+        }
+      }
+      if (n < P) acc_mac(a0, g[n], Us[n * NT_NE + lane]);
+      Sv[r * LD + lane] = df_add(acc_get(a0), acc_get(a1));
+    }
+    __syncthreads();
+    for (int q = warp; q < qc; q += NT_WARPS) {
+      DF g[D];
+#pragma unroll
+      for (int d = 0; d < D; ++d) g[d] = Sv[(d * NT_QC + q) * LD + lane];
+      if (valid) {
+        const DF *c = qd + (int64_t)(q0 + q) * Es + e;
+        if (D == 1) {
+          g[0] = acc_get(acc_first(c[0], g[0]));
+        } else {
+          const DF c0 = c[0], c1 = c[cs], c2 = c[2 * cs], c3 = c[3 * cs], c4 = c[4 * cs], c5 = c[5 * cs];
+          const DF g0 = g[0], g1 = g[1], g2 = g[2];
+          DFAcc A = acc_first(c0, g0), B = acc_first(c1, g0), C = acc_first(c2, g0);
+          acc_mac(A, c1, g1);
+          acc_mac(B, c3, g1);
+          acc_mac(C, c4, g1);
+          acc_mac(A, c2, g2);
+          acc_mac(B, c4, g2);
+          acc_mac(C, c5, g2);
+          g[0] = acc_get(A);
+          g[1] = acc_get(B);
+          g[2] = acc_get(C);
+        }
+      } else {
+#pragma unroll
+        for (int d = 0; d < D; ++d) g[d] = DF(0.f, 0.f);
+      }
+#pragma unroll
+      for (int d = 0; d < D; ++d) Sv[(d * NT_QC + q) * LD + lane] = g[d];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int j = 0; j < NT_YR; ++j) {
+      const int n = warp + NT_WARPS * j;
+      if (n < P) {
+        DFAcc acc = yr[j];
+        for (int d = 0; d < D; ++d) {
+          const DF *g = Gc + d * NT_QC * P + n;
+          const DF *sv = Sv + d * NT_QC * LD + lane;
+          for (int q = 0; q < qc; ++q) acc_mac(acc, g[q * P], sv[q * LD]);
+        }
+        yr[j] = acc;
+      }
+    }
+  }
+  if (valid) {
+#pragma unroll
+    for (int j = 0; j < NT_YR; ++j) {
+      const int n = warp + NT_WARPS * j;
+      if (n < P) Ye[(int64_t)n * E + e] = acc_get(yr[j]);
+    }
+  }
 }
 
 static size_t nt_fused_smem(int P, int D, size_t tsize) {
@@ -473,6 +586,25 @@ static int nt_apply(ceed_nt_t h, int op, const void *qdata, int prec, const doub
     return op == CEED_OP_MASS ? nt_apply_t<double, 1>(h, c, tab, qd, x, y, masked, s)
                               : nt_apply_t<double, 3>(h, c, tab, qd, x, y, masked, s);
   }
+  if (prec == CEED_F64_DF) {  // the fused double-float kernel (the only algorithm of this precision)
+    const DF *tab = h->d_tabdf + tab_off;
+    const DF *qd = static_cast<const DF *>(qdata);
+    DF *Ye = reinterpret_cast<DF *>(h->d_evec);
+    const int D = op == CEED_OP_MASS ? 1 : 3;
+    const size_t sm = nt_fused_smem(h->P, D, sizeof(DF));
+    const void *kfn = D == 1 ? (const void *)nt_fused_df_kernel<1> : (const void *)nt_fused_df_kernel<3>;
+    if (int st = ensure_dynamic_smem(kfn, 227 * 1024)) return st;
+    const unsigned grid = (unsigned)((h->E + NT_NE - 1) / NT_NE);
+    if (D == 1)
+      nt_fused_df_kernel<1><<<grid, NT_NE * NT_WARPS, sm, s>>>(h->E, h->Es, h->P, h->Q, h->d_rmap, x, tab, qd, Ye, masked);
+    else
+      nt_fused_df_kernel<3><<<grid, NT_NE * NT_WARPS, sm, s>>>(h->E, h->Es, h->P, h->Q, h->d_rmap, x, tab, qd, Ye, masked);
+    CEED_CUDA_CHECK(cudaGetLastError());
+    nt_assemble_kernel<DF><<<(unsigned)((h->n_ldof + 255) / 256), 256, 0, s>>>(h->n_ldof, h->d_off, h->d_pos, Ye,
+                                                                                h->d_dir, x, y, masked);
+    CEED_CUDA_CHECK(cudaGetLastError());
+    return CEED_OK;
+  }
   const float *tab = h->d_tab32 + tab_off;
   const float *qd = static_cast<const float *>(qdata);
   return op == CEED_OP_MASS ? nt_apply_t<float, 1>(h, c, tab, qd, x, y, masked, s)
@@ -482,9 +614,13 @@ static int nt_apply(ceed_nt_t h, int op, const void *qdata, int prec, const doub
 static int nt_check(ceed_nt_t h, int op, int prec) {
   if (!h) return fail(CEED_ERR_INVALID, "null non-tensor operator handle");
   if (op != CEED_OP_MASS && op != CEED_OP_DIFFUSION) return fail(CEED_ERR_INVALID, "op must be MASS or DIFFUSION");
-  if (prec != CEED_F64 && prec != CEED_F32) return fail(CEED_ERR_UNSUPPORTED, "non-tensor operator: prec F64 or F32");
+  if (prec != CEED_F64 && prec != CEED_F32 && prec != CEED_F64_DF)
+    return fail(CEED_ERR_UNSUPPORTED, "non-tensor operator: prec F64, F32 or F64_DF");
   return CEED_OK;
 }
+
+// slot of a precision in the handle's algorithm choices
+static int nt_slot(int prec) { return prec == CEED_F64 ? 0 : prec == CEED_F32 ? 1 : 2; }
 
 }  // namespace ceedgb
 
@@ -495,6 +631,7 @@ struct NtFree {
     if (h->blas) cublasDestroy(h->blas);
     cudaFree(h->d_tab64);
     cudaFree(h->d_tab32);
+    cudaFree(h->d_tabdf);
     cudaFree(h->d_qw);
     cudaFree(h->d_qref);
     cudaFree(h->d_rmap);
@@ -595,9 +732,12 @@ extern "C" int ceed_nt_setup(const ceed_nt_desc *desc, ceed_nt_t *out, void *str
   for (size_t i = 0; i < (size_t)Q * P; ++i) tab64[i] = desc->interp[i];
   for (size_t i = 0; i < (size_t)3 * Q * P; ++i) tab64[(size_t)Q * P + i] = desc->grad[i];
   for (size_t i = 0; i < tab64.size(); ++i) tab32[i] = (float)tab64[i];
+  std::vector<DF> tabdf(tab64.size());
+  for (size_t i = 0; i < tab64.size(); ++i) tabdf[i] = df_from_double(tab64[i]);
 
   CEED_CUDA_CHECK(cudaMalloc(&h->d_tab64, tab64.size() * 8));
   CEED_CUDA_CHECK(cudaMalloc(&h->d_tab32, tab32.size() * 4));
+  CEED_CUDA_CHECK(cudaMalloc(&h->d_tabdf, tabdf.size() * sizeof(DF)));
   CEED_CUDA_CHECK(cudaMalloc(&h->d_qw, (size_t)Q * 8));
   CEED_CUDA_CHECK(cudaMalloc(&h->d_qref, (size_t)Q * 24));
   CEED_CUDA_CHECK(cudaMalloc(&h->d_rmap, rmap.size() * 4));
@@ -609,6 +749,7 @@ extern "C" int ceed_nt_setup(const ceed_nt_desc *desc, ceed_nt_t *out, void *str
   CEED_CUDA_CHECK(cudaMalloc(&h->d_evec, (size_t)P * E * 8));
   CEED_CUDA_CHECK(cudaMemcpyAsync(h->d_tab64, tab64.data(), tab64.size() * 8, cudaMemcpyHostToDevice, s));
   CEED_CUDA_CHECK(cudaMemcpyAsync(h->d_tab32, tab32.data(), tab32.size() * 4, cudaMemcpyHostToDevice, s));
+  CEED_CUDA_CHECK(cudaMemcpyAsync(h->d_tabdf, tabdf.data(), tabdf.size() * sizeof(DF), cudaMemcpyHostToDevice, s));
   CEED_CUDA_CHECK(cudaMemcpyAsync(h->d_qw, desc->qweight, (size_t)Q * 8, cudaMemcpyHostToDevice, s));
   CEED_CUDA_CHECK(cudaMemcpyAsync(h->d_qref, desc->qref, (size_t)Q * 24, cudaMemcpyHostToDevice, s));
   CEED_CUDA_CHECK(cudaMemcpyAsync(h->d_rmap, rmap.data(), rmap.size() * 4, cudaMemcpyHostToDevice, s));
@@ -639,7 +780,7 @@ extern "C" int ceed_nt_destroy(ceed_nt_t h) {
 
 extern "C" size_t ceed_nt_qdata_bytes(ceed_nt_t h, int op, int prec) {
   if (nt_check(h, op, prec) != CEED_OK) return 0;
-  return (size_t)(op == CEED_OP_MASS ? 1 : 6) * h->Q * h->Es * (prec == CEED_F64 ? 8 : 4);
+  return (size_t)(op == CEED_OP_MASS ? 1 : 6) * h->Q * h->Es * (prec == CEED_F32 ? 4 : 8);
 }
 
 extern "C" int ceed_nt_build_qdata(ceed_nt_t h, int op, int coeff_kind, const double *coeff, int prec, void *qdata,
@@ -663,6 +804,9 @@ extern "C" int ceed_nt_build_qdata(ceed_nt_t h, int op, int coeff_kind, const do
   if (prec == CEED_F64)
     nt_qdata_kernel<double><<<grid, 256, 0, s>>>(h->E, h->Es, h->Q, op, h->d_vert, h->d_qw, h->d_qref, coeff_kind, cconst,
                                                  coeff, static_cast<double *>(qdata), h->d_err);
+  else if (prec == CEED_F64_DF)
+    nt_qdata_kernel<DF><<<grid, 256, 0, s>>>(h->E, h->Es, h->Q, op, h->d_vert, h->d_qw, h->d_qref, coeff_kind, cconst,
+                                             coeff, static_cast<DF *>(qdata), h->d_err);
   else
     nt_qdata_kernel<float><<<grid, 256, 0, s>>>(h->E, h->Es, h->Q, op, h->d_vert, h->d_qw, h->d_qref, coeff_kind, cconst,
                                                 coeff, static_cast<float *>(qdata), h->d_err);
@@ -680,12 +824,14 @@ extern "C" int ceed_nt_apply(ceed_nt_t h, int op, const void *qdata, int prec, c
   if (st != CEED_OK) return st;
   if (!qdata || !x || !y) return fail(CEED_ERR_INVALID, "null qdata, x or y");
   if (x == y) return fail(CEED_ERR_INVALID, "x and y must not overlap");
-  return nt_apply(h, op, qdata, prec, x, y, flags, h->choice[op][prec == CEED_F64 ? 0 : 1], (cudaStream_t)stream);
+  return nt_apply(h, op, qdata, prec, x, y, flags, h->choice[op][nt_slot(prec)], (cudaStream_t)stream);
 }
 
 static int nt_check_choice(ceed_nt_t h, int prec, int algo, int64_t eta, int gemm_mode) {
   if (algo != CEED_NT_FUSED && algo != CEED_NT_GEMM && algo != CEED_NT_TC)
     return fail(CEED_ERR_INVALID, "algo must be FUSED, GEMM or TC");
+  if (prec == CEED_F64_DF && algo != CEED_NT_FUSED)
+    return fail(CEED_ERR_INVALID, "the double-float precision has the fused algorithm only");
   if (algo == CEED_NT_TC) {
     if (prec != CEED_F32) return fail(CEED_ERR_INVALID, "the tensor-core algorithm computes in FP32 (prec F32)");
     if (!nt_tc_supported(h->P)) return fail(CEED_ERR_UNSUPPORTED, "tensor-core algorithm: P must be 4, 10, 20, 35, 56 or 84");
@@ -704,7 +850,7 @@ extern "C" int ceed_nt_set_algorithm(ceed_nt_t h, int op, int prec, int algo, in
   if ((st = nt_check_choice(h, prec, algo, eta, gemm_mode)) != CEED_OK) return st;
   if (algo == CEED_NT_GEMM && (st = nt_ensure_gemm_workspace(h)) != CEED_OK) return st;
   if (algo == CEED_NT_TC && (st = nt_tc_prepare(h)) != CEED_OK) return st;
-  NtChoice &c = h->choice[op][prec == CEED_F64 ? 0 : 1];
+  NtChoice &c = h->choice[op][nt_slot(prec)];
   c.algo = algo;
   c.eta = algo == CEED_NT_GEMM ? eta : 0;
   c.gemm_mode = algo == CEED_NT_GEMM ? gemm_mode : 0;
@@ -716,7 +862,7 @@ extern "C" int ceed_nt_get_algorithm(ceed_nt_t h, int op, int prec, int32_t *alg
                                      float *ms) {
   int st = nt_check(h, op, prec);
   if (st != CEED_OK) return st;
-  const NtChoice &c = h->choice[op][prec == CEED_F64 ? 0 : 1];
+  const NtChoice &c = h->choice[op][nt_slot(prec)];
   if (algo) *algo = c.algo;
   if (eta) *eta = c.eta;
   if (gemm_mode) *gemm_mode = c.gemm_mode;
@@ -740,7 +886,8 @@ extern "C" int ceed_nt_autotune(ceed_nt_t h, int op, const void *qdata, int prec
     cand.push_back(c);
   }
   const int64_t etas[] = {0, 1024, 4096, 16384, 65536};
-  const int nmodes = (prec == CEED_F32 && include_tf32) ? 3 : 2;
+  // the double-float precision has the fused algorithm only
+  const int nmodes = prec == CEED_F64_DF ? 0 : (prec == CEED_F32 && include_tf32) ? 3 : 2;
   for (int mode = 0; mode < nmodes; ++mode)
     for (int64_t eta : etas) {
       if (eta != 0 && eta >= h->E) continue;
@@ -777,7 +924,7 @@ extern "C" int ceed_nt_autotune(ceed_nt_t h, int op, const void *qdata, int prec
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   if (st != CEED_OK) return st;
-  h->choice[op][prec == CEED_F64 ? 0 : 1] = best;
+  h->choice[op][nt_slot(prec)] = best;
   return CEED_OK;
 }
 

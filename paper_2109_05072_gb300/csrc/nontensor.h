@@ -31,6 +31,7 @@ struct ceed_nt_s {
   int P = 0, Q = 0;
   double *d_tab64 = nullptr;   // [4][Q][P]: interp, then grad along xi_1, xi_2, xi_3
   float *d_tab32 = nullptr;
+  ceedgb::DF *d_tabdf = nullptr;  // the same as double-float pairs (FP64-accurate fused kernel)
   double *d_qw = nullptr;      // [Q]
   double *d_qref = nullptr;    // [Q][3]
   uint32_t *d_rmap = nullptr;  // [P][E]
@@ -46,7 +47,7 @@ struct ceed_nt_s {
   float *d_tc_tab[2] = {nullptr, nullptr};  // tensor-core tables per op (mass, diffusion), see nontensor_tc.cu
   int tc_nchunk = 0;
   cublasHandle_t blas = nullptr;
-  ceedgb::NtChoice choice[2][2];  // [op][prec: 0 F64, 1 F32]
+  ceedgb::NtChoice choice[2][3];  // [op][prec: 0 F64, 1 F32, 2 F64_DF (fused only)]
 };
 
 namespace ceedgb {

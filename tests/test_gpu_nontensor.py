@@ -85,6 +85,25 @@ def test_fused_fp64_matches_oracle(ceed, p, op):
     nt.close()
 
 
+@pytest.mark.parametrize("p,op", CASES)
+def test_fused_double_float_matches_oracle(ceed, p, op):
+    # FP64 accuracy on the FP32 pipe (double-float values, tables and quadrature data; Dot2 sums):
+    # held to the FP64 bound against the oracle, and only the fused algorithm exists for it
+    m = synthetic.TetMesh(3, 2, 2, p, seed=p) if p <= 4 else synthetic.TetMesh(2, 2, 1, p, seed=p)
+    q = p + 1
+    nt = _setup(ceed, m, q)
+    qd = _qdata(ceed, nt, op, ceed.CEED_F64_DF)
+    x = synthetic.uniform(m.n_ldof, seed=20 + p)
+    y = _apply(ceed, nt, op, qd, ceed.CEED_F64_DF, x)
+    ref = _oracle(m, q, op, x)
+    assert rel_err(y, ref) <= 1e-12
+    assert np.abs(y - ref).max() <= 1e-12 * np.abs(ref).max()
+    cop = ceed.CEED_OP_DIFFUSION if op == "diffusion" else ceed.CEED_OP_MASS
+    with pytest.raises(ceed.CeedError):
+        ceed.ceed_nt_set_algorithm(nt, cop, ceed.CEED_F64_DF, ceed.CEED_NT_GEMM, 0, 0)
+    nt.close()
+
+
 GEMM_CASES = [("f64", 0, 1e-12), ("f64", 1, 1e-12), ("f32", 0, 2e-5), ("f32", 1, 2e-5), ("f32", 2, 5e-3)]
 
 
