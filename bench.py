@@ -533,6 +533,10 @@ def compact_summary(line):
         sep = cg.get("mixed_f32_reliable_separate_kernels_to_1e-10")
         if sep:
             out["cg_mixed_f32_reliable_separate_kernels_s"] = r(sep.get("seconds"))
+        spl = cg.get("mixed_f32_reliable_iteration_split")
+        if spl:
+            out["cg_mixed_f32_iter_split_ms"] = {"apply": r(spl["apply_ms"]), "vector": r(spl["vector_ms"]),
+                                                 "vector_hbm_frac": r(spl["vector_hbm_frac"])}
         for key in ("mixed_f32", "mixed_f32_reliable", "mixed_f64df_reliable", "pmg_fp32_smoothers"):
             d = cg.get(f"{key}_to_1e-10")
             if d:
@@ -801,6 +805,28 @@ def main():
                 if rep64["seconds"] > 0 and repm["seconds"] > 0:
                     cg[f"{key}_speedup"] = rep64["seconds"] / repm["seconds"]
                 if name == "f32" and mode == "reliable":
+                    # per-iteration split: the masked apply as the fused iteration runs it (element
+                    # kernel, 2 elements per block, quadrature data read directly), timed on its own,
+                    # and the rest of the iteration (the FP64 vector phases: 11 passes of 8 bytes per
+                    # entry, the reductions, the grid barriers)
+                    saved = variants.get(name)
+                    ceed.ceed_set_apply_variant(mesh, ceed.CEED_OP_DIFFUSION, prec, 2, 0)
+                    xm = torch.from_numpy(synthetic.uniform(m.n_ldof, seed=3)).to(dev)
+                    ym = torch.empty_like(xm)
+                    ms_ap = timed(lambda: ceed.ceed_apply_diffusion(mesh, qlo, prec, xm, ym,
+                                                                    flags=ceed.CEED_APPLY_DIRICHLET), 10, 3)
+                    del xm, ym
+                    if saved:
+                        ceed.ceed_set_apply_variant(mesh, ceed.CEED_OP_DIFFUSION, prec,
+                                                    max(1, saved["elems_per_block"]), saved["tma_staging"])
+                    ms_it = 1e3 * repm["seconds"] / max(1, repm["iterations"])
+                    vec_bytes = 11 * 8 * m.n_ldof
+                    cg["mixed_f32_reliable_iteration_split"] = {
+                        "ms_per_iter": ms_it, "apply_ms": ms_ap, "vector_ms": ms_it - ms_ap,
+                        "vector_bytes": vec_bytes, "vector_gbs": vec_bytes / ((ms_it - ms_ap) * 1e-3) / 1e9,
+                        "vector_hbm_frac": vec_bytes / ((ms_it - ms_ap) * 1e-3) / 1e9 / load_peaks()[0],
+                        "note": "apply timed stand-alone (masked, the fused iteration's element variant); "
+                                "vector = the rest of the iteration"}
                     # the same solve with one kernel per step instead of the fused iteration
                     st, reps = ceed.ceed_cg_solve(mesh, qd64, ceed.CEED_F64, b, xs, mode=ceed.CEED_CG_MIXED_RELIABLE,
                                                   tol=1e-10, max_iter=8000, op=ceed.CEED_OP_DIFFUSION, qdata_lo=qlo,
