@@ -336,7 +336,8 @@ def run_batched(ceed, dev, args, peaks=None, nrhs_list=(1, 4, 8, 16), steps=5, p
 
 def run_adjoint(ceed, dev, args):
     """Forward A(k) x and the fused adjoint (dL/dx, dL/dk) with a lognormal per-point k, p = 4 and 8 on
-    32^3 elements (GLL collocated), geometry stored vs recomputed from the vertices."""
+    32^3 elements (GLL collocated), geometry stored vs recomputed from the vertices, and with stored
+    geometry in the FP64-accurate double-float arithmetic."""
     import torch
     out = []
     for p in (4, 8):
@@ -352,9 +353,10 @@ def run_adjoint(ceed, dev, args):
         geo = ceed.alloc_qdata(mesh, ceed.CEED_OP_DIFFUSION, ceed.CEED_F64, dev)
         ceed.ceed_build_geometry(mesh, geo)
         row = {"p": p, "mesh": "32^3", "n_ldof": m.n_ldof, "n_qpts": m.n_elem * nq}
-        for name, g in (("stored", geo), ("recomputed", None)):
-            ms_f = _time_cuda(lambda: ceed.ceed_apply_diffusion_k(mesh, k, g, x, y), 5, 3)
-            ms_a = _time_cuda(lambda: ceed.ceed_apply_diffusion_adjoint(mesh, k, g, x, r, y, dLdk), 5, 3)
+        for name, g, fl in (("stored", geo, 0), ("recomputed", None, 0),
+                            ("stored_f64_df", geo, ceed.CEED_APPLY_F64_DF)):
+            ms_f = _time_cuda(lambda: ceed.ceed_apply_diffusion_k(mesh, k, g, x, y, flags=fl), 5, 3)
+            ms_a = _time_cuda(lambda: ceed.ceed_apply_diffusion_adjoint(mesh, k, g, x, r, y, dLdk, flags=fl), 5, 3)
             row[name] = {"forward_ms": ms_f, "adjoint_ms": ms_a, "forward_gdofs": m.n_ldof / ms_f / 1e6,
                          "adjoint_gdofs": m.n_ldof / ms_a / 1e6}
         out.append(row)

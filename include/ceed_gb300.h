@@ -74,6 +74,8 @@ typedef enum { CEED_COEFF_ONE = 0, CEED_COEFF_CONST = 1, CEED_COEFF_SINE = 2, CE
 
 /* Apply flags. */
 #define CEED_APPLY_DIRICHLET 1u  /* rows/columns of Dirichlet nodes replaced by the identity */
+#define CEED_APPLY_F64_DF 2u     /* per-point-coefficient operator and adjoint: FP64 accuracy on the FP32
+                                    pipe (double-float arithmetic; needs the stored geometry) */
 
 typedef struct {
   int64_t n_elem;            /* E >= 1 */
@@ -343,7 +345,9 @@ int ceed_build_geometry(ceed_mesh_t mesh, void *geo, void *stream);
 
 /* y = A(k) x for a per-point coefficient k (device [n_elem][Q^3], caller's element order),
  * with geometry either stored (geo from ceed_build_geometry) or recomputed from the vertices
- * (geo = NULL).  FP64.  nrhs/ncomp = 1. */
+ * (geo = NULL).  FP64; with CEED_APPLY_F64_DF (stored geometry only) the same result to FP64
+ * accuracy from double-float arithmetic on the FP32 pipe (compensated sums).  nrhs/ncomp = 1.
+ * Errors: INVALID (unknown flag bits), UNSUPPORTED (CEED_APPLY_F64_DF without stored geometry). */
 int ceed_apply_diffusion_k(ceed_mesh_t mesh, const double *k, const void *geo, const double *x,
                            double *y, unsigned flags, void *stream);
 
@@ -351,9 +355,10 @@ int ceed_apply_diffusion_k(ceed_mesh_t mesh, const double *k, const void *geo, c
  *   dLdx = A(k) r                                   (A is symmetric)
  *   dLdk[e][q] = (grad_xi r^e)_q^T Ghat_q (grad_xi x^e)_q
  * in one fused kernel per colour.  dLdx: device FP64 [n_ldof]; dLdk: device [n_elem][Q^3]
- * (caller's element order).  geo: stored geometry or NULL (recompute). */
+ * (caller's element order).  geo: stored geometry or NULL (recompute).  flags: 0, or
+ * CEED_APPLY_F64_DF (stored geometry only) for the double-float arithmetic. */
 int ceed_apply_diffusion_adjoint(ceed_mesh_t mesh, const double *k, const void *geo, const double *x,
-                                 const double *r, double *dLdx, double *dLdk, void *stream);
+                                 const double *r, double *dLdx, double *dLdk, unsigned flags, void *stream);
 
 /* ---------------------------------------------------------------- non-tensor (simplex) elements */
 

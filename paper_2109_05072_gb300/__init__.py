@@ -25,6 +25,7 @@ CEED_QRULE_GLL, CEED_QRULE_GAUSS = 0, 1
 CEED_OP_MASS, CEED_OP_DIFFUSION = 0, 1
 CEED_COEFF_ONE, CEED_COEFF_CONST, CEED_COEFF_SINE, CEED_COEFF_PER_QPT = 0, 1, 2, 3
 CEED_APPLY_DIRICHLET = 1
+CEED_APPLY_F64_DF = 2
 CEED_CG_FP64, CEED_CG_MIXED, CEED_CG_MIXED_RELIABLE = 0, 1, 2
 CEED_NT_FUSED, CEED_NT_GEMM, CEED_NT_TC = 0, 1, 2
 
@@ -113,7 +114,7 @@ def _load():
         "ceed_pmg_info": (ctypes.c_int, [vp, ctypes.c_int, ctypes.POINTER(ctypes.c_double)]),
         "ceed_pmg_destroy": (ctypes.c_int, [vp]),
         "ceed_apply_diffusion_k": (ctypes.c_int, [vp, vp, vp, vp, vp, u32, vp]),
-        "ceed_apply_diffusion_adjoint": (ctypes.c_int, [vp, vp, vp, vp, vp, vp, vp, vp]),
+        "ceed_apply_diffusion_adjoint": (ctypes.c_int, [vp, vp, vp, vp, vp, vp, vp, u32, vp]),
         "ceed_batch_create": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.c_int,
                                              ctypes.c_int, ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.c_int,
                                              ctypes.POINTER(vp)]),
@@ -474,9 +475,9 @@ def ceed_apply_diffusion_k(mesh: Mesh, k, geo, x, y, flags=0, stream=None):
     _check(_lib.ceed_apply_diffusion_k(mesh.handle, _ptr(k), _ptr(geo), _ptr(x), _ptr(y), flags, _stream(stream)))
 
 
-def ceed_apply_diffusion_adjoint(mesh: Mesh, k, geo, x, r, dLdx, dLdk, stream=None):
+def ceed_apply_diffusion_adjoint(mesh: Mesh, k, geo, x, r, dLdx, dLdk, flags=0, stream=None):
     _check(_lib.ceed_apply_diffusion_adjoint(mesh.handle, _ptr(k), _ptr(geo), _ptr(x), _ptr(r), _ptr(dLdx),
-                                             _ptr(dLdk), _stream(stream)))
+                                             _ptr(dLdk), flags, _stream(stream)))
 
 
 def ceed_simplex_sizes(p: int, q: int):
@@ -729,12 +730,14 @@ class DiffusionK(torch.autograd.Function):
 
     grad_x = A(k) grad_y (A is symmetric), grad_k[e, q] = (grad_xi g)_q^T Ghat_q (grad_xi x)_q with
     g = grad_y.  geo: stored geometry (ceed_build_geometry) or None to recompute it from the vertices.
+    df: both passes in the FP64-accurate double-float arithmetic (stored geometry only).
     """
 
     @staticmethod
-    def forward(ctx, x, k, mesh, geo):
+    def forward(ctx, x, k, mesh, geo, df=False):
         y = torch.empty_like(x)
-        ceed_apply_diffusion_k(mesh, k, geo, x, y)
+        ctx.flags = CEED_APPLY_F64_DF if df else 0
+        ceed_apply_diffusion_k(mesh, k, geo, x, y, flags=ctx.flags)
         ctx.save_for_backward(x, k)
         ctx.mesh, ctx.geo = mesh, geo
         return y
@@ -745,9 +748,9 @@ class DiffusionK(torch.autograd.Function):
         gy = gy.contiguous()
         gx = torch.empty_like(x)
         gk = torch.empty_like(k)
-        ceed_apply_diffusion_adjoint(ctx.mesh, k, ctx.geo, x, gy, gx, gk)
-        return gx, gk, None, None
+        ceed_apply_diffusion_adjoint(ctx.mesh, k, ctx.geo, x, gy, gx, gk, flags=ctx.flags)
+        return gx, gk, None, None, None
 
 
-def diffusion_k(x, k, mesh, geo=None):
-    return DiffusionK.apply(x, k, mesh, geo)
+def diffusion_k(x, k, mesh, geo=None, df=False):
+    return DiffusionK.apply(x, k, mesh, geo, df)

@@ -234,6 +234,161 @@ __global__ void __launch_bounds__(P * P * kop_ne<P>()) kop_kernel(const KArgs a)
   }
 }
 
+// The same operator and adjoint with FP64 accuracy on the FP32 pipe (flag CEED_APPLY_F64_DF): values
+// as double-float pairs (split from FP64 on the gather, collapsed to FP64 on the scatter), every
+// contraction, the pointwise products and the dL/dk bilinear form as compensated dot products
+// (Dot2, df.cuh); the geometry is the stored FP64 form, split per point.
+template <int P, bool ADJ>
+__global__ void __launch_bounds__(P * P * kop_ne<P>()) kop_df_kernel(const KArgs a, const OpTab<DF> tab) {
+  constexpr int NE = kop_ne<P>();
+  constexpr int NPT = P * P, ND = P * P * P;
+  constexpr int TW = tile_words<P>();
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  const int tid = threadIdx.x;
+  const int el = tid / NPT;
+  const int ij = tid - el * NPT;
+  const int i = ij % P, j = ij / P;
+  const int64_t e = a.e_begin + (int64_t)blockIdx.x * NE + el;
+  const bool active = e < a.e_begin + a.e_count;
+  DF *t0 = (DF *)(smem_raw + el * kop_elem_smem<P, ADJ>());
+  DF *t1 = t0 + TW, *t2 = t1 + TW;
+  DF *t3 = t2 + TW, *t4 = t3 + TW;  // adjoint only
+
+  uint32_t idx[P];
+  DF u[P], rv[P];
+#pragma unroll
+  for (int c = 0; c < P; ++c) {
+    idx[c] = active ? __ldg(a.emap + e * ND + (c * P + j) * P + i) : 0u;
+    const bool dir = a.masked && (idx[c] & FLAG_DIR);
+    const int64_t dof = idx[c] & DOF_MASK;
+    u[c] = (active && !dir) ? LVec<DF>::in(__ldg(a.x + dof)) : DF(0.f, 0.f);
+    rv[c] = (ADJ && active && !dir) ? LVec<DF>::in(__ldg(a.r + dof)) : DF(0.f, 0.f);
+  }
+  DF xt[P], xr[P], xs[P];
+  eo_apply<P, P, -1>(tab.eD, u, xt);
+#pragma unroll
+  for (int k = 0; k < P; ++k) t0[tix<P>(k, j, i)] = u[k];
+  __syncthreads();
+  {
+    DF v[P], g[P];
+#pragma unroll
+    for (int m = 0; m < P; ++m) v[m] = t0[tix<P>(j, i, m)];
+    eo_apply<P, P, -1>(tab.eD, v, g);
+#pragma unroll
+    for (int n = 0; n < P; ++n) t1[tix<P>(j, i, n)] = g[n];
+#pragma unroll
+    for (int m = 0; m < P; ++m) v[m] = t0[tix<P>(j, m, i)];
+    eo_apply<P, P, -1>(tab.eD, v, g);
+#pragma unroll
+    for (int n = 0; n < P; ++n) t2[tix<P>(j, n, i)] = g[n];
+  }
+  __syncthreads();
+  DF rt[P];
+  if constexpr (ADJ) {
+    eo_apply<P, P, -1>(tab.eD, rv, rt);
+#pragma unroll
+    for (int k = 0; k < P; ++k) t0[tix<P>(k, j, i)] = rv[k];
+    __syncthreads();
+    DF v[P], g[P];
+#pragma unroll
+    for (int m = 0; m < P; ++m) v[m] = t0[tix<P>(j, i, m)];
+    eo_apply<P, P, -1>(tab.eD, v, g);
+#pragma unroll
+    for (int n = 0; n < P; ++n) t3[tix<P>(j, i, n)] = g[n];
+#pragma unroll
+    for (int m = 0; m < P; ++m) v[m] = t0[tix<P>(j, m, i)];
+    eo_apply<P, P, -1>(tab.eD, v, g);
+#pragma unroll
+    for (int n = 0; n < P; ++n) t4[tix<P>(j, n, i)] = g[n];
+    __syncthreads();
+  }
+#pragma unroll
+  for (int k = 0; k < P; ++k) {
+    xr[k] = t1[tix<P>(k, j, i)];
+    xs[k] = t2[tix<P>(k, j, i)];
+  }
+  const int64_t eo = active ? a.perm[e] : 0;
+  DF vt[P];
+#pragma unroll
+  for (int k = 0; k < P; ++k) {
+    const int q = (k * P + j) * P + i;
+    DF g0(0.f, 0.f), g1(0.f, 0.f), g2(0.f, 0.f), g3(0.f, 0.f), g4(0.f, 0.f), g5(0.f, 0.f), kq(0.f, 0.f);
+    if (active) {
+      const double *gp = a.geo + e * a.gstride + q;
+      g0 = LVec<DF>::in(__ldg(gp));
+      g1 = LVec<DF>::in(__ldg(gp + ND));
+      g2 = LVec<DF>::in(__ldg(gp + 2 * ND));
+      g3 = LVec<DF>::in(__ldg(gp + 3 * ND));
+      g4 = LVec<DF>::in(__ldg(gp + 4 * ND));
+      g5 = LVec<DF>::in(__ldg(gp + 5 * ND));
+      kq = LVec<DF>::in(__ldg(a.k + eo * ND + q));
+    }
+    DF wr, ws, wt;
+    if constexpr (ADJ) {
+      wr = t3[tix<P>(k, j, i)];
+      ws = t4[tix<P>(k, j, i)];
+      wt = rt[k];
+    } else {
+      wr = xr[k];
+      ws = xs[k];
+      wt = xt[k];
+    }
+    const DF hr = dot3<DF>(g0, wr, g1, ws, g2, wt);
+    const DF hs = dot3<DF>(g1, wr, g3, ws, g4, wt);
+    const DF ht = dot3<DF>(g2, wr, g4, ws, g5, wt);
+    if (ADJ && active) a.dLdk[eo * ND + q] = LVec<DF>::out(dot3<DF>(hr, xr[k], hs, xs[k], ht, xt[k]));
+    t1[tix<P>(k, j, i)] = qmul<DF>(kq, hr);
+    t2[tix<P>(k, j, i)] = qmul<DF>(kq, hs);
+    vt[k] = qmul<DF>(kq, ht);
+  }
+  __syncthreads();
+  {  // transposed passes
+    DF v[P], g[P];
+#pragma unroll
+    for (int m = 0; m < P; ++m) v[m] = t1[tix<P>(j, i, m)];
+    eo_apply<P, P, -1>(tab.eDT, v, g);
+#pragma unroll
+    for (int n = 0; n < P; ++n) t0[tix<P>(j, i, n)] = g[n];
+#pragma unroll
+    for (int m = 0; m < P; ++m) v[m] = t2[tix<P>(j, m, i)];
+    eo_apply<P, P, -1>(tab.eDT, v, g);
+#pragma unroll
+    for (int n = 0; n < P; ++n) t2[tix<P>(j, n, i)] = g[n];
+  }
+  DF yt[P];
+  eo_apply<P, P, -1>(tab.eDT, vt, yt);
+  __syncthreads();
+  if (!active) return;
+#pragma unroll
+  for (int c = 0; c < P; ++c) {
+    const DF acc = add3<DF>(yt[c], t0[tix<P>(c, j, i)], t2[tix<P>(c, j, i)]);
+    const uint32_t v = idx[c];
+    const int64_t dof = v & DOF_MASK;
+    if (a.masked && (v & FLAG_DIR)) {
+      if (v & FLAG_FIRST) a.y[dof] = ADJ ? a.r[dof] : a.x[dof];
+    } else if (v & FLAG_FIRST) {
+      a.y[dof] = LVec<DF>::out(acc);
+    } else {
+      a.y[dof] = LVec<DF>::add(__ldcg(a.y + dof), acc);
+    }
+  }
+}
+
+template <int P, bool ADJ>
+static int run_kop_df(ceed_mesh_t m, KArgs a, cudaStream_t s) {
+  constexpr int NE = kop_ne<P>();
+  const size_t smem = NE * kop_elem_smem<P, ADJ>();
+  if (int st = ensure_dynamic_smem((const void *)kop_df_kernel<P, ADJ>, smem)) return st;
+  for (int c = 0; c < m->n_colors; ++c) {
+    a.e_begin = m->color_start[c];
+    a.e_count = m->color_start[c + 1] - a.e_begin;
+    if (a.e_count == 0) continue;
+    kop_df_kernel<P, ADJ><<<(unsigned)((a.e_count + NE - 1) / NE), P * P * NE, smem, s>>>(a, m->tabdf);
+  }
+  CEED_CUDA_CHECK(cudaGetLastError());
+  return CEED_OK;
+}
+
 template <int P, bool ADJ>
 static int run_kop(ceed_mesh_t m, KArgs a, cudaStream_t s) {
   constexpr int NE = kop_ne<P>();
@@ -250,7 +405,20 @@ static int run_kop(ceed_mesh_t m, KArgs a, cudaStream_t s) {
 }
 
 template <bool ADJ>
-static int dispatch_kop(ceed_mesh_t m, const KArgs &a, cudaStream_t s) {
+static int dispatch_kop(ceed_mesh_t m, const KArgs &a, bool df, cudaStream_t s) {
+  if (df) {
+    switch (m->P) {
+      case 2: return run_kop_df<2, ADJ>(m, a, s);
+      case 3: return run_kop_df<3, ADJ>(m, a, s);
+      case 4: return run_kop_df<4, ADJ>(m, a, s);
+      case 5: return run_kop_df<5, ADJ>(m, a, s);
+      case 6: return run_kop_df<6, ADJ>(m, a, s);
+      case 7: return run_kop_df<7, ADJ>(m, a, s);
+      case 8: return run_kop_df<8, ADJ>(m, a, s);
+      case 9: return run_kop_df<9, ADJ>(m, a, s);
+      default: return fail(CEED_ERR_UNSUPPORTED, "p outside 1..8");
+    }
+  }
   switch (m->P) {
     case 2: return run_kop<2, ADJ>(m, a, s);
     case 3: return run_kop<3, ADJ>(m, a, s);
@@ -287,27 +455,41 @@ static int kop_prepare(ceed_mesh_t m, const double *k, const void *geo, KArgs *a
   return CEED_OK;
 }
 
+// the arithmetic requested by the flags: CEED_APPLY_F64_DF needs the stored geometry
+static int kop_df_flag(const void *geo, unsigned flags, bool *df) {
+  if (flags & ~(CEED_APPLY_DIRICHLET | CEED_APPLY_F64_DF)) return fail(CEED_ERR_INVALID, "unknown flag bits");
+  *df = (flags & CEED_APPLY_F64_DF) != 0;
+  if (*df && !geo) return fail(CEED_ERR_UNSUPPORTED, "CEED_APPLY_F64_DF needs the stored geometry");
+  return CEED_OK;
+}
+
 extern "C" int ceed_apply_diffusion_k(ceed_mesh_t m, const double *k, const void *geo, const double *x, double *y,
                                       unsigned flags, void *stream) {
   KArgs a;
   if (int st = kop_prepare(m, k, geo, &a)) return st;
   if (!x || !y || x == y) return fail(CEED_ERR_INVALID, "bad x or y");
+  bool df = false;
+  if (int st = kop_df_flag(geo, flags, &df)) return st;
   a.x = x;
   a.y = y;
   a.masked = (flags & CEED_APPLY_DIRICHLET) ? 1 : 0;
   if (a.masked && !m->has_dirichlet) return fail(CEED_ERR_INVALID, "mesh has no Dirichlet mask");
-  return dispatch_kop<false>(m, a, (cudaStream_t)stream);
+  return dispatch_kop<false>(m, a, df, (cudaStream_t)stream);
 }
 
 extern "C" int ceed_apply_diffusion_adjoint(ceed_mesh_t m, const double *k, const void *geo, const double *x,
-                                            const double *r, double *dLdx, double *dLdk, void *stream) {
+                                            const double *r, double *dLdx, double *dLdk, unsigned flags,
+                                            void *stream) {
   KArgs a;
   if (int st = kop_prepare(m, k, geo, &a)) return st;
   if (!x || !r || !dLdx || !dLdk || dLdx == r || dLdx == x) return fail(CEED_ERR_INVALID, "bad adjoint arguments");
+  if (flags & CEED_APPLY_DIRICHLET) return fail(CEED_ERR_INVALID, "the adjoint is unmasked");
+  bool df = false;
+  if (int st = kop_df_flag(geo, flags, &df)) return st;
   a.x = x;
   a.r = r;
   a.y = dLdx;
   a.dLdk = dLdk;
   a.masked = 0;
-  return dispatch_kop<true>(m, a, (cudaStream_t)stream);
+  return dispatch_kop<true>(m, a, df, (cudaStream_t)stream);
 }

@@ -181,8 +181,11 @@ def test_dot_deterministic(ceed):
     assert abs(vals[0] - ref) <= 1e-12 * np.sqrt(n)
 
 
-@pytest.mark.parametrize("p,stored", [(4, True), (4, False), (8, True), (2, False)])
-def test_adjoint_matches_oracle(ceed, p, stored):
+@pytest.mark.parametrize("p,stored,df", [(4, True, False), (4, False, False), (8, True, False), (2, False, False),
+                                         (4, True, True), (8, True, True), (1, True, True), (6, True, True)])
+def test_adjoint_matches_oracle(ceed, p, stored, df):
+    # df: the forward operator and the adjoint in FP64-accurate double-float arithmetic (stored
+    # geometry), held to the same 1e-12 bounds
     m = synthetic.HexMesh(3, 2, 2, p, seed=11)
     sp_ = fem.Space(p, "gll")
     mesh = gpu_mesh(ceed, m, "gll")
@@ -196,7 +199,7 @@ def test_adjoint_matches_oracle(ceed, p, stored):
     kd = torch.from_numpy(k).cuda()
     xd = torch.from_numpy(x).cuda().requires_grad_(True)
     kd.requires_grad_(True)
-    y = ceed.diffusion_k(xd, kd, mesh, geo)
+    y = ceed.diffusion_k(xd, kd, mesh, geo, df)
     bd = torch.from_numpy(b).cuda()
     L = 0.5 * ((y - bd) ** 2).sum()
     L.backward()
@@ -208,11 +211,18 @@ def test_adjoint_matches_oracle(ceed, p, stored):
     v = torch.from_numpy(synthetic.uniform(k.size, seed=4).reshape(k.shape)).cuda()
     h = 1e-6 * kd.detach().abs().max() / v.abs().max()
     with torch.no_grad():
-        Lp = 0.5 * ((ceed.diffusion_k(xd.detach(), kd.detach() + h * v, mesh, geo) - bd) ** 2).sum()
-        Lm = 0.5 * ((ceed.diffusion_k(xd.detach(), kd.detach() - h * v, mesh, geo) - bd) ** 2).sum()
+        Lp = 0.5 * ((ceed.diffusion_k(xd.detach(), kd.detach() + h * v, mesh, geo, df) - bd) ** 2).sum()
+        Lm = 0.5 * ((ceed.diffusion_k(xd.detach(), kd.detach() - h * v, mesh, geo, df) - bd) ** 2).sum()
     fd = ((Lp - Lm) / (2 * h)).item()
     an = (kd.grad * v).sum().item()
     assert abs(fd - an) <= 1e-6 * abs(an)
+    if df:  # the flag needs stored geometry, and the adjoint takes no mask
+        with pytest.raises(ceed.CeedError):
+            ceed.ceed_apply_diffusion_k(mesh, kd.detach(), None, xd.detach(), torch.empty_like(xd),
+                                        flags=ceed.CEED_APPLY_F64_DF)
+        with pytest.raises(ceed.CeedError):
+            ceed.ceed_apply_diffusion_adjoint(mesh, kd.detach(), geo, xd.detach(), bd, torch.empty_like(xd),
+                                              torch.empty_like(kd), flags=ceed.CEED_APPLY_DIRICHLET)
     mesh.close()
 
 
